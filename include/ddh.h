@@ -1,0 +1,187 @@
+/*
+ * ddh.h -- C ABI of the GB300 dual-primal domain-decomposition spectral-element Helmholtz
+ * solver (Galagusz & McFee, "An iterative domain decomposition, spectral finite element
+ * method on non-conforming meshes suitable for high frequency Helmholtz problems").
+ *
+ * Problem (Sec. 2, eqs. prototype_pde / prototype_robin with alpha = I, beta = -k^2 eps,
+ * gamma = -i k, q = g):   -lap u - k^2 eps(x) u = 0 in [0,1]^2,  du/dn - i k u = g on the
+ * boundary, discretised by degree-p tensor-product integrated-Legendre elements on a quadtree
+ * of squares (Sec. 2.2), with weak hierarchical edge-moment continuity (eq. final_constraint)
+ * and hanging nodes.  The saddle system is solved by the partial-nullspace dual-primal method
+ * (Sec. 2.3): primal constraints are vertex continuity plus the first l-1 bubble moments per
+ * edge (l from eq. dispersion_criterion unless overridden), the dual interface problem
+ * C^ A^-1 C^T nu = C^ A^-1 b^ (eq. schur_complement_system) by flexible GMRES with the
+ * Dirichlet preconditioner (eqs. general_preconditioner, weight_matrix).
+ *
+ * Conventions
+ *  - Every function returns ddh_status; DDH_OK == 0.  No C++ exception crosses the ABI.
+ *    On error, ddh_last_error() returns a message owned by the context.
+ *  - Vectors of element coefficients ("local vectors") are complex128 (interleaved
+ *    re, im doubles), laid out [R][n_local]: elements in leaf order, each element's
+ *    (p+1) x (p+1) coefficient matrix Phi of the N basis (the paper's phi, Sec. 2.2.1)
+ *    stored column-major (x1 index fastest).  ddh_elem_offsets gives element starts.
+ *  - Device pointers must be on the context's device, 16-byte aligned; the caller owns
+ *    them and keeps them alive until the call returns (calls synchronise the context
+ *    stream before returning unless stated otherwise).  Host pointers are read during the
+ *    call only.
+ *  - The context owns every internal buffer and the factorisation; a context is not
+ *    thread safe.  All device work is enqueued on the stream given to ddh_create.
+ */
+#ifndef DDH_H
+#define DDH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ddh_ctx ddh_ctx;
+
+typedef enum {
+    DDH_OK = 0,
+    DDH_ERR_INVALID_ARG = 1,     /* bad pointer, size, mesh or option */
+    DDH_ERR_CUDA = 2,            /* a CUDA runtime call failed (message has the CUDA error) */
+    DDH_ERR_OOM = 3,             /* device allocation failed */
+    DDH_ERR_NOT_READY = 4,       /* call order violated (e.g. solve before factor) */
+    DDH_ERR_NO_CONVERGENCE = 5,  /* tolerance not reached in maxit; best iterate written */
+    DDH_ERR_SINGULAR = 6,        /* a local or coarse matrix is singular (resonant element) */
+    DDH_WARN_NEAR_RESONANT = 7,  /* factor succeeded; some element is within 1e-6 of resonance */
+    DDH_ERR_DEVICE_FLAG = 8      /* a kernel reported an error through its status word */
+} ddh_status;
+
+/* Precision of the interface-operator applications inside the Krylov loop. */
+typedef enum {
+    DDH_PREC_FP64 = 0,           /* plain method: everything complex128 */
+    DDH_PREC_MIXED_FP32 = 1      /* complex64 local solves / gather / scatter / preconditioner
+                                    inside an FP64 flexible-GMRES refinement on the
+                                    conforming primal system; coarse solve, residuals and
+                                    Arnoldi stay FP64 */
+} ddh_precision;
+
+typedef enum { DDH_PRECOND_DIRICHLET = 0, DDH_PRECOND_LUMPED = 1, DDH_PRECOND_NONE = 2 } ddh_precond;
+
+typedef struct {
+    double tol;            /* relative residual target (default 1e-10) */
+    int32_t maxit;         /* total Krylov iterations per RHS (default 300) */
+    int32_t restart;       /* FGMRES restart length m (default 100, max 200) */
+    int32_t l_override;    /* 0: dispersion criterion; >0: primal constraints per edge */
+    int32_t precision;     /* ddh_precision */
+    int32_t precond;       /* ddh_precond */
+    int32_t inner_iters;   /* mixed precision: dual FGMRES iterations per preconditioner
+                              application (default 12) */
+    int32_t check_every;   /* host polls convergence every this many iterations (default 4) */
+    int32_t use_graph;     /* 1: replay one FGMRES iteration as a CUDA graph (default 1) */
+} ddh_options;
+
+typedef struct {
+    int32_t n_elem;
+    int32_t l;             /* primal constraints per edge in use */
+    int64_t n_local;       /* sum over elements of (p+1)^2 */
+    int64_t n_dual;        /* dual rows (interface unknowns nu) */
+    int64_t n_coarse;      /* coarse (type-2) unknowns, size of K */
+    int64_t n_conforming;  /* global conforming DoF */
+    int32_t n_coarse_blocks;
+    int32_t max_block;     /* largest diagonal block of the coarse factorisation */
+    double min_resonance_gap; /* min over elements of min |D_ab| / max |D_ab| of the FDM */
+    double factor_seconds; /* wall time of the last ddh_factor */
+} ddh_info;
+
+typedef struct {
+    int32_t iterations;    /* Krylov iterations (outer iterations in mixed mode) */
+    int32_t inner_iterations; /* mixed mode: total inner dual iterations */
+    double dual_residual;  /* plain: final ||g - F nu|| / ||g|| (estimate, then true) */
+    double primal_residual;/* ||Z_c^T (b - A phi)|| / ||Z_c^T b|| in FP64 */
+} ddh_rhs_stats;
+
+/* Fill *opt with the defaults listed above. */
+void ddh_default_options(ddh_options* opt);
+
+/* Create a context on CUDA device `device`; `cuda_stream` is a cudaStream_t (NULL: the
+ * legacy default stream).  The stream is borrowed, not destroyed by ddh_destroy. */
+ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream);
+
+/* Quadtree mesh of [0,1]^2 (Sec. 2.2.3): base_n x base_n base squares; leaf e is
+ * (level, i, j) = leaves[3e..3e+2], the square of side 1/(base_n 2^level) with lower-left
+ * corner (i, j) * side.  p[e] in [3, 32] is its degree.  Leaves must tile the square
+ * exactly (checked).  Host pointers. */
+ddh_status ddh_set_mesh(ddh_ctx* ctx, int32_t base_n, const int32_t* leaves,
+                        const int32_t* p, int32_t n_elem);
+
+/* Wavenumber k > 0 and relative permittivity eps_r[e] > 0 per element (host pointer). */
+ddh_status ddh_set_coefficients(ddh_ctx* ctx, double k, const double* eps_r);
+
+/* Build every table and factor: per-element edge Schur complements of A11 through the
+ * fast-diagonalisation solver (Sec. 2.2.1 fast solver; Sec. 2.3.3 block inversion), the
+ * coarse matrix K = A22 - A12^T A11^-1 A12 and its block-tridiagonal LU, the preconditioner
+ * pieces.  Returns DDH_WARN_NEAR_RESONANT when an element is within 1e-6 of a resonance of
+ * A11 (the factorisation is still usable).  opt may be NULL (defaults). */
+ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt);
+
+ddh_status ddh_get_info(const ddh_ctx* ctx, ddh_info* out);
+
+/* Element start offsets into a local vector, host array of n_elem + 1 int64. */
+ddh_status ddh_elem_offsets(const ddh_ctx* ctx, int64_t* offsets_host);
+
+/* Load vectors b (Sec. 2.2.1, r_i terms) of R plane-wave problems: g = du/dn - i k u of
+ * u = exp(i k (x cos theta + y sin theta)) on every boundary side.  theta: host [R];
+ * b_dev: device complex128 [R][n_local] written (N basis). */
+ddh_status ddh_rhs_planewave(ddh_ctx* ctx, const double* theta, int32_t R, void* b_dev);
+
+/* Solve A-phi = b subject to the continuity constraints for R right-hand sides.
+ * b_dev, u_dev: device complex128 [R][n_local] (N basis).  tol <= 0 uses the factor
+ * options' tol.  stats: host array of R entries, or NULL.  Returns
+ * DDH_ERR_NO_CONVERGENCE (best iterate written) if some RHS missed the tolerance. */
+ddh_status ddh_solve(ddh_ctx* ctx, const void* b_dev, void* u_dev, int32_t R, double tol,
+                     ddh_rhs_stats* stats);
+
+/* Same as ddh_solve with host buffers: copies b to the device, solves, copies u back
+ * (all on the context stream; the copies are part of the call). */
+ddh_status ddh_solve_host(ddh_ctx* ctx, const void* b_host, void* u_host, int32_t R,
+                          double tol, ddh_rhs_stats* stats);
+
+/* Adjoint solve A^H lambda = g.  The operator is complex symmetric (A^T = A, gamma = -ik),
+ * so A^H = conj(A) and lambda = conj(solve(conj(g))).  Layout as ddh_solve. */
+ddh_status ddh_adjoint_solve(ddh_ctx* ctx, const void* g_dev, void* lam_dev, int32_t R,
+                             double tol, ddh_rhs_stats* stats);
+
+/* Gradient of J = sum_r Re(<lambda_r, ...>) style adjoint objectives with respect to the
+ * element permittivities: grad_eps[e] = sum_r Re( lambda_r^T (dA/deps_e) u_r ) * (-1), i.e.
+ * dJ/deps_e = k^2 Re( lambda_e^T M_e u_e ) summed over r, with M_e = (h_e/2)^2 M (x) M the
+ * element mass matrix, for lambda solving A^T lambda = dJ/du (complex-symmetric A).
+ * u_dev, lam_dev: device [R][n_local]; grad_eps_dev: device double [n_elem] (written). */
+ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, int32_t R,
+                        double* grad_eps_dev);
+
+/* Point evaluation u(x_i) of local vectors (adjoint = 0), or its transpose, the injection
+ * of point weights into a local vector (adjoint = 1).  xy: host [n][2] inside [0,1]^2.
+ * adjoint = 0: in_dev [R][n_local] -> out_dev complex128 [R][n].
+ * adjoint = 1: in_dev complex128 [R][n] -> out_dev [R][n_local] (overwritten). */
+ddh_status ddh_eval_points(ddh_ctx* ctx, const double* xy, int32_t n, int32_t R,
+                           const void* in_dev, void* out_dev, int32_t adjoint);
+
+/* FP64 primal residual ||Z_c^T (b - A phi)|| / ||Z_c^T b|| per RHS (the conforming
+ * assembled system, Sec. 2.3.1 with every constraint primal).  out_host: [R]. */
+ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
+                               double* out_host);
+
+/* Number of kernels this context launched since creation (for launch accounting). */
+int64_t ddh_kernel_launches(const ddh_ctx* ctx);
+
+const char* ddh_last_error(const ddh_ctx* ctx);
+void ddh_destroy(ddh_ctx* ctx);
+
+/* ---- host-only table checks (no GPU needed; used by the CPU test suite) ----
+ * Affine re-expansion N~(a t + b) = Lt N~(t) of the interpolatory basis computed by the
+ * Sylvester row recurrence of Sec. 2.1.6; out: (n+1)^2 doubles, row-major Lt[k][m]. */
+ddh_status ddh_table_affine(int32_t n, double a, double b, double* out);
+/* Bubble-mass fast-diagonalisation table for degree p: V (n x n, row-major, n = p-1) and
+ * mu (n) with M_b = V diag(mu) V^T (even/odd blocks, own implicit-QL eigensolver). */
+ddh_status ddh_table_fdm(int32_t p, double* V_out, double* mu_out);
+/* Gauss-Legendre nodes/weights by the Golub-Welsch method (own eigensolver). */
+ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDH_H */

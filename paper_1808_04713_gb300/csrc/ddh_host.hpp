@@ -1,0 +1,119 @@
+// Host-side model of the dual-primal DD spectral-element Helmholtz solver: per-degree
+// tables, quadtree bookkeeping, unknown classification and the factorisation.
+// Everything here is plain C++17 (runs on the x86 build host and the Arm GPU host alike).
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ddh {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------- 1-D tables (Sec. 2.1)
+struct PTable {
+    int p = 0, n = 0;                 // degree, interior size n = p - 1
+    std::vector<double> Mt;           // (p+1)^2 row-major: int N~ N~^T (interpolatory basis mass)
+    std::vector<double> V;            // n x n row-major: bubble-mass eigenvectors (even/odd blocks)
+    std::vector<double> mu;           // n eigenvalues
+    std::vector<double> Slap;         // (4(p-1))^2 row-major: stiffness Schur complement onto all
+                                      // edge bubbles (side s, bubble m) -> s*(p-1) + m-2
+    std::vector<double> Btrans;       // (p+1)^2 row-major B matrix (N~ = B N), for basis changes
+};
+
+void legendre_S(int n, std::vector<double>& S);                  // (n+1)^2 row-major
+void tilde_mass(int p, std::vector<double>& Mt);
+void sym_eig_jacobi(int n, std::vector<double> A, std::vector<double>& w, std::vector<double>& Vc);
+void gauss_legendre(int m, std::vector<double>& x, std::vector<double>& w);
+void affine_tilde(int n, double a, double b, std::vector<double>& Lt);  // (n+1)^2, Lt[k][m]
+void fdm_table(int p, std::vector<double>& V, std::vector<double>& mu);
+PTable make_ptable(int p);
+
+// ---------------------------------------------------------------- mesh model
+struct SlaveTerm { int32_t col; double w; };
+
+struct Elem {
+    int p = 0, n = 0, lev = 0, i = 0, j = 0;
+    int64_t X0 = 0, X1 = 0, Y0 = 0, Y1 = 0;       // integer box (finest units)
+    double h = 0, x0 = 0, y0 = 0, eps = 1, c = 0;
+    cd gam[4];                                     // Robin gamma_eff per side (0 if interior)
+    bool boundary[4] = {false, false, false, false};
+    int64_t off = 0;                               // start in local vectors
+    int32_t e1_off = 0, nE1 = 0;                   // E1 (type-1 edge) slots
+    int32_t t_off = 0, nT = 0;                     // T (type-2 / slaved) slots
+    int64_t sinv_off = 0;                          // start of nE1^2 complex inverse
+    int32_t ptab = 0;                              // index into tables
+};
+
+struct MasterEdge {
+    int kind = 0;                 // 0 boundary, 1 conforming, 2 hanging
+    int elem = 0, side = 0;       // boundary elem / conforming left-bottom elem / coarse elem
+    struct Sub { int elem, side; double a, b; };
+    std::vector<Sub> subs;        // conforming: 1 entry (a=1, b=0); hanging: fine sides
+    int degree = 0;               // trace degree d (min incident degree)
+    int64_t Y2 = 0;               // twice the y coordinate of the edge midpoint (block ordering)
+};
+
+struct Model {
+    // inputs
+    int base_n = 0, maxlev = 0;
+    std::vector<Elem> el;
+    double k = 0;
+    int l = 0;
+    // tables
+    std::vector<PTable> tabs;
+    std::vector<int> ptab_of_p;   // p -> table index
+    // mesh
+    std::vector<MasterEdge> edges;
+    std::vector<std::pair<int, int>> side_edge;   // [4e+s] -> (edge, role 0 b / 1 c / 2 f)
+    int64_t n_local = 0;
+    int32_t n_vert = 0, n_coarse = 0;
+    std::vector<int64_t> coarse_Y2;               // twice the y of each coarse dof
+    // slots
+    std::vector<int32_t> e1_slot, e1_row, e1_eall;
+    std::vector<double> e1_sign;
+    std::vector<int32_t> t_slot, t_ptr, t_col;
+    std::vector<double> t_w;
+    // dual rows
+    int64_t n_dual = 0;
+    std::vector<int32_t> row_c, row_f;            // E1 global index (c may be -1)
+    std::vector<int32_t> row_hblock;              // -1 conforming, else hanging block id
+    std::vector<int32_t> c2_ptr, c2_col;          // C2 CSR by dual row
+    std::vector<double> c2_w;
+    std::vector<int32_t> hblk_row0, hblk_n;       // hanging blocks of D
+    std::vector<double> hblk_Dinv;                // dense inverses, concatenated
+    std::vector<int64_t> hblk_off;
+    std::vector<int32_t> mh_ptr, mh_col;          // C2 K^Lap C2^T on hanging rows (CSR)
+    std::vector<double> mh_val;
+    // conforming (all constraints primal) numbering for the primal residual
+    int64_t n_conf = 0;
+    std::vector<int32_t> cf_ptr, cf_col;          // per local slot (n_local+1), tilde basis
+    std::vector<double> cf_w;
+    // factor
+    std::vector<cd> sinv;                         // per element nE1^2, column-major
+    double min_gap = 1e300;
+    // coarse factorisation (block tridiagonal over base rows)
+    int nb = 0;
+    std::vector<int32_t> blk_of;                  // coarse dof -> block
+    std::vector<int32_t> pos_in_blk;              // coarse dof -> position inside its block
+    std::vector<int32_t> blk_size, blk_start;     // block sizes and start in the permuted order
+    std::vector<int32_t> perm;                    // permuted position -> coarse dof
+    std::vector<std::vector<cd>> Dinv, Lo, Up;    // per block dense row-major
+    bool dense_coarse = false;                    // use a dense K^-1 instead
+    std::vector<cd> Kinv;                         // n_coarse^2 row-major when dense_coarse
+    std::string err;
+};
+
+bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, int n_elem,
+                 std::string& err);
+void set_coefficients(Model& m, double k, const double* eps);
+int dispersion_l(const Model& m);
+bool classify(Model& m, int l, std::string& err);
+bool factor(Model& m, int nthreads, std::string& err);
+
+// entry of the element operator (interpolatory basis) for element e:
+// A[(a,b),(c,d)] = Kt[a,c] Mt[b,d] + Mt[a,c] Kt[b,d] + c_e Mt[a,c] Mt[b,d] + Robin.
+cd elem_entry(const Model& m, const Elem& e, int a, int b, int c, int d, bool stiff_only);
+
+}  // namespace ddh

@@ -1,0 +1,53 @@
+// Host-callable launch wrappers of the CUDA kernels (one translation unit owns the kernels).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include "ddh_dev.cuh"
+
+namespace ddh {
+
+// Flexible-GMRES state on the device (FP64).  Per RHS r: V[r][j][nd] (j <= m),
+// Zb[r][j][nd] (j < m), H[r][j][m+1] (column j), cs[r][m], sn[r][m], g[r][m+1].
+// ctl[0] = current column j, ctl[1] = stop flag (all converged or restart boundary).
+struct KrylovDev {
+    double2* V; double2* Zb; double2* H; double* cs; double2* sn; double2* g; double* bnorm;
+    double* resid; int* ctl; int* rdone; int* iters; double2* partial; double2* hcol; double2* w;
+    double2* vin; double2* zw;
+    int nd, m, R, nchunk; double tol;
+};
+
+template <class T>
+void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
+                  int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+template <class T>
+void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
+                            double2* t, int R, const int* done, cudaStream_t st);
+template <class T>
+void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const void* xE_in, void* xE_out,
+                  int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st);
+template <class T>
+void launch_jump_gather(const DevModel& dm, const void* xE, const double2* x2, double2* w, int R, const int* done,
+                        cudaStream_t st);
+template <class T>
+void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, double2* m, double2* z, int lumped,
+                int R, const int* done, cudaStream_t st);
+
+void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st);
+void launch_gemv(const double2* A, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
+                 int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st);
+void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
+                          int nq, double2* bt, int R, cudaStream_t st);
+void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st);
+void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st);
+void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st);
+void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st);
+void launch_fetch(const KrylovDev& K, cudaStream_t st);
+void launch_store(const KrylovDev& K, cudaStream_t st);
+void launch_update(const double2* Zb, const double2* y, const int* nit, double2* nu, int nd, int m, int R, cudaStream_t st);
+void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st);
+void launch_norm2(const double2* x, int64_t n, double* out, int R, cudaStream_t st);
+size_t pass_smem(int pmax, bool fp64);
+void set_smem_limits(int pmax);
+
+}  // namespace ddh

@@ -1,0 +1,234 @@
+"""ctypes binding of libddh.so (argument marshalling only; every step runs in the library).
+
+The library must have been built (``paper_1808_04713_gb300.build.build()``); loading fails
+loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libddh.so")
+_lib = None
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_READY, ERR_NO_CONVERGENCE, ERR_SINGULAR, \
+    WARN_NEAR_RESONANT, ERR_DEVICE_FLAG = range(9)
+PREC_FP64, PREC_MIXED_FP32 = 0, 1
+PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
+
+
+class DDHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ddh status {status}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
+                ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
+                ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("l", C.c_int32), ("n_local", C.c_int64),
+                ("n_dual", C.c_int64), ("n_coarse", C.c_int64), ("n_conforming", C.c_int64),
+                ("n_coarse_blocks", C.c_int32), ("max_block", C.c_int32),
+                ("min_resonance_gap", C.c_double), ("factor_seconds", C.c_double)]
+
+
+class RhsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("inner_iterations", C.c_int32),
+                ("dual_residual", C.c_double), ("primal_residual", C.c_double)]
+
+
+_SIGS = {
+    "ddh_default_options": (None, [C.POINTER(Options)]),
+    "ddh_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "ddh_set_mesh": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ddh_set_coefficients": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
+    "ddh_factor": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "ddh_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    "ddh_elem_offsets": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ddh_rhs_planewave": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ddh_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
+    "ddh_solve_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
+    "ddh_adjoint_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
+    "ddh_grad_eps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ddh_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ddh_primal_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "ddh_last_error": (C.c_char_p, [C.c_void_p]),
+    "ddh_destroy": (None, [C.c_void_p]),
+    "ddh_table_affine": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_void_p]),
+    "ddh_table_fdm": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
+    "ddh_table_gauss": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
+}
+
+
+def load_library(path: str | None = None):
+    """Load libddh.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libddh.so not built at {p}; run paper_1808_04713_gb300.build.build()")
+    lib = C.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().ddh_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class DDH:
+    """One solver context on one CUDA device (names follow the C ABI)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load_library()
+        self.torch = torch
+        self.device = device
+        self.h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(stream.cuda_stream)
+        self._check(self.lib.ddh_create(C.byref(self.h), device, s))
+        self.n_elem = 0
+        self.n_local = 0
+        self.last_status = OK
+
+    def _check(self, st: int, allow=(OK,)):
+        self.last_status = st
+        if st not in allow:
+            msg = self.lib.ddh_last_error(self.h).decode() if self.h else "create failed"
+            raise DDHError(st, msg)
+        return st
+
+    def close(self):
+        if self.h:
+            self.lib.ddh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup
+    def set_mesh(self, base_n: int, leaves, p):
+        lv = np.ascontiguousarray(leaves, dtype=np.int32)
+        pp = np.ascontiguousarray(p, dtype=np.int32)
+        self._check(self.lib.ddh_set_mesh(self.h, int(base_n), lv.ctypes.data, pp.ctypes.data, int(lv.shape[0])))
+        self.n_elem = int(lv.shape[0])
+
+    def set_coefficients(self, k: float, eps):
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        self._check(self.lib.ddh_set_coefficients(self.h, float(k), e.ctypes.data))
+
+    def factor(self, **opts) -> int:
+        o = default_options(**opts)
+        st = self._check(self.lib.ddh_factor(self.h, C.byref(o)), allow=(OK, WARN_NEAR_RESONANT))
+        self.n_local = self.info().n_local
+        return st
+
+    def info(self) -> Info:
+        i = Info()
+        self._check(self.lib.ddh_get_info(self.h, C.byref(i)))
+        return i
+
+    def elem_offsets(self) -> np.ndarray:
+        o = np.zeros(self.n_elem + 1, np.int64)
+        self._check(self.lib.ddh_elem_offsets(self.h, o.ctypes.data))
+        return o
+
+    def _vec(self, R):
+        return self.torch.zeros((R, self.n_local), dtype=self.torch.complex128, device=f"cuda:{self.device}")
+
+    def rhs_planewave(self, thetas):
+        th = np.ascontiguousarray(np.atleast_1d(thetas), dtype=np.float64)
+        b = self._vec(th.size)
+        self._check(self.lib.ddh_rhs_planewave(self.h, th.ctypes.data, int(th.size), _ptr(b)))
+        return b
+
+    def solve(self, b, tol: float = 0.0, out=None, stats: bool = True, allow_noconv: bool = False):
+        b = b.contiguous()
+        R = b.shape[0]
+        u = self._vec(R) if out is None else out
+        st = (RhsStats * R)() if stats else None
+        allow = (OK, ERR_NO_CONVERGENCE) if allow_noconv else (OK,)
+        self._check(self.lib.ddh_solve(self.h, _ptr(b), _ptr(u), R, float(tol),
+                                       C.cast(st, C.c_void_p) if stats else None), allow=allow)
+        return u, (list(st) if stats else None)
+
+    def solve_host(self, b_host: np.ndarray, tol: float = 0.0, stats: bool = False):
+        b = np.ascontiguousarray(b_host, dtype=np.complex128)
+        u = np.zeros_like(b)
+        R = b.shape[0]
+        st = (RhsStats * R)() if stats else None
+        self._check(self.lib.ddh_solve_host(self.h, b.ctypes.data, u.ctypes.data, R, float(tol),
+                                            C.cast(st, C.c_void_p) if stats else None))
+        return u, (list(st) if stats else None)
+
+    def adjoint_solve(self, g, tol: float = 0.0):
+        g = g.contiguous()
+        R = g.shape[0]
+        lam = self._vec(R)
+        st = (RhsStats * R)()
+        self._check(self.lib.ddh_adjoint_solve(self.h, _ptr(g), _ptr(lam), R, float(tol), C.cast(st, C.c_void_p)))
+        return lam, list(st)
+
+    def primal_residual(self, b, u) -> np.ndarray:
+        R = b.shape[0]
+        out = np.zeros(R)
+        self._check(self.lib.ddh_primal_residual(self.h, _ptr(b.contiguous()), _ptr(u.contiguous()), R, out.ctypes.data))
+        return out
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.ddh_kernel_launches(self.h))
+
+
+# -- host-only tables (no GPU needed)
+def table_affine(n: int, a: float, b: float) -> np.ndarray:
+    out = np.zeros((n + 1, n + 1))
+    st = load_library().ddh_table_affine(n, a, b, out.ctypes.data)
+    if st:
+        raise DDHError(st, "table_affine")
+    return out
+
+
+def table_fdm(p: int):
+    n = p - 1
+    V = np.zeros((n, n))
+    mu = np.zeros(n)
+    st = load_library().ddh_table_fdm(p, V.ctypes.data, mu.ctypes.data)
+    if st:
+        raise DDHError(st, "table_fdm")
+    return V, mu
+
+
+def table_gauss(m: int):
+    x = np.zeros(m)
+    w = np.zeros(m)
+    st = load_library().ddh_table_gauss(m, x.ctypes.data, w.ctypes.data)
+    if st:
+        raise DDHError(st, "table_gauss")
+    return x, w
