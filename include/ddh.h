@@ -165,6 +165,14 @@ ddh_status ddh_eval_points(ddh_ctx* ctx, const double* xy, int32_t n, int32_t R,
 ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
                                double* out_host);
 
+/* Time the components of one interface-operator application F = C^ A^-1 C^T and of the
+ * preconditioner on the context stream with CUDA events, each launched `reps` times on the
+ * buffers of the last solve (call after a ddh_solve with the same R and precision).
+ * ms_out[0..5]: average milliseconds per launch of pass 1 (local solve, FDM cross +
+ * S_E^-1), coarse assembly, coarse solve, pass 2, jump gather, preconditioner.
+ * precision: ddh_precision of the element-level kernels to time. */
+ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t reps, double* ms_out);
+
 /* Number of kernels this context launched since creation (for launch accounting). */
 int64_t ddh_kernel_launches(const ddh_ctx* ctx);
 

@@ -892,6 +892,52 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
     return DDH_OK;
 }
 
+ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t reps, double* ms_out) {
+    if (!ctx || !ms_out || R <= 0 || reps <= 0) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored || ctx->K_R != R) return fail(ctx, DDH_ERR_NOT_READY, "solve with the same R first");
+    const bool fp64 = precision == DDH_PREC_FP64;
+    Work w;
+    ddh_status st;
+    if ((st = get_op_work(ctx, R, fp64, w))) return st;
+    const DevModel& d = ctx->dm;
+    KrylovDev& K = ctx->K;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timeit = [&](auto&& fn) -> double {
+        fn();
+        cudaEventRecord(e0, ctx->stream);
+        for (int i = 0; i < reps; ++i) fn();
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / reps;
+    };
+    const void* sinv = fp64 ? ctx->sinv64 : ctx->sinv32;
+    cudaStream_t s = ctx->stream;
+    const double2* z = K.zw;
+    if (fp64) {
+        ms_out[0] = timeit([&] { launch_pass1<double>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s); });
+        ms_out[1] = timeit([&] { launch_coarse_assemble<double>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
+        ms_out[3] = timeit([&] { launch_pass2<double>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s); });
+        ms_out[4] = timeit([&] { launch_jump_gather<double>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
+        ms_out[5] = timeit([&] { launch_pre<double>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
+    } else {
+        ms_out[0] = timeit([&] { launch_pass1<float>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s); });
+        ms_out[1] = timeit([&] { launch_coarse_assemble<float>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
+        ms_out[3] = timeit([&] { launch_pass2<float>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s); });
+        ms_out[4] = timeit([&] { launch_jump_gather<float>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
+        ms_out[5] = timeit([&] { launch_pre<float>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
+    }
+    // the coarse solve overwrites its input in block-tridiagonal mode: keep a copy
+    ms_out[2] = timeit([&] { coarse_solve(ctx, w.t, w.x2, w.ctmp, R, nullptr); });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    return DDH_OK;
+}
+
 int64_t ddh_kernel_launches(const ddh_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 const char* ddh_last_error(const ddh_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }

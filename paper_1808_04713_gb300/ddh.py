@@ -60,6 +60,7 @@ _SIGS = {
     "ddh_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
     "ddh_primal_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "ddh_profile_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "ddh_last_error": (C.c_char_p, [C.c_void_p]),
     "ddh_destroy": (None, [C.c_void_p]),
     "ddh_table_affine": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_void_p]),
@@ -200,6 +201,12 @@ class DDH:
         R = b.shape[0]
         out = np.zeros(R)
         self._check(self.lib.ddh_primal_residual(self.h, _ptr(b.contiguous()), _ptr(u.contiguous()), R, out.ctypes.data))
+        return out
+
+    def profile_op(self, R: int, precision: int = PREC_FP64, reps: int = 20) -> np.ndarray:
+        """Average ms per launch: pass1, coarse assembly, coarse solve, pass2, jump gather, precond."""
+        out = np.zeros(6)
+        self._check(self.lib.ddh_profile_op(self.h, R, precision, reps, out.ctypes.data))
         return out
 
     def kernel_launches(self) -> int:

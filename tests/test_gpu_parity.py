@@ -1,0 +1,139 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle on identical seeded inputs.
+
+Tolerance: FP64 plain path, relative L2 over the element-local N-basis coefficients
+<= 1e-10 (both sides solved to relative residual 1e-12 so the stopping point does not
+dominate); identical FGMRES iteration counts (same algorithm, same preconditioner).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import dd  # noqa: E402
+from paper_1808_04713_gb300 import ddh  # noqa: E402
+
+SMALL = {
+    "plane_2x2": W.plane_2x2,
+    "uniform3_eps": lambda: W.small_uniform(3, 6, 8.0, seed=2, eps_range=(1, 2)),
+    "uniform4_mixed_p": lambda: W.small_uniform(4, 6, 9.0, seed=7, eps_range=(1, 2), p_range=(4, 9)),
+    "hanging_1level": lambda: W.small_hanging(3, refine=[(1, 1)], levels=1, p=6, k=5.0),
+    "hanging_2level": lambda: W.small_hanging(3, refine=[(1, 1)], levels=2, p=6, k=5.0),
+    "hanging_mixed_p": lambda: W.small_hanging(3, refine=[(1, 1)], levels=2, p=6, k=5.0, seed=1,
+                                               p_range=(4, 8), eps_in=2.0),
+    "hanging_corner": lambda: W.small_hanging(4, refine=[(0, 0), (3, 2)], levels=2, p=7, k=9.0, seed=4,
+                                              p_range=(5, 9), n_rhs=3),
+    "multilevel": lambda: W.multilevel_hanging(p=5, k=3.0),
+}
+
+
+def _solver(w, **opt):
+    s = ddh.DDH(0)
+    s.set_mesh(w.base_n, w.leaves, w.p)
+    s.set_coefficients(w.k, w.eps)
+    s.factor(**opt)
+    return s
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("l", [None, 1, 2])
+def test_solution_matches_oracle(name, l):
+    w = SMALL[name]()
+    s = _solver(w, tol=1e-12, l_override=l or 0)
+    lu = s.info().l
+    b = s.rhs_planewave(w.thetas)
+    u, st = s.solve(b, tol=1e-12)
+    prob = dd.problem_from_workload(w)
+    # load vectors first: same boundary data, independent quadrature
+    bref = prob.b_N
+    assert np.linalg.norm(b.cpu().numpy() - bref) <= 1e-12 * np.linalg.norm(bref)
+    ref = dd.DDSolver(prob, l=lu).solve(tol=1e-12)
+    got = u.cpu().numpy()
+    for r in range(got.shape[0]):
+        err = np.linalg.norm(got[r] - ref["phi_N"][r]) / np.linalg.norm(ref["phi_N"][r])
+        assert err <= 1e-10, (name, l, r, err)
+        assert abs(st[r].iterations - ref["iterations"][r]) <= 1
+        assert st[r].primal_residual <= 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("precond", [ddh.PRECOND_LUMPED, ddh.PRECOND_NONE])
+def test_other_preconditioners(precond):
+    w = SMALL["hanging_2level"]()
+    s = _solver(w, tol=1e-12, precond=precond, l_override=2)
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-12)
+    prob = dd.problem_from_workload(w)
+    ref = dd.Conforming(prob).solve_direct()
+    assert np.linalg.norm(u.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-10
+    s.close()
+
+
+def test_plane_wave_closed_form_2x2():
+    """p = 8 on 2x2 squares, k = 10: the discretisation error of the exact plane wave."""
+    w = W.plane_2x2()
+    s = _solver(w, tol=1e-10)
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
+    prob = dd.problem_from_workload(w)
+    rng = np.random.default_rng(0)
+    x, y = rng.uniform(0, 1, 400), rng.uniform(0, 1, 400)
+    f = dd.field_at(prob, u.cpu().numpy()[0], x, y)
+    err = np.abs(f - dd.plane_wave(w.k, w.thetas[0])(x, y)).max()
+    assert 1e-7 < err < 1e-4        # spectral error at p = 8 (oracle's own value ~2e-5)
+    assert st[0].dual_residual <= 1e-10 and st[0].primal_residual <= 1e-10
+
+
+def test_full_size_16x16_against_oracle():
+    """The 16x16, p = 16, k = 100 plane-wave workload at full size: element-by-element
+    against the oracle's dual-primal solve, plus the oracle's own primal residual of the
+    GPU solution."""
+    w = W.plane_16x16()
+    s = _solver(w, tol=1e-10)
+    assert s.info().l == 4 and s.info().n_dual == 5760 and s.info().n_coarse == 1921
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
+    assert st[0].dual_residual <= 1e-10 and st[0].primal_residual <= 1e-10
+    prob = dd.problem_from_workload(w)
+    ref = dd.DDSolver(prob).solve(tol=1e-10)
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - ref["phi_N"]) / np.linalg.norm(ref["phi_N"]) <= 1e-9
+    assert abs(st[0].iterations - ref["iterations"][0]) <= 1
+    assert dd.Conforming(prob).residual(got)[0] <= 1e-10
+    # the GPU's own FP64 yardstick agrees with the oracle's
+    assert abs(s.primal_residual(s.rhs_planewave(w.thetas), u)[0] - dd.Conforming(prob).residual(got)[0]) < 1e-12
+    s.close()
+
+
+def test_host_buffers_and_adjoint():
+    w = SMALL["hanging_corner"]()
+    s = _solver(w, tol=1e-12)
+    b = s.rhs_planewave(w.thetas)
+    u, _ = s.solve(b, tol=1e-12)
+    uh, _ = s.solve_host(b.cpu().numpy(), tol=1e-12)
+    assert np.allclose(uh, u.cpu().numpy(), atol=1e-13 * np.abs(uh).max())
+    # adjoint: A^H lam = g  <=>  lam = conj(A^-1 conj(g))
+    lam, _ = s.adjoint_solve(b, tol=1e-12)
+    u2, _ = s.solve(torch.conj(b).resolve_conj().contiguous(), tol=1e-12)
+    assert np.allclose(lam.cpu().numpy(), np.conj(u2.cpu().numpy()), atol=1e-12 * np.abs(uh).max())
+    s.close()
+
+
+def test_errors_are_reported():
+    s = ddh.DDH(0)
+    with pytest.raises(ddh.DDHError):
+        s.set_mesh(2, np.array([[0, 0, 0], [0, 1, 0]]), np.array([8, 8]))     # does not tile
+    with pytest.raises(ddh.DDHError):
+        s.factor()                                                          # before mesh
+    w = W.plane_2x2()
+    s.set_mesh(w.base_n, w.leaves, w.p)
+    with pytest.raises(ddh.DDHError):
+        s.set_coefficients(-1.0, w.eps)
+    s.set_coefficients(w.k, w.eps)
+    s.factor(maxit=2, tol=1e-14)
+    with pytest.raises(ddh.DDHError) as ei:
+        s.solve(s.rhs_planewave(w.thetas), tol=1e-14)
+    assert ei.value.status == ddh.ERR_NO_CONVERGENCE
+    s.close()
