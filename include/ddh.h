@@ -72,6 +72,9 @@ typedef struct {
                               application (default 12) */
     int32_t check_every;   /* host polls convergence every this many iterations (default 4) */
     int32_t use_graph;     /* 1: replay one FGMRES iteration as a CUDA graph (default 1) */
+    int32_t coarse_fp32;   /* mixed precision only: 1 = apply a complex64 copy of the coarse
+                              factor inside the inner (preconditioner) solves; 0 (default) keeps
+                              the coarse solve FP64 everywhere */
 } ddh_options;
 
 typedef struct {
@@ -188,6 +191,16 @@ ddh_status ddh_table_affine(int32_t n, double a, double b, double* out);
 ddh_status ddh_table_fdm(int32_t p, double* V_out, double* mu_out);
 /* Gauss-Legendre nodes/weights by the Golub-Welsch method (own eigensolver). */
 ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);
+
+/* Host-only setup and factorisation (no device work) of a mesh, for checks of the host
+ * logic without a GPU.  sizes_out[8]: n_local, n_dual, n_coarse, n_conforming, type-1 edge
+ * slots, type-2 slots, coarse blocks, largest block (0 blocks when the coarse inverse is
+ * dense); seconds_out[5]: classification and factorisation wall time, the relative residual
+ * ||K x - t||/||t|| of one coarse solve with a seeded random t, max_e ||S_E S_E^-1 - I||_max, and
+ * the minimum relative resonance gap of the interior blocks; l_out: l in use. */
+ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem,
+                           double k, const double* eps_r, int32_t l_override, int64_t* sizes_out,
+                           double* seconds_out, int32_t* l_out);
 
 #ifdef __cplusplus
 }

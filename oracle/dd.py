@@ -303,8 +303,11 @@ class DDSolver:
 # ------------------------------------------------------------------ conforming yardstick
 
 class Conforming:
-    """The globally assembled basis (all constraints primal) for the primal residual
-    ||Z_c^T (b - A phi)|| / ||Z_c^T b|| on the interpolatory basis."""
+    """The globally assembled basis (all constraints primal).  Primal residual yardstick:
+    phi is projected onto the conforming space (u_c = argmin ||Z_c u - phi||, least squares),
+    then r = ||Z_c^T (b - A Z_c u_c)|| / ||Z_c^T b|| on the interpolatory basis.  (For an
+    iterate of the dual method Z_c^T (b - A phi) vanishes identically, whatever the dual
+    variable, so phi itself cannot be used.)"""
 
     def __init__(self, prob: Problem):
         self.prob = prob
@@ -317,7 +320,10 @@ class Conforming:
         b = prob.b_N if b_N is None else b_N
         bt = to_tilde_vec(prob, np.atleast_2d(b))
         pt = to_tilde_vec(prob, np.atleast_2d(phi_N))
-        r = (bt - (self.A @ pt.T).T) @ self.Zc
+        ZtZ = (self.Zc.T @ self.Zc).astype(complex).tocsc()
+        uc = spla.splu(ZtZ).solve((pt @ self.Zc).T)
+        pc = (self.Zc @ uc).T
+        r = (bt - (self.A @ pc.T).T) @ self.Zc
         bc = bt @ self.Zc
         return np.linalg.norm(r, axis=1) / np.linalg.norm(bc, axis=1)
 

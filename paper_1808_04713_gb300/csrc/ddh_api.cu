@@ -6,6 +6,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <thread>
@@ -30,6 +31,23 @@ struct GraphKey {
     bool operator<(const GraphKey& o) const { return R != o.R ? R < o.R : prec < o.prec; }
 };
 
+// one FGMRES instance: device state, pinned polling buffers, captured iteration graphs
+struct KState {
+    KrylovDev K{};
+    int R = 0, m = 0, nd = 0;
+    std::vector<void*> allocs;
+    double2* r = nullptr;
+    double* nrm2 = nullptr;
+    double2* ydev = nullptr;
+    int* nitdev = nullptr;
+    int* h_ctl = nullptr;       // pinned: ctl[0..3], rdone[R], iters[R]
+    double* h_resid = nullptr;  // pinned: resid[R]
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, int64_t> graph_kernels;
+    double graph_tol = -1;
+    void release();
+};
+
 }  // namespace
 
 struct ddh_ctx {
@@ -48,7 +66,17 @@ struct ddh_ctx {
     void* sinv64 = nullptr;
     void* sinv32 = nullptr;
     double2* Kinv = nullptr;                       // dense coarse inverse (new order)
+    float2* Kinv32 = nullptr;
     std::vector<double2*> bt_Dinv, bt_Lo, bt_Up;   // block-tridiagonal factors
+    std::vector<float2*> bt_Dinv32, bt_Lo32, bt_Up32;
+    bool coarse32 = false;                         // current inner solves use the complex64 copy
+    bool refine_coarse = false;                    // one FP64 refinement step per coarse solve
+    bool refine_active = false;                    // refinement used by the current solves
+    const double2* const* Kd_dev = nullptr;        // device arrays of block pointers
+    const double2* const* Kl_dev = nullptr;
+    const double2* const* Ku_dev = nullptr;
+    const int* blk_start_dev = nullptr;
+    const int* row_blk_dev = nullptr;
     std::vector<int> blk_start, blk_size;
     // gauss rule for loads
     double* gx = nullptr;
@@ -56,15 +84,9 @@ struct ddh_ctx {
     int nq = 0;
     // work buffers (grow on demand)
     std::map<std::string, Buf> work;
-    // krylov
-    KrylovDev K{};
-    int K_R = 0, K_m = 0;
-    std::vector<void*> K_allocs;
-    int* h_ctl = nullptr;                          // pinned: ctl[2], rdone[R], iters[R]; resid via pinned double
-    double* h_resid = nullptr;
-    std::map<GraphKey, cudaGraphExec_t> graphs;
-    std::map<GraphKey, int64_t> graph_kernels;
-    double graph_tol = -1;
+    // Krylov solvers: dual interface problem (plain solve / inner preconditioner) and the
+    // FP64 outer refinement on the conforming primal system (mixed precision)
+    KState kin, kout;
 };
 
 #define CK(call)                                                                 \
@@ -96,17 +118,17 @@ static void free_model(ddh_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (void* p : ctx->model_allocs) cudaFree(p);
     ctx->model_allocs.clear();
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
-    ctx->graph_kernels.clear();
-    for (void* p : ctx->K_allocs) cudaFree(p);
-    ctx->K_allocs.clear();
-    ctx->K_R = 0;
+    ctx->kin.release();
+    ctx->kout.release();
     for (auto& kv : ctx->work) cudaFree(kv.second.p);
     ctx->work.clear();
     ctx->sinv64 = ctx->sinv32 = nullptr;
     ctx->Kinv = nullptr;
+    ctx->Kinv32 = nullptr;
+    ctx->refine_coarse = false;
+    ctx->Kd_dev = ctx->Kl_dev = ctx->Ku_dev = nullptr;
     ctx->bt_Dinv.clear(); ctx->bt_Lo.clear(); ctx->bt_Up.clear();
+    ctx->bt_Dinv32.clear(); ctx->bt_Lo32.clear(); ctx->bt_Up32.clear();
     ctx->gx = ctx->gw = nullptr;
 }
 
@@ -115,8 +137,10 @@ static ddh_status get_work(ddh_ctx* ctx, const std::string& name, size_t bytes, 
     if (b.bytes < bytes) {
         if (b.p) { cudaStreamSynchronize(ctx->stream); cudaFree(b.p); b.p = nullptr; }
         // graphs capture buffer addresses; invalidate them when a buffer moves
-        for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
+        for (KState* ks : {&ctx->kin, &ctx->kout}) {
+            for (auto& kv : ks->graphs) cudaGraphExecDestroy(kv.second);
+            ks->graphs.clear();
+        }
         if (cudaMalloc(&b.p, bytes) != cudaSuccess) { b.bytes = 0; ctx->err = "cudaMalloc failed (" + name + ")"; return DDH_ERR_OOM; }
         b.bytes = bytes;
     }
@@ -263,6 +287,18 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, cnt, &d.cf_ptr))) return st;
         if ((st = upload(ctx, loc, &d.cf_loc))) return st;
         if ((st = upload(ctx, w, &d.cf_w))) return st;
+        // by local slot (scatter), and one master slot per dof: a slot whose expression is
+        // exactly that dof with weight 1 (vertex, master-edge bubble or interior copy)
+        if ((st = upload(ctx, m.cf_ptr, &d.cfl_ptr))) return st;
+        if ((st = upload(ctx, m.cf_col, &d.cfl_col))) return st;
+        if ((st = upload(ctx, m.cf_w, &d.cfl_w))) return st;
+        std::vector<int64_t> master(nq, -1);
+        for (int64_t sl = 0; sl < m.n_local; ++sl)
+            if (m.cf_ptr[sl + 1] - m.cf_ptr[sl] == 1 && m.cf_w[m.cf_ptr[sl]] == 1.0 && master[m.cf_col[m.cf_ptr[sl]]] < 0)
+                master[m.cf_col[m.cf_ptr[sl]]] = sl;
+        for (int q = 0; q < nq; ++q)
+            if (master[q] < 0) { ctx->err = "conforming dof without a master slot"; return DDH_ERR_INVALID_ARG; }
+        if ((st = upload(ctx, master, &d.master))) return st;
     }
     // Sinv (FP64 and FP32 copies)
     {
@@ -292,21 +328,73 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         const double2* a;
         if ((st = upload(ctx, Kn, &a))) return st;
         ctx->Kinv = (double2*)a;
+        std::vector<float2> K32(Kn.size());
+        for (size_t i = 0; i < Kn.size(); ++i) K32[i] = make_float2((float)Kn[i].x, (float)Kn[i].y);
+        const float2* a32;
+        if ((st = upload(ctx, K32, &a32))) return st;
+        ctx->Kinv32 = (float2*)a32;
     } else {
         auto conv = [](const std::vector<cd>& v) {
             std::vector<double2> o(v.size());
             for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
             return o;
         };
+        auto conv32 = [](const std::vector<cd>& v) {
+            std::vector<float2> o(v.size());
+            for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+            return o;
+        };
         for (int b = 0; b < m.nb; ++b) {
             const double2* a;
+            const float2* a32;
             if ((st = upload(ctx, conv(m.Dinv[b]), &a))) return st;
             ctx->bt_Dinv.push_back((double2*)a);
             if ((st = upload(ctx, conv(m.Lo[b]), &a))) return st;
             ctx->bt_Lo.push_back((double2*)a);
             if ((st = upload(ctx, conv(m.Up[b]), &a))) return st;
             ctx->bt_Up.push_back((double2*)a);
+            if (ctx->opt.precision == DDH_PREC_MIXED_FP32 && ctx->opt.coarse_fp32) {
+                if ((st = upload(ctx, conv32(m.Dinv[b]), &a32))) return st;
+                ctx->bt_Dinv32.push_back((float2*)a32);
+                if ((st = upload(ctx, conv32(m.Lo[b]), &a32))) return st;
+                ctx->bt_Lo32.push_back((float2*)a32);
+                if ((st = upload(ctx, conv32(m.Up[b]), &a32))) return st;
+                ctx->bt_Up32.push_back((float2*)a32);
+            }
         }
+    }
+    // assembled blocks for the refinement step of an unstable block factorisation
+    ctx->refine_coarse = !m.dense_coarse && m.coarse_refine;
+    if (ctx->refine_coarse) {
+        auto conv = [](const std::vector<cd>& v) {
+            std::vector<double2> o(std::max<size_t>(1, v.size()));
+            for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+            return o;
+        };
+        std::vector<const double2*> pd(m.nb), pl(m.nb), pu(m.nb);
+        for (int b = 0; b < m.nb; ++b) {
+            const double2* a;
+            if ((st = upload(ctx, conv(m.Kd[b]), &a))) return st;
+            pd[b] = a;
+            if (b > 0) { if ((st = upload(ctx, conv(m.Kl[b]), &a))) return st; pl[b] = a; } else pl[b] = nullptr;
+            pu[b] = ctx->bt_Up[b];
+        }
+        const double2* const* q;
+        if ((st = upload(ctx, pd, (const double2* const**)&q))) return st;
+        ctx->Kd_dev = q;
+        if ((st = upload(ctx, pl, (const double2* const**)&q))) return st;
+        ctx->Kl_dev = q;
+        if ((st = upload(ctx, pu, (const double2* const**)&q))) return st;
+        ctx->Ku_dev = q;
+        std::vector<int> rb(nc);
+        for (int b = 0; b < m.nb; ++b)
+            for (int i = m.blk_start[b]; i < m.blk_start[b + 1]; ++i) rb[i] = b;
+        const int* qi;
+        if ((st = upload(ctx, m.blk_start, &qi))) return st;
+        ctx->blk_start_dev = qi;
+        if ((st = upload(ctx, rb, &qi))) return st;
+        ctx->row_blk_dev = qi;
+        m.Kd.clear(); m.Kl.clear();
     }
     // Gauss rule for the boundary loads
     {
@@ -345,7 +433,7 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     w.t = (double2*)p;
     if ((st = get_work(ctx, "x2", sizeof(double2) * (size_t)R * d.n_coarse, &p))) return st;
     w.x2 = (double2*)p;
-    if ((st = get_work(ctx, "ctmp", sizeof(double2) * (size_t)R * d.n_coarse, &p))) return st;
+    if ((st = get_work(ctx, "ctmp", sizeof(double2) * (size_t)4 * R * d.n_coarse, &p))) return st;
     w.ctmp = (double2*)p;
     if ((st = get_work(ctx, "vd", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.vd = (double2*)p;
@@ -354,27 +442,52 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     return DDH_OK;
 }
 
-// x2 = K^-1 t (FP64), t is overwritten in block-tridiagonal mode
+// x2 = K^-1 t (vectors FP64), t is overwritten in block-tridiagonal mode.  The factor is
+// complex128, or its complex64 copy while ctx->coarse32 is set (mixed-precision inner solves).
+static void coarse_solve_once(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done);
+
 static void coarse_solve(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done) {
+    if (!(ctx->refine_active && ctx->refine_coarse && !ctx->coarse32)) { coarse_solve_once(ctx, t, x2, tmp, R, done); return; }
+    // x = BT(t); r = t - K x; x += BT(r)   (t is overwritten by the block sweep: keep a copy)
     const int nc = ctx->dm.n_coarse;
     cudaStream_t s = ctx->stream;
+    double2* t0 = tmp + (size_t)R * nc;
+    double2* r = tmp + (size_t)2 * R * nc;
+    double2* dx = tmp + (size_t)3 * R * nc;
+    cudaMemcpyAsync(t0, t, sizeof(double2) * (size_t)R * nc, cudaMemcpyDeviceToDevice, s);
+    coarse_solve_once(ctx, t, x2, tmp, R, done);
+    launch_coarse_residual(ctx->Kd_dev, ctx->Kl_dev, ctx->Ku_dev, ctx->blk_start_dev, ctx->row_blk_dev,
+                           (int)ctx->blk_size.size(), nc, x2, t0, r, R, done, s);
+    coarse_solve_once(ctx, r, dx, tmp, R, done);
+    launch_axpby(x2, 1.0, dx, 1.0, x2, (int64_t)R * nc, s);
+    ctx->launches += 2;
+}
+
+static void coarse_solve_once(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done) {
+    const int nc = ctx->dm.n_coarse;
+    cudaStream_t s = ctx->stream;
+    const bool f32 = ctx->coarse32;
     if (ctx->Kinv) {
-        launch_gemv(ctx->Kinv, nc, nc, t, x2, nullptr, 0, nc, nc, R, done, s);
+        launch_gemv(f32 ? (const void*)ctx->Kinv32 : (const void*)ctx->Kinv, f32, nc, nc, t, x2, nullptr, 0, nc, nc, R,
+                    done, s);
         ctx->launches++;
         return;
     }
     const int nb = (int)ctx->blk_size.size();
     const auto& bs = ctx->blk_start;
     const auto& sz = ctx->blk_size;
+    auto D = [&](int b) { return f32 ? (const void*)ctx->bt_Dinv32[b] : (const void*)ctx->bt_Dinv[b]; };
+    auto L = [&](int b) { return f32 ? (const void*)ctx->bt_Lo32[b] : (const void*)ctx->bt_Lo[b]; };
+    auto U = [&](int b) { return f32 ? (const void*)ctx->bt_Up32[b] : (const void*)ctx->bt_Up[b]; };
     for (int b = 1; b < nb; ++b) {
-        launch_gemv(ctx->bt_Lo[b], sz[b], sz[b - 1], t + bs[b - 1], t + bs[b], nullptr, 1, nc, nc, R, done, s);
+        launch_gemv(L(b), f32, sz[b], sz[b - 1], t + bs[b - 1], t + bs[b], nullptr, 1, nc, nc, R, done, s);
         ctx->launches++;
     }
-    launch_gemv(ctx->bt_Dinv[nb - 1], sz[nb - 1], sz[nb - 1], t + bs[nb - 1], x2 + bs[nb - 1], nullptr, 0, nc, nc, R, done, s);
+    launch_gemv(D(nb - 1), f32, sz[nb - 1], sz[nb - 1], t + bs[nb - 1], x2 + bs[nb - 1], nullptr, 0, nc, nc, R, done, s);
     ctx->launches++;
     for (int b = nb - 2; b >= 0; --b) {
-        launch_gemv(ctx->bt_Up[b], sz[b], sz[b + 1], x2 + bs[b + 1], tmp + bs[b], t + bs[b], 2, nc, nc, R, done, s);
-        launch_gemv(ctx->bt_Dinv[b], sz[b], sz[b], tmp + bs[b], x2 + bs[b], nullptr, 0, nc, nc, R, done, s);
+        launch_gemv(U(b), f32, sz[b], sz[b + 1], x2 + bs[b + 1], tmp + bs[b], t + bs[b], 2, nc, nc, R, done, s);
+        launch_gemv(D(b), f32, sz[b], sz[b], tmp + bs[b], x2 + bs[b], nullptr, 0, nc, nc, R, done, s);
         ctx->launches += 2;
     }
 }
@@ -417,21 +530,31 @@ static void apply_prec(ddh_ctx* ctx, const Work& w, const double2* v, double2* z
 }
 
 // ---------------------------------------------------------------- Krylov state
-static ddh_status ensure_krylov(ddh_ctx* ctx, int R, int m) {
-    if (ctx->K_R == R && ctx->K_m == m) return DDH_OK;
+void KState::release() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    graph_kernels.clear();
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_resid) cudaFreeHost(h_resid);
+    h_ctl = nullptr;
+    h_resid = nullptr;
+    R = m = nd = 0;
+}
+
+static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) {
+    nd = std::max(1, nd);
+    if (ks.R == R && ks.m == m && ks.nd == nd) return DDH_OK;
     cudaStreamSynchronize(ctx->stream);
-    for (void* p : ctx->K_allocs) cudaFree(p);
-    ctx->K_allocs.clear();
-    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-    ctx->graphs.clear();
-    const int nd = std::max(1, ctx->dm.n_dual);
-    KrylovDev& K = ctx->K;
+    ks.release();
+    KrylovDev& K = ks.K;
     K.nd = nd; K.m = m; K.R = R;
-    K.nchunk = std::max(1, std::min(64, (nd + 1023) / 1024));
+    K.nchunk = std::max(1, std::min(296, (nd + 63) / 64));
     auto al = [&](size_t bytes, void** p) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
         cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), ctx->stream);
-        ctx->K_allocs.push_back(*p);
+        ks.allocs.push_back(*p);
         return true;
     };
     void* p;
@@ -452,53 +575,68 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, int R, int m) {
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.w = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.vin = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.zw = (double2*)p;
+    ok &= al(sizeof(double2) * (size_t)R * nd, &p); ks.r = (double2*)p;
+    ok &= al(sizeof(double) * (size_t)R, &p); ks.nrm2 = (double*)p;
+    ok &= al(sizeof(double2) * (size_t)R * m, &p); ks.ydev = (double2*)p;
+    ok &= al(sizeof(int) * (size_t)R, &p); ks.nitdev = (int*)p;
     if (!ok) { ctx->err = "cudaMalloc failed (Krylov state)"; return DDH_ERR_OOM; }
-    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
-    if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
-    CK(cudaMallocHost((void**)&ctx->h_ctl, sizeof(int) * (4 + 2 * (size_t)R)));
-    CK(cudaMallocHost((void**)&ctx->h_resid, sizeof(double) * (size_t)R));
-    ctx->K_R = R;
-    ctx->K_m = m;
+    CK(cudaMallocHost((void**)&ks.h_ctl, sizeof(int) * (4 + 2 * (size_t)R)));
+    CK(cudaMallocHost((void**)&ks.h_resid, sizeof(double) * (size_t)R));
+    ks.R = R; ks.m = m; ks.nd = nd;
     return DDH_OK;
 }
 
-// one FGMRES iteration: fetch V[j], precondition, store Zb[j], w = F Zb[j], CGS2 + Givens
-template <class T>
-static void iteration_body(ddh_ctx* ctx, const Work& w) {
-    KrylovDev& K = ctx->K;
+// Operator and preconditioner callbacks of one FGMRES instance: out = op(in), out = prec(in).
+// `done` is the device stop flag the kernels check (graph replays past convergence are no-ops).
+struct KrylovOps {
+    std::function<void(const double2*, double2*, const int*)> op;
+    std::function<ddh_status(const double2*, double2*, const int*)> prec;
+    bool graph = false;     // the body may be captured as a CUDA graph
+    int key = 0;            // graph cache key (precision of the element kernels)
+};
+
+// one FGMRES iteration: fetch V[j], precondition, store Zb[j], w = A Zb[j], CGS2 + Givens
+static ddh_status iteration_body(ddh_ctx* ctx, KState& ks, const KrylovOps& ops) {
+    KrylovDev& K = ks.K;
     const int* done = K.ctl + 1;
     launch_fetch(K, ctx->stream);
-    apply_prec<T>(ctx, w, K.vin, K.zw, K.R, done);
+    ddh_status st = ops.prec(K.vin, K.zw, done);
+    if (st) return st;
     launch_store(K, ctx->stream);
-    apply_op<T>(ctx, w, K.zw, 1.0, nullptr, 0, K.w, nullptr, K.R, done);
+    ops.op(K.zw, K.w, done);
     launch_krylov_iter_tail(K, ctx->stream);
-    ctx->launches += 2 + 11;
+    ctx->launches += 2 + 6;
+    return DDH_OK;
 }
 
-template <class T>
-static ddh_status run_iteration(ddh_ctx* ctx, const Work& w, int count) {
-    const GraphKey key{ctx->K.R, std::is_same<T, double>::value ? 0 : 1};
-    if (ctx->opt.use_graph) {
-        auto it = ctx->graphs.find(key);
-        if (it == ctx->graphs.end()) {
+static ddh_status run_iteration(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, int count) {
+    const GraphKey key{ks.K.R, ops.key};
+    if (ops.graph && ctx->opt.use_graph) {
+        auto it = ks.graphs.find(key);
+        if (it == ks.graphs.end()) {
             const int64_t before = ctx->launches;
             cudaGraph_t g;
             CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            iteration_body<T>(ctx, w);
-            CK(cudaStreamEndCapture(ctx->stream, &g));
+            ddh_status st = iteration_body(ctx, ks, ops);
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+            if (st) return st;
+            if (ce != cudaSuccess) return fail(ctx, DDH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
             cudaGraphExec_t ge;
             CK(cudaGraphInstantiate(&ge, g, 0));
             cudaGraphDestroy(g);
-            ctx->graph_kernels[key] = ctx->launches - before;
+            ks.graph_kernels[key] = ctx->launches - before;
             ctx->launches = before;
-            it = ctx->graphs.emplace(key, ge).first;
+            it = ks.graphs.emplace(key, ge).first;
         }
         for (int i = 0; i < count; ++i) {
             CK(cudaGraphLaunch(it->second, ctx->stream));
-            ctx->launches += ctx->graph_kernels[key];
+            ctx->launches += ks.graph_kernels[key];
         }
     } else {
-        for (int i = 0; i < count; ++i) iteration_body<T>(ctx, w);
+        for (int i = 0; i < count; ++i) {
+            ddh_status st = iteration_body(ctx, ks, ops);
+            if (st) return st;
+        }
     }
     CK(cudaGetLastError());
     return DDH_OK;
@@ -514,38 +652,36 @@ static void host_upper_solve(int n, int m, const std::complex<double>* Hcols, co
     }
 }
 
-// FGMRES on F nu = g (dual), nu written to nu_out (zero initial guess).  Returns iterations.
-template <class T>
-static ddh_status fgmres_dual(ddh_ctx* ctx, const Work& w, const double2* gvec, double2* nu_out, int R, double tol,
-                              int maxit, std::vector<int>& its, std::vector<double>& res) {
-    const int nd = ctx->dm.n_dual;
+// Restarted right-preconditioned FGMRES (CGS2, zero initial guess) on A x = b for R
+// independent right-hand sides of length nd.  Stops per RHS at ||b - A x|| <= tol ||b||
+// (Givens estimate) or after maxit iterations; x_out receives the iterates.
+static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, const double2* bvec, double2* x_out,
+                             int nd, int R, int m, double tol, int maxit, int check_every,
+                             std::vector<int>& its, std::vector<double>& res, bool warm = false) {
     its.assign(R, 0);
     res.assign(R, 0.0);
-    CK(cudaMemsetAsync(nu_out, 0, sizeof(double2) * (size_t)R * nd, ctx->stream));
+    if (!warm) CK(cudaMemsetAsync(x_out, 0, sizeof(double2) * (size_t)R * std::max(1, nd), ctx->stream));
     if (nd == 0) return DDH_OK;
-    const int m = std::min(std::max(2, ctx->opt.restart), 200);
     ddh_status st;
-    if ((st = ensure_krylov(ctx, R, m))) return st;
-    KrylovDev& K = ctx->K;
+    if ((st = ensure_krylov(ctx, ks, nd, R, m))) return st;
+    KrylovDev& K = ks.K;
     K.tol = tol;
-    // graphs captured for another tolerance must be rebuilt (tol is a kernel parameter)
-    if (ctx->graph_tol != tol) {
-        for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
-        ctx->graphs.clear();
-        ctx->graph_tol = tol;
+    if (ks.graph_tol != tol) {            // tol is a kernel parameter of the captured graph
+        for (auto& kv : ks.graphs) cudaGraphExecDestroy(kv.second);
+        ks.graphs.clear();
+        ks.graph_tol = tol;
     }
-    double* nrm2;
-    void* p;
-    if ((st = get_work(ctx, "nrm2", sizeof(double) * R, &p))) return st;
-    nrm2 = (double*)p;
-    void* rbuf;
-    if ((st = get_work(ctx, "kres", sizeof(double2) * (size_t)R * nd, &rbuf))) return st;
-    double2* r = (double2*)rbuf;
-    CK(cudaMemcpyAsync(r, gvec, sizeof(double2) * (size_t)R * nd, cudaMemcpyDeviceToDevice, ctx->stream));
+    double2* r = ks.r;
     std::vector<double> h_b(R), h_n(R);
-    CK(cudaMemsetAsync(nrm2, 0, sizeof(double) * R, ctx->stream));
-    launch_norm2(r, nd, nrm2, R, ctx->stream);
-    CK(cudaMemcpyAsync(h_b.data(), nrm2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemsetAsync(ks.nrm2, 0, sizeof(double) * R, ctx->stream));
+    launch_norm2(bvec, nd, ks.nrm2, R, ctx->stream);
+    if (warm) {
+        ops.op(x_out, K.w, nullptr);
+        launch_axpby(bvec, 1.0, K.w, -1.0, r, (int64_t)R * nd, ctx->stream);
+    } else {
+        CK(cudaMemcpyAsync(r, bvec, sizeof(double2) * (size_t)R * nd, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(h_b.data(), ks.nrm2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     for (auto& v : h_b) v = std::sqrt(v);
     CK(cudaMemcpyAsync(K.bnorm, h_b.data(), sizeof(double) * R, cudaMemcpyHostToDevice, ctx->stream));
@@ -555,10 +691,10 @@ static ddh_status fgmres_dual(ddh_ctx* ctx, const Work& w, const double2* gvec, 
     std::vector<std::complex<double>> Hh((size_t)R * m * (m + 1)), gh((size_t)R * (m + 1)), y((size_t)R * m);
     std::vector<int> nit(R);
     while (true) {
-        // restart: V0 = r / ||r||, g = (||r||, 0, ...)
-        CK(cudaMemsetAsync(nrm2, 0, sizeof(double) * R, ctx->stream));
-        launch_norm2(r, nd, nrm2, R, ctx->stream);
-        CK(cudaMemcpyAsync(h_n.data(), nrm2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+        // (re)start: V0 = r / ||r||, g = (||r||, 0, ...)
+        CK(cudaMemsetAsync(ks.nrm2, 0, sizeof(double) * R, ctx->stream));
+        launch_norm2(r, nd, ks.nrm2, R, ctx->stream);
+        CK(cudaMemcpyAsync(h_n.data(), ks.nrm2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         std::vector<double2> g0((size_t)R * (m + 1), make_double2(0, 0));
         std::vector<int> rd(R);
@@ -579,44 +715,110 @@ static ddh_status fgmres_dual(ddh_ctx* ctx, const Work& w, const double2* gvec, 
         int j = 0;
         bool stop = false;
         while (!stop) {
-            const int batch = std::max(1, std::min(ctx->opt.check_every, m - j));
-            if ((st = run_iteration<T>(ctx, w, batch))) return st;
-            CK(cudaMemcpyAsync(ctx->h_ctl, K.ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->h_ctl + 4, K.rdone, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->h_ctl + 4 + R, K.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaMemcpyAsync(ctx->h_resid, K.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
+            const int batch = std::max(1, std::min({check_every, m - j, maxit - total - j}));
+            if ((st = run_iteration(ctx, ks, ops, batch))) return st;
+            CK(cudaMemcpyAsync(ks.h_ctl, K.ctl, sizeof(int) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(ks.h_ctl + 4, K.rdone, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(ks.h_ctl + 4 + R, K.iters, sizeof(int) * R, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(ks.h_resid, K.resid, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
-            j = ctx->h_ctl[0];
-            stop = ctx->h_ctl[1] != 0 || total + j >= maxit;
+            j = ks.h_ctl[0];
+            stop = ks.h_ctl[1] != 0 || total + j >= maxit;
         }
-        // solve the small least-squares systems and update nu for RHS active in this cycle
+        // small least-squares solves and x update for the RHS active in this cycle
         CK(cudaMemcpyAsync(Hh.data(), K.H, sizeof(double2) * Hh.size(), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(gh.data(), K.g, sizeof(double2) * gh.size(), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         bool alldone = true;
         for (int i = 0; i < R; ++i) {
-            nit[i] = active[i] ? ctx->h_ctl[4 + R + i] : 0;
+            nit[i] = active[i] ? ks.h_ctl[4 + R + i] : 0;
             if (nit[i] > 0)
                 host_upper_solve(nit[i], m, &Hh[(size_t)i * m * (m + 1)], &gh[(size_t)i * (m + 1)], &y[(size_t)i * m]);
             if (active[i]) {
                 its[i] += nit[i];
-                res[i] = ctx->h_resid[i];
-                if (ctx->h_ctl[4 + i]) active[i] = 0;
+                res[i] = ks.h_resid[i];
+                if (ks.h_ctl[4 + i]) active[i] = 0;
             }
             alldone &= !active[i];
         }
-        void* yd;
-        void* nitd;
-        if ((st = get_work(ctx, "ydev", sizeof(double2) * (size_t)R * m, &yd))) return st;
-        if ((st = get_work(ctx, "nitdev", sizeof(int) * (size_t)R, &nitd))) return st;
-        CK(cudaMemcpyAsync(yd, y.data(), sizeof(double2) * (size_t)R * m, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(nitd, nit.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
-        launch_update(K.Zb, (const double2*)yd, (const int*)nitd, nu_out, nd, m, R, ctx->stream);
+        CK(cudaMemcpyAsync(ks.ydev, y.data(), sizeof(double2) * (size_t)R * m, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ks.nitdev, nit.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
+        launch_update(K.Zb, ks.ydev, ks.nitdev, x_out, nd, m, R, ctx->stream);
         total += j;
         if (alldone || total >= maxit) break;
-        // true residual r = g - F nu for the next cycle
-        apply_op<T>(ctx, w, nu_out, 1.0, nullptr, 0, K.w, nullptr, R, nullptr);
-        launch_axpby(gvec, 1.0, K.w, -1.0, r, (int64_t)R * nd, ctx->stream);
+        // true residual r = b - A x for the next cycle
+        ops.op(x_out, K.w, nullptr);
+        launch_axpby(bvec, 1.0, K.w, -1.0, r, (int64_t)R * nd, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    return DDH_OK;
+}
+
+template <class T>
+static KrylovOps dual_ops(ddh_ctx* ctx, const Work& w) {
+    KrylovOps o;
+    o.op = [ctx, w](const double2* in, double2* out, const int* done) {
+        apply_op<T>(ctx, w, in, 1.0, nullptr, 0, out, nullptr, ctx->kin.K.R, done);
+    };
+    o.prec = [ctx, w](const double2* in, double2* out, const int* done) -> ddh_status {
+        apply_prec<T>(ctx, w, in, out, ctx->kin.K.R, done);
+        return DDH_OK;
+    };
+    o.graph = true;
+    o.key = (std::is_same<T, double>::value ? 0 : 1) + (ctx->coarse32 ? 2 : 0) + (ctx->refine_active ? 4 : 0);
+    return o;
+}
+
+// One dual-primal solve of A phi = b (element-local tilde vectors): RHS pass, FGMRES on the
+// dual interface problem, recovery.  Element-level kernels in precision T.  With
+// primal_tol > 0 the dual iteration continues (warm restarts with a tighter dual tolerance)
+// until the FP64 primal residual ||Z_c^T (b - A phi)|| / ||Z_c^T b|| <= primal_tol.
+static ddh_status primal_residual_dev(ddh_ctx* ctx, const double2* bt, const double2* phit, int R, std::vector<double>& out);
+
+template <class T>
+static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit, int R, double tol, int maxit,
+                                 int restart, int check_every, std::vector<int>& its, std::vector<double>& res,
+                                 double primal_tol = 0.0, std::vector<double>* primal = nullptr) {
+    const DevModel& d = ctx->dm;
+    Work w;
+    ddh_status st;
+    if ((st = get_op_work(ctx, R, std::is_same<T, double>::value, w))) return st;
+    void *g, *nu;
+    const char* gname = std::is_same<T, double>::value ? "gdual64" : "gdual32";
+    const char* nname = std::is_same<T, double>::value ? "nu64" : "nu32";
+    if ((st = get_work(ctx, gname, sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &g))) return st;
+    if ((st = get_work(ctx, nname, sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &nu))) return st;
+    // g = C^ A^-1 b^
+    apply_op<T>(ctx, w, nullptr, 0.0, bt, 1, (double2*)g, nullptr, R, nullptr);
+    if ((st = ensure_krylov(ctx, ctx->kin, d.n_dual, R, restart))) return st;
+    KrylovOps ops = dual_ops<T>(ctx, w);
+    double tol_d = tol;
+    double last_worst = 1e300;
+    std::vector<int> its_c;
+    std::vector<double> res_c;
+    its.assign(R, 0);
+    for (int round = 0; round < 6; ++round) {
+        int left = maxit;
+        for (int i = 0; i < R; ++i) left = std::min(left, maxit - its[i]);
+        if ((st = fgmres_run(ctx, ctx->kin, ops, (const double2*)g, (double2*)nu, d.n_dual, R, restart, tol_d,
+                             std::max(1, left), check_every, its_c, res_c, round > 0)))
+            return st;
+        for (int i = 0; i < R; ++i) its[i] += its_c[i];
+        res = res_c;
+        // recovery: A^ phi_p = b^ - C^T nu
+        apply_op<T>(ctx, w, (const double2*)nu, -1.0, bt, 1, nullptr, phit, R, nullptr);
+        if (primal_tol <= 0.0 || d.n_dual == 0) break;
+        std::vector<double> pr;
+        if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) return st;
+        if (primal) *primal = pr;
+        double worst = 0;
+        for (double v : pr) worst = std::max(worst, v);
+        int mx = 0;
+        for (int v : its) mx = std::max(mx, v);
+        if (worst <= primal_tol || mx >= maxit) break;
+        if (round > 0 && worst > 0.5 * last_worst) break;      // stagnation: report what was reached
+        last_worst = worst;
+        tol_d *= std::min(0.3, std::max(1e-4, 0.3 * primal_tol / worst));
     }
     CK(cudaGetLastError());
     return DDH_OK;
@@ -624,17 +826,24 @@ static ddh_status fgmres_dual(ddh_ctx* ctx, const Work& w, const double2* gvec, 
 
 // ---------------------------------------------------------------- ABI
 static ddh_status primal_residual_dev(ddh_ctx* ctx, const double2* bt, const double2* phit, int R, std::vector<double>& out) {
-    void *loc, *n1, *n2;
+    // yardstick: phi read back at the master slots (u_c), rebuilt conforming phi_c = Z_c u_c,
+    // r = ||Z_c^T (b - A phi_c)|| / ||Z_c^T b||  (FP64).  For a non-conforming iterate of the
+    // dual method Z_c^T (b - A phi) itself vanishes identically, so the projection is needed.
+    void *loc, *n1, *n2, *uc, *phc;
     ddh_status st;
     if ((st = get_work(ctx, "resloc", sizeof(double2) * (size_t)R * ctx->dm.n_local, &loc))) return st;
+    if ((st = get_work(ctx, "resphc", sizeof(double2) * (size_t)R * ctx->dm.n_local, &phc))) return st;
+    if ((st = get_work(ctx, "resuc", sizeof(double2) * (size_t)R * ctx->dm.n_conf, &uc))) return st;
     if ((st = get_work(ctx, "resn1", sizeof(double) * R, &n1))) return st;
     if ((st = get_work(ctx, "resn2", sizeof(double) * R, &n2))) return st;
-    launch_elem_matvec(ctx->dm, phit, bt, (double2*)loc, R, ctx->stream);
+    launch_readback(ctx->dm, phit, (double2*)uc, R, ctx->stream);
+    launch_conf_scatter(ctx->dm, (const double2*)uc, (double2*)phc, R, ctx->stream);
+    launch_elem_matvec(ctx->dm, (const double2*)phc, bt, (double2*)loc, R, ctx->stream);
     CK(cudaMemsetAsync(n1, 0, sizeof(double) * R, ctx->stream));
     CK(cudaMemsetAsync(n2, 0, sizeof(double) * R, ctx->stream));
     launch_conf_gather(ctx->dm, (const double2*)loc, (double*)n1, R, ctx->stream);
     launch_conf_gather(ctx->dm, bt, (double*)n2, R, ctx->stream);
-    ctx->launches += 3;
+    ctx->launches += 5;
     std::vector<double> a(R), b(R);
     CK(cudaMemcpyAsync(a.data(), n1, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(b.data(), n2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
@@ -644,43 +853,107 @@ static ddh_status primal_residual_dev(ddh_ctx* ctx, const double2* bt, const dou
     return DDH_OK;
 }
 
-template <class T>
+static ddh_status finish_stats(ddh_ctx* ctx, const double2* bt, const double2* phit, int R, const std::vector<int>& its,
+                               const std::vector<int>& inner, const std::vector<double>& res, ddh_rhs_stats* stats) {
+    if (!stats) { CK(cudaStreamSynchronize(ctx->stream)); return DDH_OK; }
+    std::vector<double> pr;
+    ddh_status st;
+    if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) return st;
+    for (int i = 0; i < R; ++i) {
+        stats[i].iterations = its[i];
+        stats[i].inner_iterations = inner.empty() ? 0 : inner[i];
+        stats[i].dual_residual = res[i];
+        stats[i].primal_residual = pr[i];
+    }
+    return DDH_OK;
+}
+
+// plain method: everything complex128
 static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev, int R, double tol, ddh_rhs_stats* stats) {
     const DevModel& d = ctx->dm;
-    Work w;
     ddh_status st;
-    if ((st = get_op_work(ctx, R, std::is_same<T, double>::value, w))) return st;
-    void *bt, *g, *nu, *phit;
+    void *bt, *phit;
     if ((st = get_work(ctx, "bt", sizeof(double2) * (size_t)R * d.n_local, &bt))) return st;
-    if ((st = get_work(ctx, "gdual", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &g))) return st;
-    if ((st = get_work(ctx, "nu", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &nu))) return st;
     if ((st = get_work(ctx, "phit", sizeof(double2) * (size_t)R * d.n_local, &phit))) return st;
     launch_basis(d, b_dev, (double2*)bt, 0, R, ctx->stream);
     ctx->launches++;
-    // g = C^ A^-1 b^
-    apply_op<T>(ctx, w, nullptr, 0.0, (const double2*)bt, 1, (double2*)g, nullptr, R, nullptr);
     std::vector<int> its;
     std::vector<double> res;
-    if ((st = fgmres_dual<T>(ctx, w, (const double2*)g, (double2*)nu, R, tol, ctx->opt.maxit, its, res))) return st;
-    // recovery: A^ phi_p = b^ - C^T nu
-    apply_op<T>(ctx, w, (const double2*)nu, -1.0, (const double2*)bt, 1, nullptr, (double2*)phit, R, nullptr);
+    std::vector<double> pr;
+    ctx->refine_active = true;
+    struct Off { ddh_ctx* c; ~Off() { c->refine_active = false; } } off_guard{ctx};
+    if ((st = dd_solve_tilde<double>(ctx, (const double2*)bt, (double2*)phit, R, tol, ctx->opt.maxit,
+                                     std::min(std::max(2, ctx->opt.restart), 200), ctx->opt.check_every, its, res,
+                                     tol, &pr)))
+        return st;
     launch_basis(d, (const double2*)phit, u_dev, 0, R, ctx->stream);
     ctx->launches++;
     CK(cudaGetLastError());
     bool conv = true;
-    for (int i = 0; i < R; ++i) conv &= (d.n_dual == 0) || res[i] <= tol;
-    if (stats) {
-        std::vector<double> pr;
-        if ((st = primal_residual_dev(ctx, (const double2*)bt, (const double2*)phit, R, pr))) return st;
-        for (int i = 0; i < R; ++i) {
-            stats[i].iterations = its[i];
-            stats[i].inner_iterations = 0;
-            stats[i].dual_residual = res[i];
-            stats[i].primal_residual = pr[i];
-        }
-    } else {
-        CK(cudaStreamSynchronize(ctx->stream));
-    }
+    for (int i = 0; i < R; ++i) conv &= (d.n_dual == 0) || (i < (int)pr.size() ? pr[i] <= tol : res[i] <= tol);
+    if ((st = finish_stats(ctx, (const double2*)bt, (const double2*)phit, R, its, {}, res, stats))) return st;
+    return conv ? DDH_OK : fail(ctx, DDH_ERR_NO_CONVERGENCE, "tolerance not reached within maxit");
+}
+
+// mixed precision: FP64 FGMRES on the conforming primal system A_c u = b_c (residuals,
+// Arnoldi, Hessenberg least squares in FP64); preconditioner = one dual-primal solve with
+// complex64 element kernels and a fixed number of dual FGMRES iterations (coarse solve FP64),
+// the residual injected at master slots and the result read back at the same slots.
+static ddh_status solve_mixed(ddh_ctx* ctx, const double2* b_dev, double2* u_dev, int R, double tol, ddh_rhs_stats* stats) {
+    const DevModel& d = ctx->dm;
+    ddh_status st;
+    void *bt, *phit, *bc, *uc, *mphi, *mloc, *bin, *phin;
+    const size_t lb = sizeof(double2) * (size_t)R * d.n_local, cb = sizeof(double2) * (size_t)R * d.n_conf;
+    if ((st = get_work(ctx, "bt", lb, &bt))) return st;
+    if ((st = get_work(ctx, "phit", lb, &phit))) return st;
+    if ((st = get_work(ctx, "mx_phi", lb, &mphi))) return st;
+    if ((st = get_work(ctx, "mx_loc", lb, &mloc))) return st;
+    if ((st = get_work(ctx, "mx_bin", lb, &bin))) return st;
+    if ((st = get_work(ctx, "mx_phin", lb, &phin))) return st;
+    if ((st = get_work(ctx, "mx_bc", cb, &bc))) return st;
+    if ((st = get_work(ctx, "mx_uc", cb, &uc))) return st;
+    cudaStream_t s = ctx->stream;
+    launch_basis(d, b_dev, (double2*)bt, 0, R, s);
+    launch_conf_gather_vec(d, (const double2*)bt, (double2*)bc, 1.0, R, s);
+    ctx->launches += 2;
+    const int m_in = std::max(1, std::min(ctx->opt.inner_iters, 200));
+    std::vector<int> inner(R, 0);
+    KrylovOps ops;
+    ops.op = [=](const double2* in, double2* out, const int*) {
+        launch_conf_scatter(d, in, (double2*)mphi, R, s);
+        launch_elem_matvec(d, (const double2*)mphi, nullptr, (double2*)mloc, R, s);     // -A phi
+        launch_conf_gather_vec(d, (const double2*)mloc, out, -1.0, R, s);
+        ctx->launches += 3;
+    };
+    ops.prec = [=, &inner](const double2* in, double2* out, const int*) -> ddh_status {
+        CK(cudaMemsetAsync(bin, 0, lb, s));
+        launch_inject(d, in, (double2*)bin, R, s);
+        std::vector<int> its_in;
+        std::vector<double> res_in;
+        ctx->coarse32 = ctx->opt.coarse_fp32 != 0;
+        ddh_status st2 = dd_solve_tilde<float>(ctx, (const double2*)bin, (double2*)phin, R, 0.0, m_in, m_in, m_in,
+                                               its_in, res_in);
+        ctx->coarse32 = false;
+        if (st2) return st2;
+        launch_readback(d, (const double2*)phin, out, R, s);
+        ctx->launches += 2;
+        for (int i = 0; i < R; ++i) inner[i] += its_in[i];
+        return DDH_OK;
+    };
+    ops.graph = false;
+    std::vector<int> its;
+    std::vector<double> res;
+    const int m_out = std::min(std::max(2, ctx->opt.restart), 40);
+    if ((st = fgmres_run(ctx, ctx->kout, ops, (const double2*)bc, (double2*)uc, d.n_conf, R, m_out, tol,
+                         ctx->opt.maxit, 1, its, res)))
+        return st;
+    launch_conf_scatter(d, (const double2*)uc, (double2*)phit, R, s);
+    launch_basis(d, (const double2*)phit, u_dev, 0, R, s);
+    ctx->launches += 2;
+    CK(cudaGetLastError());
+    bool conv = true;
+    for (int i = 0; i < R; ++i) conv &= res[i] <= tol;
+    if ((st = finish_stats(ctx, (const double2*)bt, (const double2*)phit, R, its, inner, res, stats))) return st;
     return conv ? DDH_OK : fail(ctx, DDH_ERR_NO_CONVERGENCE, "tolerance not reached within maxit");
 }
 
@@ -696,6 +969,7 @@ void ddh_default_options(ddh_options* o) {
     o->inner_iters = 12;
     o->check_every = 4;
     o->use_graph = 1;
+    o->coarse_fp32 = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -819,7 +1093,9 @@ ddh_status ddh_solve(ddh_ctx* ctx, const void* b_dev, void* u_dev, int32_t R, do
     if (((uintptr_t)b_dev | (uintptr_t)u_dev) & 15) return fail(ctx, DDH_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     if (tol <= 0) tol = ctx->opt.tol;
     cudaSetDevice(ctx->device);
-    return solve_plain<double>(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
+    if (ctx->opt.precision == DDH_PREC_MIXED_FP32)
+        return solve_mixed(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
+    return solve_plain(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
 }
 
 ddh_status ddh_solve_host(ddh_ctx* ctx, const void* b_host, void* u_host, int32_t R, double tol, ddh_rhs_stats* stats) {
@@ -894,13 +1170,13 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
 
 ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t reps, double* ms_out) {
     if (!ctx || !ms_out || R <= 0 || reps <= 0) return DDH_ERR_INVALID_ARG;
-    if (!ctx->factored || ctx->K_R != R) return fail(ctx, DDH_ERR_NOT_READY, "solve with the same R first");
+    if (!ctx->factored || ctx->kin.R != R) return fail(ctx, DDH_ERR_NOT_READY, "solve with the same R first");
     const bool fp64 = precision == DDH_PREC_FP64;
     Work w;
     ddh_status st;
     if ((st = get_op_work(ctx, R, fp64, w))) return st;
     const DevModel& d = ctx->dm;
-    KrylovDev& K = ctx->K;
+    KrylovDev& K = ctx->kin.K;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -946,10 +1222,36 @@ void ddh_destroy(ddh_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     free_model(ctx);
-    if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
-    if (ctx->h_resid) cudaFreeHost(ctx->h_resid);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem, double k,
+                           const double* eps, int32_t l_override, int64_t* sizes, double* secs, int32_t* l_out) {
+    if (!leaves || !p || !eps || !sizes || !secs || n_elem <= 0 || !(k > 0)) return DDH_ERR_INVALID_ARG;
+    Model m;
+    std::string err;
+    if (!build_model(m, base_n, leaves, p, n_elem, err)) return DDH_ERR_INVALID_ARG;
+    set_coefficients(m, k, eps);
+    const int l = l_override > 0 ? l_override : dispersion_l(m);
+    auto t0 = std::chrono::steady_clock::now();
+    if (!classify(m, l, err)) return DDH_ERR_INVALID_ARG;
+    auto t1 = std::chrono::steady_clock::now();
+    m.check_factor = true;
+    if (!factor(m, std::max(1u, std::thread::hardware_concurrency()), err)) return DDH_ERR_SINGULAR;
+    auto t2 = std::chrono::steady_clock::now();
+    int mx = 0;
+    for (int b : m.blk_size) mx = std::max(mx, b);
+    sizes[0] = m.n_local; sizes[1] = m.n_dual; sizes[2] = m.n_coarse; sizes[3] = m.n_conf;
+    sizes[4] = (int64_t)m.e1_slot.size(); sizes[5] = (int64_t)m.t_slot.size();
+    sizes[6] = m.dense_coarse ? 0 : m.nb; sizes[7] = mx;
+    secs[0] = std::chrono::duration<double>(t1 - t0).count();
+    secs[1] = std::chrono::duration<double>(t2 - t1).count();
+    secs[2] = m.coarse_check;
+    secs[3] = m.sinv_check;
+    secs[4] = m.min_gap;
+    if (l_out) *l_out = l;
+    return DDH_OK;
 }
 
 // ---- host-only tables

@@ -88,6 +88,11 @@ struct DevModel {
     const int* cf_ptr = nullptr;
     const int64_t* cf_loc = nullptr;
     const double* cf_w = nullptr;
+    // conforming numbering by local slot (scatter) and master slot per conforming dof
+    const int* cfl_ptr = nullptr;
+    const int* cfl_col = nullptr;
+    const double* cfl_w = nullptr;
+    const int64_t* master = nullptr;
 };
 
 }  // namespace ddh

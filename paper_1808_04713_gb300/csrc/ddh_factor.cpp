@@ -15,19 +15,77 @@
 #include <map>
 #include <set>
 #include <thread>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include "ddh_host.hpp"
 
 namespace ddh {
 
+// Persistent worker pool: parallel_for(n, f) runs f(0..n-1) on all workers and returns
+// when every index is done.  Used by the dense block kernels of the coarse factorisation.
+class Pool {
+  public:
+    explicit Pool(int n) : n_(std::max(1, n)) {
+        for (int t = 1; t < n_; ++t) th_.emplace_back([this, t] { worker(t); });
+    }
+    ~Pool() {
+        { std::lock_guard<std::mutex> g(mu_); stop_ = true; ++gen_; }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+    int size() const { return n_; }
+    template <class F>
+    void run(int n, F&& f) {
+        if (n <= 0) return;
+        if (n_ == 1 || n == 1) { for (int i = 0; i < n; ++i) f(i); return; }
+        std::function<void(int)> fn = f;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            job_ = &fn; njob_ = n; next_.store(0); pending_.store(n_ - 1);
+            ++gen_;
+        }
+        cv_.notify_all();
+        for (int i = next_++; i < n; i = next_++) fn(i);
+        std::unique_lock<std::mutex> lk(mu_);
+        done_cv_.wait(lk, [&] { return pending_.load() == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    void worker(int) {
+        uint64_t seen = 0;
+        while (true) {
+            std::function<void(int)>* fn;
+            int n;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+                if (stop_) return;
+                fn = job_; n = njob_;
+            }
+            for (int i = next_++; i < n; i = next_++) (*fn)(i);
+            { std::lock_guard<std::mutex> g(mu_); if (--pending_ == 0) done_cv_.notify_all(); }
+        }
+    }
+    int n_;
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    std::function<void(int)>* job_ = nullptr;
+    int njob_ = 0;
+    std::atomic<int> next_{0}, pending_{0};
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+
+static Pool* g_pool = nullptr;
+
 template <class F>
 static void parallel_for(int n, int nthreads, F&& f) {
-    nthreads = std::max(1, std::min(nthreads, n));
-    if (nthreads == 1) { for (int i = 0; i < n; ++i) f(i); return; }
-    std::atomic<int> next(0);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nthreads; ++t)
-        th.emplace_back([&]() { for (int i = next++; i < n; i = next++) f(i); });
-    for (auto& t : th) t.join();
+    if (g_pool && nthreads > 1) { g_pool->run(n, f); return; }
+    for (int i = 0; i < n; ++i) f(i);
 }
 
 static inline double Kt(int a, int c) {
@@ -52,13 +110,15 @@ cd elem_entry(const Model& m, const Elem& E, int a, int b, int c, int d, bool st
     return v;
 }
 
-// Complex Gauss-Jordan inverse with partial pivoting (row-major, in place into inv).
-static bool invert(int n, std::vector<cd> A, std::vector<cd>& inv, double& minpiv) {
+// Complex Gauss-Jordan inverse with partial pivoting on the augmented system [A | I]
+// (row-major).  For n >= 128 the row eliminations of each pivot step run on the pool.
+static bool invert(int n, std::vector<cd> A, std::vector<cd>& inv, double& minpiv, int nthreads = 1) {
     inv.assign((size_t)n * n, cd(0));
     for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
     double scale = 0;
     for (auto& v : A) scale = std::max(scale, std::abs(v));
     minpiv = 1e300;
+    const bool par = nthreads > 1 && n >= 128;
     for (int c = 0; c < n; ++c) {
         int piv = c;
         for (int r = c + 1; r < n; ++r)
@@ -72,16 +132,26 @@ static bool invert(int n, std::vector<cd> A, std::vector<cd>& inv, double& minpi
                 std::swap(inv[(size_t)c * n + j], inv[(size_t)piv * n + j]);
             }
         const cd d = 1.0 / A[(size_t)c * n + c];
-        for (int j = 0; j < n; ++j) { A[(size_t)c * n + j] *= d; inv[(size_t)c * n + j] *= d; }
-        for (int r = 0; r < n; ++r) {
-            if (r == c) continue;
+        for (int j = c; j < n; ++j) A[(size_t)c * n + j] *= d;
+        for (int j = 0; j < n; ++j) inv[(size_t)c * n + j] *= d;
+        auto elim = [&](int r) {
+            if (r == c) return;
             const cd f = A[(size_t)r * n + c];
-            if (f == cd(0)) continue;
+            if (f == cd(0)) return;
             cd* ar = &A[(size_t)r * n];
             const cd* ac = &A[(size_t)c * n];
             cd* ir = &inv[(size_t)r * n];
             const cd* ic = &inv[(size_t)c * n];
-            for (int j = 0; j < n; ++j) { ar[j] -= f * ac[j]; ir[j] -= f * ic[j]; }
+            for (int j = c; j < n; ++j) ar[j] -= f * ac[j];
+            for (int j = 0; j < n; ++j) ir[j] -= f * ic[j];
+        };
+        if (par) {
+            const int chunk = 16, nchunks = (n + chunk - 1) / chunk;
+            parallel_for(nchunks, nthreads, [&](int q) {
+                for (int r = q * chunk; r < std::min(n, (q + 1) * chunk); ++r) elim(r);
+            });
+        } else {
+            for (int r = 0; r < n; ++r) elim(r);
         }
     }
     return true;
@@ -159,6 +229,7 @@ static void cross_green(const PTable& T, double c, const std::vector<int>& X, st
 namespace {
 struct ElemFactor {
     std::vector<cd> Se;      // nT x nT local coarse Schur complement
+    double sinv_err = 0;
     double gap = 1;
     double minpiv = 1;
     bool ok = true;
@@ -222,6 +293,9 @@ static void build_slap_tables(Model& m) {
 }
 
 bool factor(Model& m, int nthreads, std::string& err) {
+    Pool pool(nthreads);
+    g_pool = &pool;
+    struct Reset { ~Reset() { g_pool = nullptr; } } reset_pool;
     const int E = (int)m.el.size();
     build_slap_tables(m);
     // Sinv storage
@@ -257,6 +331,14 @@ bool factor(Model& m, int nthreads, std::string& err) {
             gemm(nX, nX, nE, G.data(), AXE.data(), GX.data(), false, 1);
             gemm(nE, nX, nE, AEX.data(), GX.data(), AEE.data(), true, 1);
             if (!invert(nE, AEE, Sinv, ef[e].minpiv)) { ef[e].ok = false; return; }
+            if (m.check_factor) {
+                std::vector<cd> P((size_t)nE * nE);
+                gemm(nE, nE, nE, AEE.data(), Sinv.data(), P.data(), false, 1);
+                double mx = 0;
+                for (int i = 0; i < nE; ++i)
+                    for (int j = 0; j < nE; ++j) mx = std::max(mx, std::abs(P[(size_t)i * nE + j] - (i == j ? 1.0 : 0.0)));
+                ef[e].sinv_err = mx;
+            }
             for (int i = 0; i < nE; ++i)          // store column-major
                 for (int j = 0; j < nE; ++j) m.sinv[El.sinv_off + (size_t)j * nE + i] = Sinv[(size_t)i * nE + j];
         }
@@ -267,6 +349,10 @@ bool factor(Model& m, int nthreads, std::string& err) {
         gemm(nT, nX, nT, ATX.data(), yX.data(), ef[e].Se.data(), true, 1);
     });
     m.min_gap = 1e300;
+    if (m.check_factor) {
+        m.sinv_check = 0;
+        for (int e = 0; e < E; ++e) m.sinv_check = std::max(m.sinv_check, ef[e].sinv_err);
+    }
     for (int e = 0; e < E; ++e) {
         if (!ef[e].ok) { err = "singular edge Schur complement in element " + std::to_string(e) + " (resonant element)"; return false; }
         m.min_gap = std::min(m.min_gap, ef[e].gap);
@@ -333,8 +419,54 @@ bool factor(Model& m, int nthreads, std::string& err) {
             m.Up[b - 1] = KlT;          // K_{b-1,b}  (np x nbk)
         }
         double mp;
-        if (!invert(nbk, D, m.Dinv[b], mp)) { err = "singular coarse matrix block"; return false; }
+        if (!invert(nbk, D, m.Dinv[b], mp, nthreads)) { err = "singular coarse matrix block"; return false; }
     }
+    {
+        // self-check: x = K^-1 t by the block factorisation, then ||K x - t|| / ||t|| with the
+        // assembled blocks for a seeded random t
+        std::vector<std::vector<cd>> t(m.nb), w(m.nb), x(m.nb);
+        uint64_t st = 12345;
+        for (int b = 0; b < m.nb; ++b) {
+            t[b].resize(m.blk_size[b]);
+            for (auto& v : t[b]) {
+                st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+                const double re = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+                st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+                const double im = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+                v = cd(re, im);
+            }
+            w[b] = t[b];
+        }
+        auto mv = [](const std::vector<cd>& A, int r, int c, const std::vector<cd>& v, std::vector<cd>& out, double sg) {
+            for (int i = 0; i < r; ++i) { cd s = 0; for (int j = 0; j < c; ++j) s += A[(size_t)i * c + j] * v[j]; out[i] += sg * s; }
+        };
+        for (int b = 1; b < m.nb; ++b) mv(m.Lo[b], m.blk_size[b], m.blk_size[b - 1], w[b - 1], w[b], -1.0);
+        for (int b = m.nb - 1; b >= 0; --b) {
+            std::vector<cd> r = w[b];
+            if (b + 1 < m.nb) mv(m.Up[b], m.blk_size[b], m.blk_size[b + 1], x[b + 1], r, -1.0);
+            x[b].assign(m.blk_size[b], cd(0));
+            mv(m.Dinv[b], m.blk_size[b], m.blk_size[b], r, x[b], 1.0);
+        }
+        double num = 0, den = 0;
+        for (int b = 0; b < m.nb; ++b) {
+            std::vector<cd> y(m.blk_size[b], cd(0));
+            mv(Kd[b], m.blk_size[b], m.blk_size[b], x[b], y, 1.0);
+            if (b > 0) mv(Kl[b], m.blk_size[b], m.blk_size[b - 1], x[b - 1], y, 1.0);
+            if (b + 1 < m.nb) {
+                // K_{b,b+1} = Kl[b+1]^T
+                const int nn = m.blk_size[b + 1];
+                for (int i = 0; i < m.blk_size[b]; ++i) {
+                    cd s = 0;
+                    for (int j = 0; j < nn; ++j) s += Kl[b + 1][(size_t)j * m.blk_size[b] + i] * x[b + 1][j];
+                    y[i] += s;
+                }
+            }
+            for (int i = 0; i < m.blk_size[b]; ++i) { num += std::norm(y[i] - t[b][i]); den += std::norm(t[b][i]); }
+        }
+        m.coarse_check = std::sqrt(num / den);
+    }
+    m.coarse_refine = m.coarse_check > 1e-12;
+    if (m.coarse_refine) { m.Kd = Kd; m.Kl = Kl; } else { m.Kd.clear(); m.Kl.clear(); }
     // dense inverse for small coarse problems: K^-1 e_g by block-tridiagonal solves
     m.dense_coarse = nc <= 6144;
     if (m.dense_coarse) {
@@ -369,6 +501,37 @@ bool factor(Model& m, int nthreads, std::string& err) {
                     for (int j = 0; j < nbk; ++j) s += m.Dinv[b][(size_t)i * nbk + j] * r[j];
                     x[b][i] = s;
                 }
+            }
+            if (m.coarse_refine) {
+                // one refinement step: r = e_col - K x, x += BT(r)
+                std::vector<std::vector<cd>> r(m.nb), dx(m.nb);
+                for (int b = 0; b < m.nb; ++b) {
+                    const int nbk = m.blk_size[b];
+                    r[b].assign(nbk, cd(0));
+                    if (b == m.blk_of[col]) r[b][m.pos_in_blk[col]] = 1.0;
+                    for (int i = 0; i < nbk; ++i) {
+                        cd s = 0;
+                        for (int j = 0; j < nbk; ++j) s += Kd[b][(size_t)i * nbk + j] * x[b][j];
+                        if (b > 0) for (int j = 0; j < m.blk_size[b - 1]; ++j) s += Kl[b][(size_t)i * m.blk_size[b - 1] + j] * x[b - 1][j];
+                        if (b + 1 < m.nb) for (int j = 0; j < m.blk_size[b + 1]; ++j) s += Kl[b + 1][(size_t)j * nbk + i] * x[b + 1][j];
+                        r[b][i] -= s;
+                    }
+                }
+                for (int b = 1; b < m.nb; ++b) {
+                    const int nbk = m.blk_size[b], np = m.blk_size[b - 1];
+                    for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < np; ++j) s += m.Lo[b][(size_t)i * np + j] * r[b - 1][j]; r[b][i] -= s; }
+                }
+                for (int b = m.nb - 1; b >= 0; --b) {
+                    const int nbk = m.blk_size[b];
+                    std::vector<cd> q = r[b];
+                    if (b + 1 < m.nb) {
+                        const int nn = m.blk_size[b + 1];
+                        for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < nn; ++j) s += m.Up[b][(size_t)i * nn + j] * dx[b + 1][j]; q[i] -= s; }
+                    }
+                    dx[b].assign(nbk, cd(0));
+                    for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < nbk; ++j) s += m.Dinv[b][(size_t)i * nbk + j] * q[j]; dx[b][i] = s; }
+                }
+                for (int b = 0; b < m.nb; ++b) for (int i = 0; i < m.blk_size[b]; ++i) x[b][i] += dx[b][i];
             }
             for (int b = 0; b < m.nb; ++b)
                 for (int i = 0; i < m.blk_size[b]; ++i)

@@ -102,6 +102,14 @@ struct Model {
     std::vector<std::vector<cd>> Dinv, Lo, Up;    // per block dense row-major
     bool dense_coarse = false;                    // use a dense K^-1 instead
     std::vector<cd> Kinv;                         // n_coarse^2 row-major when dense_coarse
+    // diagnostics: relative residual ||K x - t|| / ||t|| of one coarse solve with a seeded
+    // random t, and max_e ||S_E S_E^-1 - I||_max (computed when check_factor is set)
+    bool check_factor = false;
+    double coarse_check = -1, sinv_check = -1;
+    // block factorisation without pivoting across blocks: when the self-check residual exceeds
+    // 1e-12 the FP64 solves apply one step of iterative refinement with the assembled blocks
+    bool coarse_refine = false;
+    std::vector<std::vector<cd>> Kd, Kl;          // K_bb and K_{b,b-1} (kept for refinement)
     std::string err;
 };
 

@@ -5,6 +5,7 @@
 // FP64.
 #include "ddh_kernels.cuh"
 #include "ddh_launch.hpp"
+#include <algorithm>
 
 namespace ddh {
 
@@ -22,98 +23,127 @@ __device__ __forceinline__ void elem_gam(const DevModel& dm, int e, T* g) {
     for (int s = 0; s < 4; ++s) g[s] = (T)dm.gam[4 * e + s];
 }
 
-// x_E = Sinv r_E, Sinv column-major (coalesced across output rows); r in smem, out in smem
-template <class T>
-__device__ inline void sinv_apply(const cpx<T>* __restrict__ sinv, int nE, const cpx<T>* r, cpx<T>* out) {
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        cpx<T> acc = mk<T>(0, 0);
-        for (int j = 0; j < nE; ++j) fma_c(acc, sinv[(int64_t)j * nE + i], r[j]);
-        out[i] = acc;
+// X = Sinv R for cnt right-hand sides (R, X in smem, [rb][nE]); Sinv column-major so that the
+// loads of a column are coalesced across output rows; each Sinv entry is read once per CTA.
+template <class T, int RB, class G>
+__device__ inline void sinv_apply_batched(const G& g, const cpx<T>* __restrict__ sinv, int nE, int cnt, const cpx<T>* r,
+                                          int rstride, cpx<T>* out) {
+    for (int i = g.t(); i < nE; i += g.n()) {
+        cpx<T> acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
+#pragma unroll 4
+        for (int j = 0; j < nE; ++j) {
+            const cpx<T> s = sinv[(int64_t)j * nE + i];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                if (q < cnt) fma_c(acc[q], s, r[q * rstride + j]);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (q < cnt) out[q * rstride + i] = acc[q];
     }
-    __syncthreads();
+    g.sync();
+}
+
+// A_II^-1 b_I on the cross for one RHS (b_I read from the local vector): leaves the divided
+// spectral coefficients in spec and the cross values in rrow/rcol.
+template <class T, class G>
+__device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, const double2* bt, int64_t base, int p, T ce) {
+    const int N = p + 1, n = p - 1;
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
+        const int a = idx / n, b = idx % n;
+        s.tmp[idx] = ld<T>(bt, base + (a + 2) + N * (b + 2));
+    }
+    g.sync();
+    spec_from_full<T>(g, s, n);
+    spec_divide<T>(g, s, n, ce);
+    cross_from_spec<T>(g, s, n);
 }
 
 // ------------------------------------------------------------------ pass 1
 // y1 = A11^-1 [r_E; r_I] with r_E = s * C1^T z + b_E, r_I = b_I (flag), then
 // tT = (A Phi)_T with Phi = [x_E; y_I; 0] (i.e. A_T1 y1).  Writes x_E and tT.
-template <class T>
+// One CTA per (element, block of RB right-hand sides).
+template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                const double2* __restrict__ z, double zsign,
-                                               const double2* __restrict__ bt, int has_bI,
+                                               const double2* __restrict__ bt, int has_bI, int R,
                                                cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
-                                               const int* __restrict__ done) {
+                                               const int* __restrict__ done, int ntask, int per_warp) {
     if (done && *done) return;
     extern __shared__ __align__(16) char smem[];
-    const int e = blockIdx.x, r = blockIdx.y;
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
     const int p = dm.p[e], N = p + 1, n = p - 1;
     ElemSmem<T> s = carve<T>(smem, dm.pmax, 0);
-    cpx<T>* rE = s.vec;
-    cpx<T>* xE = s.vec + 4 * N;
-    load_tables<T>(dm, e, s);
+    (void)per_warp;
+    const int stride = 4 * N;
+    cpx<T>* rE = s.vec;                     // [RB][4N]
+    cpx<T>* xE = s.vec + RB * stride;       // [RB][4N]
+    load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const int64_t off = dm.off[e];
     const T ce = (T)dm.c[e];
     T gam[4];
     elem_gam<T>(dm, e, gam);
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.tile[i] = mk<T>(0, 0);
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE, r = r0 + q;
         cpx<T> v = mk<T>(0, 0);
         const int row = dm.e1_row[e1o + i];
-        if (z && row >= 0) {
-            const cpx<T> zz = ld<T>(z, (int64_t)r * dm.n_dual + row);
-            v = (T)(zsign * dm.e1_sign[e1o + i]) * zz;
-        }
+        if (z && row >= 0) v = (T)(zsign * dm.e1_sign[e1o + i]) * ld<T>(z, (int64_t)r * dm.n_dual + row);
         if (bt) v += ld<T>(bt, (int64_t)r * dm.n_local + off + dm.e1_slot[e1o + i]);
-        rE[i] = v;
+        rE[q * stride + i] = v;
     }
-    __syncthreads();
+    g.sync();
     if (bt && has_bI) {
-        // spec_b = V^T b_I V / D ; r_E -= A_EI (A_II^-1 b_I)
-        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-            const int a = idx / n, b = idx % n;
-            s.tmp[idx] = ld<T>(bt, (int64_t)r * dm.n_local + off + (a + 2) + N * (b + 2));
+        // r_E -= A_EI (A_II^-1 b_I) for every RHS of the block
+        for (int q = 0; q < cnt; ++q) {
+            for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
+            interior_load_cross<T>(g, s, bt, (int64_t)(r0 + q) * dm.n_local + off, p, ce);
+            cross_to_tile<T>(g, s, p, (T)1);
+            for (int i = g.t(); i < nE; i += g.n()) {
+                const int slot = dm.e1_slot[e1o + i];
+                rE[q * stride + i] -= apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+            }
+            g.sync();
         }
-        __syncthreads();
-        spec_from_full<T>(s, n);
-        spec_divide<T>(s, n, ce);
-        cross_from_spec<T>(s, n);
-        cross_to_tile<T>(s, p, (T)1);
-        for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-            const int slot = dm.e1_slot[e1o + i];
-            rE[i] -= apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+    }
+    sinv_apply_batched<T, RB>(g, sinv + dm.sinv_off[e], nE, cnt, rE, stride, xE);
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE;
+        xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = xE[q * stride + i];
+    }
+    for (int q = 0; q < cnt; ++q) {
+        const int r = r0 + q;
+        for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
+        g.sync();
+        for (int i = g.t(); i < nE; i += g.n()) s.tile[dm.e1_slot[e1o + i]] = xE[q * stride + i];
+        g.sync();
+        // y_I = A_II^-1 (b_I - A_IE x_E) on the cross: the coupling part first ...
+        cross_coupling<T>(g, s, p, ce, (T)-1);
+        spec_from_cross<T>(g, s, n, false);
+        spec_divide<T>(g, s, n, ce);
+        cross_from_spec<T>(g, s, n);
+        cross_to_tile<T>(g, s, p, (T)1);
+        if (bt && has_bI) {
+            // ... then + A_II^-1 b_I on the cross (the tile keeps the coupling part)
+            interior_load_cross<T>(g, s, bt, (int64_t)r * dm.n_local + off, p, ce);
+            for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
+                const int i = idx / n, qq = idx % n;
+                s.tile[(i + 2) + N * (qq + 2)] += s.rrow[i * n + qq];
+                if (qq >= 2) s.tile[(qq + 2) + N * (i + 2)] += s.rcol[i * n + qq];
+            }
+            g.sync();
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.tile[i] = mk<T>(0, 0);
-        __syncthreads();
-    } else {
-        for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.spec[i] = mk<T>(0, 0);
-    }
-    sinv_apply<T>(sinv + dm.sinv_off[e], nE, rE, xE);
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        xE_out[(int64_t)r * dm.nE1_tot + e1o + i] = xE[i];
-        s.tile[dm.e1_slot[e1o + i]] = xE[i];
-    }
-    __syncthreads();
-    // y_I = A_II^-1 (b_I - A_IE x_E) on the cross: spec (= spec_b or 0) + V^T(-coupling)V / D
-    if (bt && has_bI) {
-        // keep spec_b (already divided); add the coupling part separately
-        for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.tmp[i] = s.spec[i];
-        __syncthreads();
-        cross_coupling<T>(s, p, ce, (T)-1);
-        spec_from_cross<T>(s, n, false);
-        spec_divide<T>(s, n, ce);
-        for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.spec[i] += s.tmp[i];
-        __syncthreads();
-    } else {
-        cross_coupling<T>(s, p, ce, (T)-1);
-        spec_from_cross<T>(s, n, false);
-        spec_divide<T>(s, n, ce);
-    }
-    cross_from_spec<T>(s, n);
-    cross_to_tile<T>(s, p, (T)1);
-    for (int i = threadIdx.x; i < nT; i += blockDim.x) {
-        const int slot = dm.t_slot[to + i];
-        tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+        for (int i = g.t(); i < nT; i += g.n()) {
+            const int slot = dm.t_slot[to + i];
+            tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+        }
+        g.sync();
     }
 }
 
@@ -151,63 +181,123 @@ __global__ void k_coarse_assemble(DevModel dm, const cpx<T>* __restrict__ tT, co
     tout[(int64_t)r * dm.n_coarse + g] = acc;
 }
 
-// ------------------------------------------------------------------ coarse solve (FP64)
-// y = A x for a dense row-major complex matrix (n_out x n_in), one warp per output row.
+// ------------------------------------------------------------------ coarse solve
+// y = A x for a dense row-major complex matrix (n_out x n_in) and R right-hand sides, one
+// warp per output row; the row is read once and applied to up to 8 RHS per pass (vectors and
+// accumulation FP64; the matrix is complex128, or complex64 for the mixed-precision inner solve).
 // mode 0: y = A x ; mode 1: y -= A x ; mode 2: y = c - A x (c given)
-__global__ void k_gemv_c64(const double2* __restrict__ A, int n_out, int n_in, const double2* __restrict__ x,
-                           double2* __restrict__ y, const double2* __restrict__ c, int mode,
-                           int64_t xs, int64_t ys, const int* __restrict__ done) {
+template <class M, int RB>
+__global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const double2* __restrict__ x,
+                       double2* __restrict__ y, const double2* __restrict__ c, int mode,
+                       int64_t xs, int64_t ys, int r0, const int* __restrict__ done) {
     if (done && *done) return;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const int r = blockIdx.y;
     if (warp >= n_out) return;
-    const double2* a = A + (int64_t)warp * n_in;
-    const double2* xr = x + r * xs;
-    double sx = 0, sy = 0;
+    const M* a = A + (int64_t)warp * n_in;
+    double sx[RB], sy[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) { sx[q] = 0; sy[q] = 0; }
     for (int j = lane; j < n_in; j += 32) {
-        const double2 av = a[j], xv = xr[j];
-        sx = fma(av.x, xv.x, fma(-av.y, xv.y, sx));
-        sy = fma(av.x, xv.y, fma(av.y, xv.x, sy));
+        const M av = a[j];
+        const double ax = (double)av.x, ay = (double)av.y;
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            const double2 xv = x[(r0 + q) * xs + j];
+            sx[q] = fma(ax, xv.x, fma(-ay, xv.y, sx[q]));
+            sy[q] = fma(ax, xv.y, fma(ay, xv.x, sy[q]));
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+        for (int o = 16; o > 0; o >>= 1) {
+            sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], o);
+            sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], o);
+        }
     }
-    if (lane == 0) {
-        double2* yr = y + r * ys;
-        if (mode == 0) yr[warp] = make_double2(sx, sy);
-        else if (mode == 1) { yr[warp].x -= sx; yr[warp].y -= sy; }
-        else { const double2 cv = c[r * ys + warp]; yr[warp] = make_double2(cv.x - sx, cv.y - sy); }
+    if (lane < RB) {
+        double vx = 0, vy = 0;
+#pragma unroll
+        for (int q = 0; q < RB; ++q) if (q == lane) { vx = sx[q]; vy = sy[q]; }
+        double2* yr = y + (r0 + lane) * ys;
+        if (mode == 0) yr[warp] = make_double2(vx, vy);
+        else if (mode == 1) { yr[warp].x -= vx; yr[warp].y -= vy; }
+        else { const double2 cv = c[(r0 + lane) * ys + warp]; yr[warp] = make_double2(cv.x - vx, cv.y - vy); }
+    }
+}
+
+// Coarse residual with the assembled blocks, all blocks at once (one warp per row):
+// r_b = t_b - (K_bb x_b + K_{b,b-1} x_{b-1} + K_{b,b+1} x_{b+1}); blocks row-major, vectors FP64.
+struct BlockK {
+    const double2* const* Kd;    // [nb] K_bb
+    const double2* const* Kl;    // [nb] K_{b,b-1} (b >= 1)
+    const double2* const* Ku;    // [nb] K_{b,b+1} (b < nb-1)
+    const int* start;            // [nb+1]
+    const int* row_blk;          // [n] block of each row
+    int nb, n;
+};
+__global__ void k_coarse_residual(BlockK B, const double2* __restrict__ x, const double2* __restrict__ t,
+                                  double2* __restrict__ r, int R, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= B.n) return;
+    const int b = B.row_blk[row];
+    const int s0 = B.start[b], nb0 = B.start[b + 1] - s0, i = row - s0;
+    for (int rr = 0; rr < R; ++rr) {
+        const double2* xr = x + (int64_t)rr * B.n;
+        double sx = 0, sy = 0;
+        auto acc = [&](const double2* M, int ncol, int c0) {
+            const double2* a = M + (int64_t)i * ncol;
+            for (int j = lane; j < ncol; j += 32) {
+                const double2 av = a[j], xv = xr[c0 + j];
+                sx = fma(av.x, xv.x, fma(-av.y, xv.y, sx));
+                sy = fma(av.x, xv.y, fma(av.y, xv.x, sy));
+            }
+        };
+        acc(B.Kd[b], nb0, s0);
+        if (b > 0) acc(B.Kl[b], B.start[b] - B.start[b - 1], B.start[b - 1]);
+        if (b + 1 < B.nb) acc(B.Ku[b], B.start[b + 2] - B.start[b + 1], B.start[b + 1]);
+        for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
+        if (lane == 0) {
+            const double2 tv = t[(int64_t)rr * B.n + row];
+            r[(int64_t)rr * B.n + row] = make_double2(tv.x - sx, tv.y - sy);
+        }
     }
 }
 
 // ------------------------------------------------------------------ pass 2
 // x1_E = x_E - [A11^-1 A_1T u_T]_E, u_T = Z2 x2.  With recover != 0 also writes the full
 // element solution (interpolatory basis) phi = [x1_E; x1_I; u_T], x1_I = A_II^-1 (b_I -
-// A_IE x1_E - A_IT u_T), into phi_out.
-template <class T>
+// A_IE x1_E - A_IT u_T), into phi_out.  One CTA per (element, block of RB RHS).
+template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
                                                cpx<T>* __restrict__ xE_out, int recover,
-                                               const double2* __restrict__ bt, int has_bI,
-                                               double2* __restrict__ phi_out, const int* __restrict__ done) {
+                                               const double2* __restrict__ bt, int has_bI, int R,
+                                               double2* __restrict__ phi_out, const int* __restrict__ done,
+                                               int ntask, int per_warp) {
     if (done && *done) return;
     extern __shared__ __align__(16) char smem[];
-    const int e = blockIdx.x, r = blockIdx.y;
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
     const int p = dm.p[e], N = p + 1, n = p - 1;
     ElemSmem<T> s = carve<T>(smem, dm.pmax, 0);
-    cpx<T>* rE = s.vec;
-    cpx<T>* sE = s.vec + 4 * N;
-    cpx<T>* uT = s.vec + 8 * N;
-    load_tables<T>(dm, e, s);
+    (void)per_warp;
+    const int stride = 4 * N;
+    cpx<T>* rE = s.vec;                       // [RB][4N]
+    cpx<T>* sE = s.vec + RB * stride;         // [RB][4N]
+    cpx<T>* uT = s.vec + 2 * RB * stride;     // [RB][4N]
+    load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const T ce = (T)dm.c[e];
     T gam[4];
     elem_gam<T>(dm, e, gam);
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.tile[i] = mk<T>(0, 0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nT; i += blockDim.x) {
+    for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
+        const int q = idx / nT, i = idx % nT, r = r0 + q;
         cpx<T> u = mk<T>(0, 0);
         for (int a = dm.t_ptr[to + i]; a < dm.t_ptr[to + i + 1]; ++a) {
             const double2 xv = x2[(int64_t)r * dm.n_coarse + dm.t_col[a]];
@@ -215,56 +305,66 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
             u.x += w * (T)xv.x;
             u.y += w * (T)xv.y;
         }
-        uT[i] = u;
-        s.tile[dm.t_slot[to + i]] = u;
+        uT[q * stride + i] = u;
     }
-    __syncthreads();
-    // w_I = A_II^-1 (A_IT u_T) on the cross
-    cross_coupling<T>(s, p, ce, (T)1);
-    spec_from_cross<T>(s, n, false);
-    spec_divide<T>(s, n, ce);
-    cross_from_spec<T>(s, n);
-    cross_to_tile<T>(s, p, (T)-1);
-    // r'_E = A_ET u_T - A_EI w_I
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        const int slot = dm.e1_slot[e1o + i];
-        rE[i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+    g.sync();
+    for (int q = 0; q < cnt; ++q) {
+        for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
+        g.sync();
+        for (int i = g.t(); i < nT; i += g.n()) s.tile[dm.t_slot[to + i]] = uT[q * stride + i];
+        g.sync();
+        // w_I = A_II^-1 (A_IT u_T) on the cross; r'_E = A_ET u_T - A_EI w_I
+        cross_coupling<T>(g, s, p, ce, (T)1);
+        spec_from_cross<T>(g, s, n, false);
+        spec_divide<T>(g, s, n, ce);
+        cross_from_spec<T>(g, s, n);
+        cross_to_tile<T>(g, s, p, (T)-1);
+        for (int i = g.t(); i < nE; i += g.n()) {
+            const int slot = dm.e1_slot[e1o + i];
+            rE[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+        }
+        g.sync();
     }
-    __syncthreads();
-    sinv_apply<T>(sinv + dm.sinv_off[e], nE, rE, sE);
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        const cpx<T> v = xE_in[(int64_t)r * dm.nE1_tot + e1o + i] - sE[i];
-        sE[i] = v;
-        if (xE_out) xE_out[(int64_t)r * dm.nE1_tot + e1o + i] = v;
+    sinv_apply_batched<T, RB>(g, sinv + dm.sinv_off[e], nE, cnt, rE, stride, sE);
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE;
+        const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
+        const cpx<T> v = xE_in[gi] - sE[q * stride + i];
+        sE[q * stride + i] = v;
+        if (xE_out) xE_out[gi] = v;
     }
-    __syncthreads();
+    g.sync();
     if (!recover) return;
-    // full recovery: tile = [x1_E; 0; u_T]; x1_I = A_II^-1 (b_I - coupling)
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.tile[i] = mk<T>(0, 0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nT; i += blockDim.x) s.tile[dm.t_slot[to + i]] = uT[i];
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) s.tile[dm.e1_slot[e1o + i]] = sE[i];
-    __syncthreads();
-    cross_coupling<T>(s, p, ce, (T)-1);
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int a = idx / n, b = idx % n;
-        cpx<T> v = mk<T>(0, 0);
-        if (bt && has_bI) v = ld<T>(bt, (int64_t)r * dm.n_local + dm.off[e] + (a + 2) + N * (b + 2));
-        if (a < 2) v += s.rrow[a * n + b];
-        if (b < 2) v += s.rcol[b * n + a];
-        s.tmp[idx] = v;
-    }
-    __syncthreads();
-    spec_from_full<T>(s, n);
-    spec_divide<T>(s, n, ce);
-    full_from_spec<T>(s, n);
-    const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        const int a = idx % N, b = idx / N;
-        cpx<T> v;
-        if (a >= 2 && b >= 2) v = s.spec[(a - 2) * n + (b - 2)];
-        else v = s.tile[idx];
-        st<T>(phi_out, base + idx, v);
+    for (int q = 0; q < cnt; ++q) {
+        const int r = r0 + q;
+        // full recovery: tile = [x1_E; 0; u_T]; x1_I = A_II^-1 (b_I - coupling)
+        for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
+        g.sync();
+        for (int i = g.t(); i < nT; i += g.n()) s.tile[dm.t_slot[to + i]] = uT[q * stride + i];
+        for (int i = g.t(); i < nE; i += g.n()) s.tile[dm.e1_slot[e1o + i]] = sE[q * stride + i];
+        g.sync();
+        cross_coupling<T>(g, s, p, ce, (T)-1);
+        for (int idx = g.t(); idx < n * n; idx += g.n()) {
+            const int a = idx / n, b = idx % n;
+            cpx<T> v = mk<T>(0, 0);
+            if (bt && has_bI) v = ld<T>(bt, (int64_t)r * dm.n_local + dm.off[e] + (a + 2) + N * (b + 2));
+            if (a < 2) v += s.rrow[a * n + b];
+            if (b < 2) v += s.rcol[b * n + a];
+            s.tmp[idx] = v;
+        }
+        g.sync();
+        spec_from_full<T>(g, s, n);
+        spec_divide<T>(g, s, n, ce);
+        full_from_spec<T>(g, s, n);
+        const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
+        for (int idx = g.t(); idx < N * N; idx += g.n()) {
+            const int a = idx % N, b = idx / N;
+            cpx<T> v;
+            if (a >= 2 && b >= 2) v = s.spec[(a - 2) * n + (b - 2)];
+            else v = s.tile[idx];
+            st<T>(phi_out, base + idx, v);
+        }
+        g.sync();
     }
 }
 
@@ -316,34 +416,42 @@ __global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __re
     (void)lumped;
 }
 
-// out_E = S^Lap[E1][E1] (C1^T v) per element (stiffness Schur complement, shared per degree)
-template <class T>
+// out_E = S^Lap[E1][E1] (C1^T v) per element (stiffness Schur complement, shared per degree);
+// one CTA per (element, block of RB RHS), each S^Lap entry read once per CTA.
+template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __restrict__ v, cpx<T>* __restrict__ outE,
-                                                  int lumped, const int* __restrict__ done) {
+                                                  int R, const int* __restrict__ done) {
     if (done && *done) return;
     extern __shared__ __align__(16) char smem[];
-    const int e = blockIdx.x, r = blockIdx.y;
+    const int e = blockIdx.x, r0 = blockIdx.y * RB;
+    const int cnt = min(RB, R - r0);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e];
-    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
+    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);     // [RB][nE]
+    for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
+        const int q = idx / nE, i = idx % nE;
         const int row = dm.e1_row[e1o + i];
         cpx<T> val = mk<T>(0, 0);
-        if (row >= 0) val = (T)dm.e1_sign[e1o + i] * ld<T>(v, (int64_t)r * dm.n_dual + row);
-        in[i] = val;
+        if (row >= 0) val = (T)dm.e1_sign[e1o + i] * ld<T>(v, (int64_t)(r0 + q) * dm.n_dual + row);
+        in[q * nE + i] = val;
     }
     __syncthreads();
     const int t = dm.ptab[e];
     const int p = dm.p[e], ne = 4 * (p - 1);
     const double* S = dm.slap_all + dm.tab_slap[t];
     for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        cpx<T> acc = mk<T>(0, 0);
-        if (lumped) {
-            acc = in[i];
-        } else {
-            const int gi = dm.e1_eall[e1o + i];
-            for (int j = 0; j < nE; ++j) fma_r(acc, (T)S[(int64_t)gi * ne + dm.e1_eall[e1o + j]], in[j]);
+        cpx<T> acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
+        const int gi = dm.e1_eall[e1o + i];
+        for (int j = 0; j < nE; ++j) {
+            const T sv = (T)S[(int64_t)gi * ne + dm.e1_eall[e1o + j]];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
         }
-        outE[(int64_t)r * dm.nE1_tot + e1o + i] = acc;
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (q < cnt) outE[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = acc[q];
     }
 }
 
@@ -455,8 +563,9 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
     extern __shared__ __align__(16) char smem[];
     const int e = blockIdx.x, r = blockIdx.y;
     const int p = dm.p[e], N = p + 1;
+    const CtaGroup g;
     ElemSmem<double> s = carve<double>(smem, dm.pmax, 0);
-    load_tables<double>(dm, e, s);
+    load_tables<double>(g, dm, e, s);
     const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) { const double2 v = phi[base + i]; s.tile[i] = mk<double>(v.x, v.y); }
     __syncthreads();
@@ -496,6 +605,47 @@ __global__ void k_conf_gather(DevModel dm, const double2* __restrict__ x, double
     }
 }
 
+// ------------------------------------------------------------------ conforming maps (FP64)
+// phi~[s] = sum_{(q, w) of slot s} w x[q]   (Z_c x: slaving/assembly basis of the conforming space)
+__global__ void k_conf_scatter(DevModel dm, const double2* __restrict__ x, double2* __restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= dm.n_local) return;
+    double sx = 0, sy = 0;
+    for (int a = dm.cfl_ptr[s]; a < dm.cfl_ptr[s + 1]; ++a) {
+        const double2 v = x[(int64_t)r * dm.n_conf + dm.cfl_col[a]];
+        sx += dm.cfl_w[a] * v.x;
+        sy += dm.cfl_w[a] * v.y;
+    }
+    out[(int64_t)r * dm.n_local + s] = make_double2(sx, sy);
+}
+// out[q] = sign * sum_{(s, w) of dof q} w x[s]   (Z_c^T x)
+__global__ void k_conf_gather_vec(DevModel dm, const double2* __restrict__ x, double2* __restrict__ out, double sign) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (q >= dm.n_conf) return;
+    double sx = 0, sy = 0;
+    for (int a = dm.cf_ptr[q]; a < dm.cf_ptr[q + 1]; ++a) {
+        const double2 v = x[(int64_t)r * dm.n_local + dm.cf_loc[a]];
+        sx += dm.cf_w[a] * v.x;
+        sy += dm.cf_w[a] * v.y;
+    }
+    out[(int64_t)r * dm.n_conf + q] = make_double2(sign * sx, sign * sy);
+}
+// b~[master[q]] = r[q] (b~ zeroed by the caller): a local load with Z_c^T b~ = r
+__global__ void k_inject(DevModel dm, const double2* __restrict__ rc, double2* __restrict__ b) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (q >= dm.n_conf) return;
+    b[(int64_t)r * dm.n_local + dm.master[q]] = rc[(int64_t)r * dm.n_conf + q];
+}
+__global__ void k_readback(DevModel dm, const double2* __restrict__ phi, double2* __restrict__ z) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (q >= dm.n_conf) return;
+    z[(int64_t)r * dm.n_conf + q] = phi[(int64_t)r * dm.n_local + dm.master[q]];
+}
+
 // ------------------------------------------------------------------ FGMRES (FP64)
 // State layout per RHS r: V[r][j][nd] (j <= m), Zb[r][j][nd] (j < m), H[r][j][m+1] column j,
 // cs[r][m], sn[r][m], g[r][m+1], bnorm[r]; ctl = {j, all_done, ...}; done[r]; iters[r].
@@ -517,89 +667,78 @@ __global__ void k_store(KrylovDev K) {
     K.Zb[((int64_t)r * K.m + j) * K.nd + i] = K.zw[(int64_t)r * K.nd + i];
 }
 
-// partial dots: partial[r][chunk][i] = sum_{rows in chunk} conj(V_i) w, i <= j
-__global__ void k_dots(KrylovDev K) {
+// CGS2 building blocks.  The rows of a length-nd vector are split into nchunk contiguous
+// chunks (one CTA each).  k_dots: partial[r][chunk][i] = sum_{rows in chunk} conj(V_i) w for
+// every i <= j, one warp per basis vector i.
+__global__ void __launch_bounds__(256) k_dots(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
     const int rows = (K.nd + K.nchunk - 1) / K.nchunk;
     const int r0 = chunk * rows, r1 = min(K.nd, r0 + rows);
-    __shared__ double2 red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2* w = K.w + (int64_t)r * K.nd;
-    for (int i = 0; i <= j; ++i) {
+    for (int i = warp; i <= j; i += (blockDim.x >> 5)) {
         const double2* v = K.V + ((int64_t)r * (K.m + 1) + i) * K.nd;
         double sx = 0, sy = 0;
-        for (int q = r0 + threadIdx.x; q < r1; q += blockDim.x) {
+        for (int q = r0 + lane; q < r1; q += 32) {
             const double2 a = v[q], b = w[q];
-            sx += a.x * b.x + a.y * b.y;
-            sy += a.x * b.y - a.y * b.x;
+            sx = fma(a.x, b.x, fma(a.y, b.y, sx));
+            sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
         }
         for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(sx, sy);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tx = 0, ty = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { tx += red[k].x; ty += red[k].y; }
-            K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + i] = make_double2(tx, ty);
-        }
-        __syncthreads();
+        if (lane == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + i] = make_double2(sx, sy);
     }
 }
 
-// h[i] = sum_chunks partial; accumulate into hcol (pass 0 sets, pass 1 adds)
-__global__ void k_dots_reduce(KrylovDev K, int pass) {
+// w -= sum_{i<=j} V_i h_i with h = the chunk sums of the partial dots (every CTA reduces them
+// itself); CTA 0 accumulates h into the Hessenberg column (pass 0 sets, pass 1 adds).  In
+// pass 1 each CTA also writes the partial squared norm of the new w to partial[..][m].
+__global__ void __launch_bounds__(256) k_axpy(KrylovDev K, int pass) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
-    const int i = threadIdx.x, r = blockIdx.x;
-    if (i > j) return;
-    double sx = 0, sy = 0;
-    for (int c = 0; c < K.nchunk; ++c) {
-        const double2 v = K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + i];
-        sx += v.x; sy += v.y;
-    }
-    double2* hc = K.hcol + (int64_t)r * (K.m + 1);
-    // the pass's coefficients go to partial slot 0 row for the axpy
-    K.partial[((int64_t)r * K.nchunk) * (K.m + 1) + i] = make_double2(sx, sy);
-    if (pass == 0) hc[i] = make_double2(sx, sy);
-    else { hc[i].x += sx; hc[i].y += sy; }
-}
-
-// w -= sum_{i<=j} V_i h_i (h from the reduce pass)
-__global__ void k_axpy(KrylovDev K) {
-    if (K.ctl[1]) return;
-    const int j = K.ctl[0];
-    const int q = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (q >= K.nd) return;
-    const double2* h = K.partial + ((int64_t)r * K.nchunk) * (K.m + 1);
-    double2 w = K.w[(int64_t)r * K.nd + q];
-    for (int i = 0; i <= j; ++i) {
-        const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
-        const double2 hh = h[i];
-        w.x -= v.x * hh.x - v.y * hh.y;
-        w.y -= v.x * hh.y + v.y * hh.x;
-    }
-    K.w[(int64_t)r * K.nd + q] = w;
-}
-
-// partial norms of w into partial[r][chunk][0].x
-__global__ void k_norm_partial(KrylovDev K) {
-    if (K.ctl[1]) return;
     const int chunk = blockIdx.x, r = blockIdx.y;
+    __shared__ double2 h[256];
+    __shared__ double red[8];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        double sx = 0, sy = 0;
+        for (int c = 0; c < K.nchunk; ++c) {
+            const double2 v = K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + i];
+            sx += v.x; sy += v.y;
+        }
+        h[i] = make_double2(sx, sy);
+    }
+    __syncthreads();
+    if (chunk == 0) {
+        double2* hc = K.hcol + (int64_t)r * (K.m + 1);
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+            if (pass == 0) hc[i] = h[i];
+            else { hc[i].x += h[i].x; hc[i].y += h[i].y; }
+        }
+    }
     const int rows = (K.nd + K.nchunk - 1) / K.nchunk;
     const int r0 = chunk * rows, r1 = min(K.nd, r0 + rows);
-    __shared__ double red[8];
-    double s = 0;
+    double nrm = 0;
     for (int q = r0 + threadIdx.x; q < r1; q += blockDim.x) {
-        const double2 a = K.w[(int64_t)r * K.nd + q];
-        s += a.x * a.x + a.y * a.y;
+        double2 w = K.w[(int64_t)r * K.nd + q];
+        for (int i = 0; i <= j; ++i) {
+            const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
+            const double2 hh = h[i];
+            w.x -= v.x * hh.x - v.y * hh.y;
+            w.y -= v.x * hh.y + v.y * hh.x;
+        }
+        K.w[(int64_t)r * K.nd + q] = w;
+        nrm += w.x * w.x + w.y * w.y;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-        K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m].x = t;
+    if (pass == 1) {
+        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+            K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m].x = t;
+        }
     }
 }
 
@@ -725,12 +864,30 @@ __global__ void k_norm2(const double2* __restrict__ x, int64_t n, double* __rest
 }
 
 // ------------------------------------------------------------------ launch wrappers
+static inline int rhs_block(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
+
+template <class T>
+static size_t pass_smem_t(int pmax, int rb) { return (elem_smem_bytes<T>(pmax, 3 * rb * 4 * (pmax + 1)) + 127) & ~(size_t)127; }
+// warps (elements) per CTA: up to 4 while the per-warp shared memory fits in 200 KB
+// one CTA of 128 threads per (element, RHS block): measured faster than one warp per element
+template <class T>
+static int pass_wpc(int, int) { return 1; }
+
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
-    const size_t sm = elem_smem_bytes<T>(dm.pmax, 12 * (dm.pmax + 1));
-    k_pass1<T><<<dim3(dm.E, R), 128, sm, st>>>(dm, (const cpx<T>*)sinv, z, zsign, bt, has_bI, (cpx<T>*)xE,
-                                                (cpx<T>*)tT, done);
+    const int rb = rhs_block(R);
+    const int per = (int)pass_smem_t<T>(dm.pmax, rb), wpc = pass_wpc<T>(dm.pmax, rb);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const dim3 g((ntask + wpc - 1) / wpc);
+    const size_t sm = (size_t)per * wpc;
+    const cpx<T>* S = (const cpx<T>*)sinv;
+    switch (rb) {
+        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
+        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
+        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
+        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per);
+    }
 }
 template <class T>
 void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
@@ -740,9 +897,20 @@ void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* b
 template <class T>
 void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const void* xE_in, void* xE_out,
                   int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st) {
-    const size_t sm = elem_smem_bytes<T>(dm.pmax, 12 * (dm.pmax + 1));
-    k_pass2<T><<<dim3(dm.E, R), 128, sm, st>>>(dm, (const cpx<T>*)sinv, x2, (const cpx<T>*)xE_in, (cpx<T>*)xE_out,
-                                                recover, bt, has_bI, phi, done);
+    const int rb = rhs_block(R);
+    const int per = (int)pass_smem_t<T>(dm.pmax, rb), wpc = pass_wpc<T>(dm.pmax, rb);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const dim3 g((ntask + wpc - 1) / wpc);
+    const size_t sm = (size_t)per * wpc;
+    const cpx<T>* S = (const cpx<T>*)sinv;
+    const cpx<T>* xi = (const cpx<T>*)xE_in;
+    cpx<T>* xo = (cpx<T>*)xE_out;
+    switch (rb) {
+        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
+        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
+        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
+        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per);
+    }
 }
 template <class T>
 void launch_jump_gather(const DevModel& dm, const void* xE, const double2* x2, double2* w, int R, const int* done,
@@ -754,8 +922,15 @@ void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, d
                 int R, const int* done, cudaStream_t st) {
     const dim3 gr((dm.n_dual + 127) / 128, R);
     k_dinv<<<gr, 128, 0, st>>>(dm, v, vd, lumped, done);
-    const size_t sm = sizeof(cpx<T>) * (size_t)(4 * (dm.pmax - 1) + 8);
-    k_pre_elem<T><<<dim3(dm.E, R), 128, sm, st>>>(dm, vd, (cpx<T>*)outE, lumped, done);
+    const int rb = rhs_block(R);
+    const dim3 g(dm.E, (R + rb - 1) / rb);
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * (4 * (dm.pmax - 1) + 8);
+    switch (rb) {
+        case 8: k_pre_elem<T, 8><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        case 4: k_pre_elem<T, 4><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        case 2: k_pre_elem<T, 2><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        default: k_pre_elem<T, 1><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done);
+    }
     k_pre_rows<T><<<gr, 128, 0, st>>>(dm, (const cpx<T>*)outE, vd, m, lumped, done);
     k_dinv<<<gr, 128, 0, st>>>(dm, m, z, lumped, done);
 }
@@ -771,14 +946,31 @@ template void launch_jump_gather<float>(const DevModel&, const void*, const doub
 template void launch_pre<double>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
 template void launch_pre<float>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
 
+void launch_coarse_residual(const double2* const* Kd, const double2* const* Kl, const double2* const* Ku,
+                            const int* start, const int* row_blk, int nb, int n, const double2* x, const double2* t,
+                            double2* r, int R, const int* done, cudaStream_t st) {
+    BlockK B{Kd, Kl, Ku, start, row_blk, nb, n};
+    k_coarse_residual<<<(n + 3) / 4, 128, 0, st>>>(B, x, t, r, R, done);
+}
 void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st) {
     k_dinv<<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, x, y, 1, done);
 }
-void launch_gemv(const double2* A, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
+void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st) {
-    const int warps_per_block = 8;
-    k_gemv_c64<<<dim3((n_out + warps_per_block - 1) / warps_per_block, R), 32 * warps_per_block, 0, st>>>(
-        A, n_out, n_in, x, y, c, mode, xs, ys, done);
+    const int warps_per_block = 4;
+    const dim3 g((n_out + warps_per_block - 1) / warps_per_block);
+    const int tb = 32 * warps_per_block;
+    // right-hand sides in chunks of 8, 4, 2, 1: every FMA issued does useful work
+    for (int r0 = 0; r0 < R;) {
+        const int left = R - r0;
+        const int rb = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+#define DDH_GEMV(RBV)                                                                                         \
+        if (f32) k_gemv<float2, RBV><<<g, tb, 0, st>>>((const float2*)A, n_out, n_in, x, y, c, mode, xs, ys, r0, done); \
+        else k_gemv<double2, RBV><<<g, tb, 0, st>>>((const double2*)A, n_out, n_in, x, y, c, mode, xs, ys, r0, done);
+        switch (rb) { case 8: DDH_GEMV(8) break; case 4: DDH_GEMV(4) break; case 2: DDH_GEMV(2) break; default: DDH_GEMV(1) }
+#undef DDH_GEMV
+        r0 += rb;
+    }
 }
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
                           int nq, double2* bt, int R, cudaStream_t st) {
@@ -798,10 +990,8 @@ void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st) {
     const dim3 gv((K.nd + 255) / 256, K.R), gc(K.nchunk, K.R);
     for (int pass = 0; pass < 2; ++pass) {
         k_dots<<<gc, 256, 0, st>>>(K);
-        k_dots_reduce<<<K.R, 256, 0, st>>>(K, pass);
-        k_axpy<<<gv, 256, 0, st>>>(K);
+        k_axpy<<<gc, 256, 0, st>>>(K, pass);
     }
-    k_norm_partial<<<gc, 256, 0, st>>>(K);
     k_normalize<<<gv, 256, 0, st>>>(K);
     k_givens<<<1, ((K.R + 31) / 32) * 32, 0, st>>>(K);
 }
@@ -821,15 +1011,33 @@ void launch_norm2(const double2* x, int64_t n, double* out, int R, cudaStream_t 
     k_norm2<<<dim3(64, R), 256, 0, st>>>(x, n, out);
 }
 
+void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st) {
+    k_conf_scatter<<<dim3((unsigned)((dm.n_local + 255) / 256), R), 256, 0, st>>>(dm, x, out);
+}
+void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, double sign, int R, cudaStream_t st) {
+    k_conf_gather_vec<<<dim3((dm.n_conf + 255) / 256, R), 256, 0, st>>>(dm, x, out, sign);
+}
+void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st) {
+    k_inject<<<dim3((dm.n_conf + 255) / 256, R), 256, 0, st>>>(dm, rc, b);
+}
+void launch_readback(const DevModel& dm, const double2* phi, double2* z, int R, cudaStream_t st) {
+    k_readback<<<dim3((dm.n_conf + 255) / 256, R), 256, 0, st>>>(dm, phi, z);
+}
+
 size_t pass_smem(int pmax, bool fp64) {
-    return fp64 ? elem_smem_bytes<double>(pmax, 12 * (pmax + 1)) : elem_smem_bytes<float>(pmax, 12 * (pmax + 1));
+    return fp64 ? pass_smem_t<double>(pmax, 8) : pass_smem_t<float>(pmax, 8);
+}
+template <class T, int RB>
+static void set_pass_limits(int pmax) {
+    const int b = (int)pass_smem_t<T>(pmax, RB) * pass_wpc<T>(pmax, RB);
+    cudaFuncSetAttribute(k_pass1<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    cudaFuncSetAttribute(k_pass2<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 void set_smem_limits(int pmax) {
-    const int a = (int)pass_smem(pmax, true), b = (int)pass_smem(pmax, false);
-    cudaFuncSetAttribute(k_pass1<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-    cudaFuncSetAttribute(k_pass2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
-    cudaFuncSetAttribute(k_pass1<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    cudaFuncSetAttribute(k_pass2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    set_pass_limits<double, 1>(pmax); set_pass_limits<double, 2>(pmax);
+    set_pass_limits<double, 4>(pmax); set_pass_limits<double, 8>(pmax);
+    set_pass_limits<float, 1>(pmax); set_pass_limits<float, 2>(pmax);
+    set_pass_limits<float, 4>(pmax); set_pass_limits<float, 8>(pmax);
     cudaFuncSetAttribute(k_elem_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
 }
 

@@ -18,6 +18,18 @@
 
 namespace ddh {
 
+// Thread group executing one element: the whole CTA, or one warp of it.
+struct CtaGroup {
+    __device__ __forceinline__ int t() const { return threadIdx.x; }
+    __device__ __forceinline__ int n() const { return blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+struct WarpGroup {
+    __device__ __forceinline__ int t() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int n() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
 template <class T>
 struct ElemSmem {
     T* Mt;          // N*N
@@ -65,16 +77,16 @@ __device__ inline ElemSmem<T> carve(char* base, int pmax, int nvec) {
     return s;
 }
 
-template <class T>
-__device__ inline void load_tables(const DevModel& dm, int e, const ElemSmem<T>& s) {
+template <class T, class G>
+__device__ inline void load_tables(const G& g, const DevModel& dm, int e, const ElemSmem<T>& s) {
     const int t = dm.ptab[e];
     const int p = dm.p[e], N = p + 1, n = p - 1;
     const double* Mt = dm.Mt_all + dm.tab_Mt[t];
     const double* V = dm.V_all + dm.tab_V[t];
     const double* mu = dm.mu_all + dm.tab_mu[t];
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.Mt[i] = (T)Mt[i];
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) s.V[i] = (T)V[i];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s.mu[i] = (T)mu[i];
+    for (int i = g.t(); i < N * N; i += g.n()) s.Mt[i] = (T)Mt[i];
+    for (int i = g.t(); i < n * n; i += g.n()) s.V[i] = (T)V[i];
+    for (int i = g.t(); i < n; i += g.n()) s.mu[i] = (T)mu[i];
 }
 
 __device__ __forceinline__ int cand_list(int a, int p, int* c) {
@@ -131,11 +143,11 @@ __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T
 // Interior coupling of the frame values: coupling = Mt_BV X + Y Mt_VB with
 // X = Phi_VB (I + c M_b) + c Phi_VV Mt_VB (2 x n),  Y = (I + c M_b) Phi_BV (n x 2).
 // Writes sign * coupling into rrow (interior rows 0,1) and rcol (interior cols 0,1).
-template <class T>
-__device__ inline void cross_coupling(const ElemSmem<T>& s, int p, T ce, T sign) {
+template <class T, class G>
+__device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T ce, T sign) {
     const int N = p + 1, n = p - 1;
     // X into rho (2 x n), Y into kap (stored [v][a], 2 x n)
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int v = idx / n, be = idx % n;
         // X[v][be] = Phi[v][be+2] + c sum_b Phi[v][b+2] Mt[b+2][be+2] + c sum_w Phi[v][w] Mt[w][be+2]
         cpx<T> x = s.tile[v + N * (be + 2)];
@@ -156,8 +168,8 @@ __device__ inline void cross_coupling(const ElemSmem<T>& s, int p, T ce, T sign)
         fma_r(y, ce, acc2);
         s.kap[v * n + al] = y;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    g.sync();
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int i = idx / n, q = idx % n;
         // row part: interior row i (bubble i+2): sum_v Mt[i+2][v] X[v][q]
         cpx<T> r = mk<T>(0, 0);
@@ -168,14 +180,14 @@ __device__ inline void cross_coupling(const ElemSmem<T>& s, int p, T ce, T sign)
         for (int v = 0; v < 2; ++v) fma_r(c, s.Mt[v * N + i + 2], s.kap[v * n + q]);
         s.rcol[i * n + q] = sign * c;
     }
-    __syncthreads();
+    g.sync();
 }
 
 // spec += V^T R V for R = rows {0,1} from rrow plus cols {0,1} from rcol (interior indexing).
-template <class T>
-__device__ inline void spec_from_cross(const ElemSmem<T>& s, int n, bool accumulate) {
+template <class T, class G>
+__device__ inline void spec_from_cross(const G& g, const ElemSmem<T>& s, int n, bool accumulate) {
     // rho_i[be] = sum_b r_i[b] V[b][be];  kap_j[al] = sum_a V[a][al] c_j[a]
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int i = idx / n, q = idx % n;
         cpx<T> r = mk<T>(0, 0), c = mk<T>(0, 0);
         for (int b = (q & 1); b < n; b += 2) {          // V[b][q] != 0 only for equal parity
@@ -185,8 +197,8 @@ __device__ inline void spec_from_cross(const ElemSmem<T>& s, int n, bool accumul
         s.rho[i * n + q] = r;
         s.kap[i * n + q] = c;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    g.sync();
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int al = idx / n, be = idx % n;
         cpx<T> v = accumulate ? s.spec[idx] : mk<T>(0, 0);
         for (int i = 0; i < 2 && i < n; ++i) {
@@ -195,27 +207,27 @@ __device__ inline void spec_from_cross(const ElemSmem<T>& s, int n, bool accumul
         }
         s.spec[idx] = v;
     }
-    __syncthreads();
+    g.sync();
 }
 
 // spec /= D,  D[al][be] = mu_al + mu_be + c mu_al mu_be
-template <class T>
-__device__ inline void spec_divide(const ElemSmem<T>& s, int n, T ce) {
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+template <class T, class G>
+__device__ inline void spec_divide(const G& g, const ElemSmem<T>& s, int n, T ce) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int al = idx / n, be = idx % n;
         const T ma = s.mu[al], mb = s.mu[be];
         const T D = ma + mb + ce * ma * mb;
         const T inv = (T)1 / D;
         s.spec[idx] = inv * s.spec[idx];
     }
-    __syncthreads();
+    g.sync();
 }
 
 // cross output of Y = V spec V^T: rows 0,1 into rrow, cols 0,1 into rcol
-template <class T>
-__device__ inline void cross_from_spec(const ElemSmem<T>& s, int n) {
+template <class T, class G>
+__device__ inline void cross_from_spec(const G& g, const ElemSmem<T>& s, int n) {
     // w_i[be] = sum_al V[i][al] spec[al][be] -> rho ; z_j[al] = sum_be spec[al][be] V[j][be] -> kap
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int i = idx / n, q = idx % n;
         cpx<T> w = mk<T>(0, 0), z = mk<T>(0, 0);
         for (int al = (i & 1); al < n; al += 2) fma_r(w, s.V[i * n + al], s.spec[al * n + q]);
@@ -223,8 +235,8 @@ __device__ inline void cross_from_spec(const ElemSmem<T>& s, int n) {
         s.rho[i * n + q] = w;
         s.kap[i * n + q] = z;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    g.sync();
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int i = idx / n, q = idx % n;
         cpx<T> r = mk<T>(0, 0), c = mk<T>(0, 0);
         for (int be = (q & 1); be < n; be += 2) fma_r(r, s.V[q * n + be], s.rho[i * n + be]);
@@ -232,64 +244,64 @@ __device__ inline void cross_from_spec(const ElemSmem<T>& s, int n) {
         s.rrow[i * n + q] = r;      // Y[i][q]
         s.rcol[i * n + q] = c;      // Y[q][i]
     }
-    __syncthreads();
+    g.sync();
 }
 
 // spec = V^T R V for a full interior R held in tmp (n x n, [a][b] = interior (a, b)), using
 // spec as the intermediate.  Even/odd structure of V halves the sums.
-template <class T>
-__device__ inline void spec_from_full(const ElemSmem<T>& s, int n) {
+template <class T, class G>
+__device__ inline void spec_from_full(const G& g, const ElemSmem<T>& s, int n) {
     // spec[al][b] = sum_a V[a][al] R[a][b]
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int al = idx / n, b = idx % n;
         cpx<T> v = mk<T>(0, 0);
         for (int a = (al & 1); a < n; a += 2) fma_r(v, s.V[a * n + al], s.tmp[a * n + b]);
         s.spec[idx] = v;
     }
-    __syncthreads();
+    g.sync();
     // tmp[al][be] = sum_b spec[al][b] V[b][be]
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int al = idx / n, be = idx % n;
         cpx<T> v = mk<T>(0, 0);
         for (int b = (be & 1); b < n; b += 2) fma_r(v, s.V[b * n + be], s.spec[al * n + b]);
         s.tmp[idx] = v;
     }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) s.spec[idx] = s.tmp[idx];
-    __syncthreads();
+    g.sync();
+    for (int idx = g.t(); idx < n * n; idx += g.n()) s.spec[idx] = s.tmp[idx];
+    g.sync();
 }
 
 // tmp = V spec V^T (full interior output, [a][b])
-template <class T>
-__device__ inline void full_from_spec(const ElemSmem<T>& s, int n) {
+template <class T, class G>
+__device__ inline void full_from_spec(const G& g, const ElemSmem<T>& s, int n) {
     // tmp[a][be] = sum_al V[a][al] spec[al][be]
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int a = idx / n, be = idx % n;
         cpx<T> v = mk<T>(0, 0);
         for (int al = (a & 1); al < n; al += 2) fma_r(v, s.V[a * n + al], s.spec[al * n + be]);
         s.tmp[idx] = v;
     }
-    __syncthreads();
+    g.sync();
     // spec[a][b] = sum_be tmp[a][be] V[b][be]
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int a = idx / n, b = idx % n;
         cpx<T> v = mk<T>(0, 0);
         for (int be = (b & 1); be < n; be += 2) fma_r(v, s.V[b * n + be], s.tmp[a * n + be]);
         s.spec[idx] = v;
     }
-    __syncthreads();
+    g.sync();
 }
 
 // write cross values (rrow/rcol) into the interior of the tile, scaled by sign
-template <class T>
-__device__ inline void cross_to_tile(const ElemSmem<T>& s, int p, T sign) {
+template <class T, class G>
+__device__ inline void cross_to_tile(const G& g, const ElemSmem<T>& s, int p, T sign) {
     const int N = p + 1, n = p - 1;
-    for (int idx = threadIdx.x; idx < 2 * n; idx += blockDim.x) {
+    for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
         const int i = idx / n, q = idx % n;
         s.tile[(i + 2) + N * (q + 2)] = sign * s.rrow[i * n + q];
         if (q >= 2) s.tile[(q + 2) + N * (i + 2)] = sign * s.rcol[i * n + q];
     }
-    __syncthreads();
+    g.sync();
 }
 
 }  // namespace ddh

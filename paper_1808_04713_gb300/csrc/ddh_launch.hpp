@@ -33,8 +33,11 @@ template <class T>
 void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, double2* m, double2* z, int lumped,
                 int R, const int* done, cudaStream_t st);
 
+void launch_coarse_residual(const double2* const* Kd, const double2* const* Kl, const double2* const* Ku,
+                            const int* start, const int* row_blk, int nb, int n, const double2* x, const double2* t,
+                            double2* r, int R, const int* done, cudaStream_t st);
 void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st);
-void launch_gemv(const double2* A, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
+void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st);
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
                           int nq, double2* bt, int R, cudaStream_t st);
@@ -47,6 +50,10 @@ void launch_store(const KrylovDev& K, cudaStream_t st);
 void launch_update(const double2* Zb, const double2* y, const int* nit, double2* nu, int nd, int m, int R, cudaStream_t st);
 void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st);
 void launch_norm2(const double2* x, int64_t n, double* out, int R, cudaStream_t st);
+void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st);
+void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, double sign, int R, cudaStream_t st);
+void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st);
+void launch_readback(const DevModel& dm, const double2* phi, double2* z, int R, cudaStream_t st);
 size_t pass_smem(int pmax, bool fp64);
 void set_smem_limits(int pmax);
 

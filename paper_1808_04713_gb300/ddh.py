@@ -29,7 +29,8 @@ class DDHError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
-                ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32)]
+                ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
+                ("coarse_fp32", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -66,6 +67,8 @@ _SIGS = {
     "ddh_table_affine": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_void_p]),
     "ddh_table_fdm": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
     "ddh_table_gauss": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p]),
+    "ddh_host_factor": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                  C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -239,3 +242,20 @@ def table_gauss(m: int):
     if st:
         raise DDHError(st, "table_gauss")
     return x, w
+
+
+def host_factor(base_n, leaves, p, k, eps, l_override: int = 0):
+    """Host-only setup + factorisation; returns (sizes dict, seconds, l)."""
+    lv = np.ascontiguousarray(leaves, dtype=np.int32)
+    pp = np.ascontiguousarray(p, dtype=np.int32)
+    ee = np.ascontiguousarray(eps, dtype=np.float64)
+    sizes = np.zeros(8, np.int64)
+    secs = np.zeros(5)
+    l = C.c_int32()
+    st = load_library().ddh_host_factor(int(base_n), lv.ctypes.data, pp.ctypes.data, int(lv.shape[0]), float(k),
+                                        ee.ctypes.data, int(l_override), sizes.ctypes.data, secs.ctypes.data,
+                                        C.byref(l))
+    if st:
+        raise DDHError(st, "host_factor")
+    keys = ["n_local", "n_dual", "n_coarse", "n_conforming", "n_e1", "n_t", "blocks", "max_block"]
+    return dict(zip(keys, sizes.tolist())), secs, l.value
