@@ -148,13 +148,22 @@ ddh_status ddh_solve_host(ddh_ctx* ctx, const void* b_host, void* u_host, int32_
 ddh_status ddh_adjoint_solve(ddh_ctx* ctx, const void* g_dev, void* lam_dev, int32_t R,
                              double tol, ddh_rhs_stats* stats);
 
-/* Gradient of J = sum_r Re(<lambda_r, ...>) style adjoint objectives with respect to the
- * element permittivities: grad_eps[e] = sum_r Re( lambda_r^T (dA/deps_e) u_r ) * (-1), i.e.
- * dJ/deps_e = k^2 Re( lambda_e^T M_e u_e ) summed over r, with M_e = (h_e/2)^2 M (x) M the
- * element mass matrix, for lambda solving A^T lambda = dJ/du (complex-symmetric A).
- * u_dev, lam_dev: device [R][n_local]; grad_eps_dev: device double [n_elem] (written). */
+/* Gradient accumulation with respect to the element permittivities (no paper counterpart:
+ * the paper has no adjoint; this differentiates its discretisation).  For a real objective
+ * J(u) of the solution, PyTorch passes G = conj(2 dJ/du); since A is complex symmetric the
+ * transposed adjoint system A^T lam = conj(G) is an ordinary solve (ddh_solve of conj(G)), and
+ *   dJ/deps_e = -Re(lam^T (dA/deps_e) u) = k^2 (h_e/2)^2 Re(lam_e^T M_e u_e),
+ * M_e = M (x) M the element mass.  u_dev, lam_dev: device complex128 [R][n_local] (N basis),
+ * summed over r.  grad_eps_dev: device double [n_elem] (overwritten). */
 ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, int32_t R,
                         double* grad_eps_dev);
+
+/* dJ/dk for the plane-wave problems of ddh_rhs_planewave (same theta, R):
+ *   -Re(lam^T (dA/dk) u) + Re(lam^T db/dk), dA/dk = sum_e -2 k eps_e (h_e/2)^2 M_e plus
+ * -i h_e/2 times the Robin side matrices, db/dk the load of dg/dk.  grad_k_host: one double
+ * (sum over r). */
+ddh_status ddh_grad_k(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, const double* theta,
+                      int32_t R, double* grad_k_host);
 
 /* Point evaluation u(x_i) of local vectors (adjoint = 0), or its transpose, the injection
  * of point weights into a local vector (adjoint = 1).  xy: host [n][2] inside [0,1]^2.

@@ -1140,14 +1140,83 @@ ddh_status ddh_adjoint_solve(ddh_ctx* ctx, const void* g_dev, void* lam_dev, int
     return st;
 }
 
-ddh_status ddh_grad_eps(ddh_ctx* ctx, const void*, const void*, int32_t, double*) {
+ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, int32_t R, double* grad_eps_dev) {
     if (!ctx) return DDH_ERR_INVALID_ARG;
-    return fail(ctx, DDH_ERR_NOT_READY, "ddh_grad_eps is not available in this build");
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!u_dev || !lam_dev || !grad_eps_dev || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    void *ut, *lt;
+    ddh_status st;
+    const size_t bytes = sizeof(double2) * (size_t)R * ctx->dm.n_local;
+    if ((st = get_work(ctx, "gr_u", bytes, &ut))) return st;
+    if ((st = get_work(ctx, "gr_l", bytes, &lt))) return st;
+    launch_basis(ctx->dm, (const double2*)u_dev, (double2*)ut, 0, R, ctx->stream);
+    launch_basis(ctx->dm, (const double2*)lam_dev, (double2*)lt, 0, R, ctx->stream);
+    launch_grad_elem(ctx->dm, (const double2*)ut, (const double2*)lt, R, ctx->m.k, 0, grad_eps_dev, ctx->stream);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DDH_OK;
 }
 
-ddh_status ddh_eval_points(ddh_ctx* ctx, const double*, int32_t, int32_t, const void*, void*, int32_t) {
+ddh_status ddh_grad_k(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, const double* theta, int32_t R,
+                      double* grad_k_host) {
     if (!ctx) return DDH_ERR_INVALID_ARG;
-    return fail(ctx, DDH_ERR_NOT_READY, "ddh_eval_points is not available in this build");
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!u_dev || !lam_dev || !theta || !grad_k_host || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    void *ut, *lt, *db, *pe, *th;
+    ddh_status st;
+    const DevModel& d = ctx->dm;
+    const size_t bytes = sizeof(double2) * (size_t)R * d.n_local;
+    if ((st = get_work(ctx, "gr_u", bytes, &ut))) return st;
+    if ((st = get_work(ctx, "gr_l", bytes, &lt))) return st;
+    if ((st = get_work(ctx, "gr_db", bytes, &db))) return st;
+    if ((st = get_work(ctx, "gr_pe", sizeof(double) * (size_t)2 * d.E, &pe))) return st;
+    if ((st = get_work(ctx, "theta", sizeof(double) * R, &th))) return st;
+    CK(cudaMemcpyAsync(th, theta, sizeof(double) * R, cudaMemcpyHostToDevice, ctx->stream));
+    launch_basis(d, (const double2*)u_dev, (double2*)ut, 0, R, ctx->stream);
+    launch_basis(d, (const double2*)lam_dev, (double2*)lt, 0, R, ctx->stream);
+    // - sum_e Re(lam^T dA_e/dk u)
+    launch_grad_elem(d, (const double2*)ut, (const double2*)lt, R, ctx->m.k, 1, (double*)pe, ctx->stream);
+    // + Re(lam^T db/dk): db/dk on the interpolatory basis, then its bilinear form with lam
+    launch_rhs_planewave(d, (const double*)th, ctx->m.k, ctx->gx, ctx->gw, ctx->nq, (double2*)db, R, ctx->stream, 1);
+    ctx->launches += 4;
+    std::vector<double> per(d.E);
+    std::vector<double2> dbh((size_t)R * d.n_local), lh((size_t)R * d.n_local);
+    CK(cudaMemcpyAsync(per.data(), pe, sizeof(double) * d.E, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(dbh.data(), db, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(lh.data(), lt, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double g = 0;
+    for (double v : per) g -= v;
+    for (size_t i = 0; i < dbh.size(); ++i) g += lh[i].x * dbh[i].x - lh[i].y * dbh[i].y;
+    *grad_k_host = g;
+    return DDH_OK;
+}
+
+ddh_status ddh_eval_points(ddh_ctx* ctx, const double* xy, int32_t n, int32_t R, const void* in_dev, void* out_dev,
+                           int32_t adjoint) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!xy || n <= 0 || R <= 0 || !in_dev || !out_dev) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    std::vector<int> pe(n);
+    std::vector<double> pu(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        pe[i] = locate_point(ctx->m, xy[2 * i], xy[2 * i + 1], pu[2 * i], pu[2 * i + 1]);
+        if (pe[i] < 0) return fail(ctx, DDH_ERR_INVALID_ARG, "point outside the unit square");
+    }
+    void *dpe, *dpu;
+    ddh_status st;
+    if ((st = get_work(ctx, "pt_e", sizeof(int) * n, &dpe))) return st;
+    if ((st = get_work(ctx, "pt_u", sizeof(double) * 2 * n, &dpu))) return st;
+    CK(cudaMemcpyAsync(dpe, pe.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dpu, pu.data(), sizeof(double) * 2 * n, cudaMemcpyHostToDevice, ctx->stream));
+    if (adjoint) CK(cudaMemsetAsync(out_dev, 0, sizeof(double2) * (size_t)R * ctx->dm.n_local, ctx->stream));
+    launch_points(ctx->dm, (const int*)dpe, (const double*)dpu, n, R, (const double2*)in_dev, (double2*)out_dev, adjoint,
+                  ctx->stream);
+    ctx->launches++;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DDH_OK;
 }
 
 ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R, double* out_host) {

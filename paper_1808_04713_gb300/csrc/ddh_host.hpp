@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 namespace ddh {
@@ -61,6 +62,7 @@ struct Model {
     std::vector<Elem> el;
     double k = 0;
     int l = 0;
+    std::unordered_map<uint64_t, int> leaf_of;    // (level, i, j) key -> element
     // tables
     std::vector<PTable> tabs;
     std::vector<int> ptab_of_p;   // p -> table index
@@ -115,6 +117,8 @@ struct Model {
 
 bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, int n_elem,
                  std::string& err);
+// element containing (x, y) in [0,1]^2 and the canonical coordinates (u1, u2) in [-1,1]^2
+int locate_point(const Model& m, double x, double y, double& u1, double& u2);
 void set_coefficients(Model& m, double k, const double* eps);
 int dispersion_l(const Model& m);
 bool classify(Model& m, int l, std::string& err);

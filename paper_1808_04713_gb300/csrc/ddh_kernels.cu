@@ -482,7 +482,7 @@ __global__ void k_pre_rows(DevModel dm, const cpx<T>* __restrict__ outE, const d
 // b~[slot(s,m)] = int N~_m(t) g(x(t)) (h/2) dt by Gauss-Legendre quadrature.
 __global__ void k_rhs_planewave(DevModel dm, const double* __restrict__ theta, double k,
                                 const double* __restrict__ gx, const double* __restrict__ gw, int nq,
-                                double2* __restrict__ bt) {
+                                double2* __restrict__ bt, int dk) {
     const int e = blockIdx.x, r = blockIdx.y;
     const int p = dm.p[e], N = p + 1;
     const double x0 = dm.geo[3 * e], y0 = dm.geo[3 * e + 1], h = dm.geo[3 * e + 2];
@@ -522,11 +522,20 @@ __global__ void k_rhs_planewave(DevModel dm, const double* __restrict__ theta, d
             }
             // g = (i k n.d - i k) exp(i k (x ct + y sn))
             double sp, cp;
-            sincos(k * (X * ct + Y * sn), &sp, &cp);
-            const double fac = k * (nd - 1.0);          // g = i fac (cp + i sp) = (-fac sp, fac cp)
+            const double xd = X * ct + Y * sn;
+            sincos(k * xd, &sp, &cp);
             const double wq = gw[q] * Nm * 0.5 * h;
-            sx += wq * (-fac * sp);
-            sy += wq * (fac * cp);
+            if (!dk) {
+                const double fac = k * (nd - 1.0);      // g = i fac (cp + i sp) = (-fac sp, fac cp)
+                sx += wq * (-fac * sp);
+                sy += wq * (fac * cp);
+            } else {
+                // dg/dk = i (nd - 1) e + i k (nd - 1) (i xd) e = (nd - 1) (i - k xd) e
+                const double f = nd - 1.0;
+                // (i - k xd)(cp + i sp) = (-sp - k xd cp) + i (cp - k xd sp)
+                sx += wq * f * (-sp - k * xd * cp);
+                sy += wq * f * (cp - k * xd * sp);
+            }
         }
         int slot;
         switch (s) { case 0: slot = 1 + N * m; break; case 1: slot = N * m; break; case 2: slot = m + N; break; default: slot = m; }
@@ -602,6 +611,98 @@ __global__ void k_conf_gather(DevModel dm, const double2* __restrict__ x, double
         double s = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
         atomicAdd(&norm2[r], s);
+    }
+}
+
+// ------------------------------------------------------------------ differentiation (FP64)
+// Per element e: s_e = sum_r lam_r^T (dA_e) u_r on the interpolatory basis (B (x) B is
+// orthogonal and involutory, so the bilinear form is basis independent), with
+//   mode 0: dA_e = (h/2)^2 Mt (x) Mt               -> grad_eps[e] = k^2 Re(s_e)
+//   mode 1: dA_e = dA_e/dk (mass -2 k eps (h/2)^2 Mt (x) Mt, Robin -i h/2 per boundary side)
+// Writes Re(s_e) scaled as documented into out[e].
+__global__ void __launch_bounds__(128) k_grad_elem(DevModel dm, const double2* __restrict__ ut,
+                                                   const double2* __restrict__ lt, int R, double k, int mode,
+                                                   double* __restrict__ out) {
+    extern __shared__ __align__(16) char smem[];
+    const CtaGroup g;
+    const int e = blockIdx.x;
+    const int p = dm.p[e], N = p + 1;
+    ElemSmem<double> s = carve<double>(smem, dm.pmax, 0);
+    load_tables<double>(g, dm, e, s);
+    const double h = dm.geo[3 * e + 2], eps = -dm.c[e] / (k * k * 0.25 * h * h);
+    double ce, gam[4];
+    if (mode == 0) { ce = 0.25 * h * h; for (int q = 0; q < 4; ++q) gam[q] = 0; }
+    else { ce = -2.0 * k * eps * 0.25 * h * h; for (int q = 0; q < 4; ++q) gam[q] = dm.gam[4 * e + q] != 0.0 ? -0.5 * h : 0.0; }
+    __shared__ double red[4];
+    double acc = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
+        g.sync();
+        for (int i = g.t(); i < N * N; i += g.n()) { const double2 v = ut[base + i]; s.tile[i] = mk<double>(v.x, v.y); }
+        g.sync();
+        for (int idx = g.t(); idx < N * N; idx += g.n()) {
+            const cpx<double> au = apply_A_entry<double>(s.tile, s.Mt, p, ce, gam, idx % N, idx / N, false, true);
+            const double2 l = lt[base + idx];
+            acc += l.x * au.x - l.y * au.y;          // Re(l * au)
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        out[e] = mode == 0 ? k * k * t : t;
+    }
+}
+
+// integrated-Legendre basis N_0..N_p at t (orthonormal Legendre recurrence, N = S p)
+__device__ inline void n_basis(int p, double t, double* Nv) {
+    double pm2 = 0.70710678118654752440, pm1 = 1.2247448713915890491 * t;
+    Nv[0] = pm2;
+    if (p >= 1) Nv[1] = t * 0.70710678118654752440;
+    for (int m = 2; m <= p; ++m) {
+        const double v = sqrt((2.0 * m + 1) * (2.0 * m - 1)) / m * t * pm1 - (m - 1.0) / m * sqrt((2.0 * m + 1) / (2.0 * m - 3)) * pm2;
+        const double gm = 1.0 / sqrt((2.0 * m + 1) * (2.0 * m - 1));
+        const double gm1 = 1.0 / sqrt((2.0 * m - 1) * (2.0 * m - 3));
+        Nv[m] = gm * v - gm1 * pm2;        // g_m p_m - g_{m-1} p_{m-2}
+        pm2 = pm1;
+        pm1 = v;
+    }
+}
+
+// u(x_i) = N(u1)^T Phi N(u2) for points with element, canonical coordinates (N basis input).
+// adjoint: out[e][a][b] += w_i N_a(u1) N_b(u2) (out zeroed by the caller).  One warp per point.
+__global__ void k_points(DevModel dm, const int* __restrict__ pe, const double* __restrict__ pu, int P, int R,
+                         const double2* __restrict__ in, double2* __restrict__ out, int adjoint) {
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    __shared__ double Nv[8][2][33];
+    const int w = threadIdx.x >> 5;
+    if (i >= P) return;
+    const int e = pe[i], p = dm.p[e], N = p + 1;
+    if (lane == 0) n_basis(p, pu[2 * i], Nv[w][0]);
+    if (lane == 1) n_basis(p, pu[2 * i + 1], Nv[w][1]);
+    __syncwarp();
+    for (int r = 0; r < R; ++r) {
+        const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
+        if (!adjoint) {
+            double sx = 0, sy = 0;
+            for (int idx = lane; idx < N * N; idx += 32) {
+                const double f = Nv[w][0][idx % N] * Nv[w][1][idx / N];
+                const double2 v = in[base + idx];
+                sx += f * v.x; sy += f * v.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
+            if (lane == 0) out[(int64_t)r * P + i] = make_double2(sx, sy);
+        } else {
+            const double2 wi = in[(int64_t)r * P + i];
+            for (int idx = lane; idx < N * N; idx += 32) {
+                const double f = Nv[w][0][idx % N] * Nv[w][1][idx / N];
+                atomicAdd(&out[base + idx].x, f * wi.x);
+                atomicAdd(&out[base + idx].y, f * wi.y);
+            }
+        }
     }
 }
 
@@ -973,8 +1074,16 @@ void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x,
     }
 }
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
-                          int nq, double2* bt, int R, cudaStream_t st) {
-    k_rhs_planewave<<<dim3(dm.E, R), 128, 0, st>>>(dm, theta, k, gx, gw, nq, bt);
+                          int nq, double2* bt, int R, cudaStream_t st, int dk) {
+    k_rhs_planewave<<<dim3(dm.E, R), 128, 0, st>>>(dm, theta, k, gx, gw, nq, bt, dk);
+}
+void launch_grad_elem(const DevModel& dm, const double2* ut, const double2* lt, int R, double k, int mode, double* out,
+                      cudaStream_t st) {
+    k_grad_elem<<<dm.E, 128, elem_smem_bytes<double>(dm.pmax, 0), st>>>(dm, ut, lt, R, k, mode, out);
+}
+void launch_points(const DevModel& dm, const int* pe, const double* pu, int P, int R, const double2* in, double2* out,
+                   int adjoint, cudaStream_t st) {
+    k_points<<<(P + 7) / 8, 256, 0, st>>>(dm, pe, pu, P, R, in, out, adjoint);
 }
 void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st) {
     k_basis<<<dim3(dm.E, R), 128, 0, st>>>(dm, x, y, conj_in);
@@ -1039,6 +1148,7 @@ void set_smem_limits(int pmax) {
     set_pass_limits<float, 1>(pmax); set_pass_limits<float, 2>(pmax);
     set_pass_limits<float, 4>(pmax); set_pass_limits<float, 8>(pmax);
     cudaFuncSetAttribute(k_elem_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
+    cudaFuncSetAttribute(k_grad_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
 }
 
 }  // namespace ddh

@@ -111,7 +111,7 @@ __device__ __forceinline__ T kt(int a, int c) {
 // (A Phi)[a][b] from the tile; gam[s] = imaginary part of gamma_eff on side s (0 if interior).
 template <class T>
 __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ce, const T* gam,
-                                        int a, int b, bool stiff_only) {
+                                        int a, int b, bool stiff_only, bool no_stiff = false) {
     const int N = p + 1;
     int ca[6], cb[6];
     const int na = cand_list(a, p, ca), nb = cand_list(b, p, cb);
@@ -122,7 +122,7 @@ __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T
         for (int j = 0; j < nb; ++j) {
             const int d = cb[j];
             const T Mbd = Mt[b * N + d];
-            T w = Kac * Mbd + Mac * kt<T>(b, d);
+            T w = no_stiff ? (T)0 : Kac * Mbd + Mac * kt<T>(b, d);
             if (!stiff_only) w += ce * Mac * Mbd;
             if (w != (T)0) fma_r(acc, w, tile[c + N * d]);
         }

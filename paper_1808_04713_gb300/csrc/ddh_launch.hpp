@@ -40,7 +40,11 @@ void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const 
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st);
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
-                          int nq, double2* bt, int R, cudaStream_t st);
+                          int nq, double2* bt, int R, cudaStream_t st, int dk = 0);
+void launch_grad_elem(const DevModel& dm, const double2* ut, const double2* lt, int R, double k, int mode, double* out,
+                      cudaStream_t st);
+void launch_points(const DevModel& dm, const int* pe, const double* pu, int P, int R, const double2* in, double2* out,
+                   int adjoint, cudaStream_t st);
 void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st);
 void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st);
 void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st);

@@ -69,6 +69,7 @@ bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, 
         if (!lookup.emplace(cell_key(E.lev, E.i, E.j), e).second) { err = "duplicate leaf"; return false; }
         area += (unsigned long long)(s * s);
     }
+    m.leaf_of = lookup;
     const unsigned long long full = (unsigned long long)((int64_t)base_n << maxlev) * ((int64_t)base_n << maxlev);
     if (area != full) { err = "leaves do not tile the unit square"; return false; }
     for (int e = 0; e < n_elem; ++e) {      // no leaf may contain another leaf
@@ -152,6 +153,22 @@ bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, 
         ed.Y2 = ed.side < 2 ? (E.Y0 + E.Y1) : (ed.side == 2 ? 2 * E.Y0 : 2 * E.Y1);
     }
     return true;
+}
+
+int locate_point(const Model& m, double x, double y, double& u1, double& u2) {
+    if (!(x >= 0.0 && x <= 1.0 && y >= 0.0 && y <= 1.0)) return -1;
+    for (int L = 0; L <= m.maxlev; ++L) {
+        const int64_t n = (int64_t)m.base_n << L;
+        const int64_t i = std::min<int64_t>(n - 1, (int64_t)std::floor(x * (double)n));
+        const int64_t j = std::min<int64_t>(n - 1, (int64_t)std::floor(y * (double)n));
+        auto it = m.leaf_of.find(cell_key(L, i, j));
+        if (it == m.leaf_of.end()) continue;
+        const Elem& E = m.el[it->second];
+        u1 = 2.0 * (x - E.x0) / E.h - 1.0;
+        u2 = 2.0 * (y - E.y0) / E.h - 1.0;
+        return it->second;
+    }
+    return -1;
 }
 
 void set_coefficients(Model& m, double k, const double* eps) {

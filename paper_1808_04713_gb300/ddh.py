@@ -59,6 +59,7 @@ _SIGS = {
     "ddh_adjoint_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
     "ddh_grad_eps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_eval_points": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ddh_grad_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_primal_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
     "ddh_profile_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
@@ -199,6 +200,36 @@ class DDH:
         st = (RhsStats * R)()
         self._check(self.lib.ddh_adjoint_solve(self.h, _ptr(g), _ptr(lam), R, float(tol), C.cast(st, C.c_void_p)))
         return lam, list(st)
+
+    def grad_eps(self, u, lam):
+        """dJ/deps_e = k^2 (h_e/2)^2 Re(lam_e^T M_e u_e) summed over right-hand sides."""
+        g = self.torch.zeros(self.n_elem, dtype=self.torch.float64, device=f"cuda:{self.device}")
+        R = u.shape[0]
+        self._check(self.lib.ddh_grad_eps(self.h, _ptr(u.contiguous()), _ptr(lam.contiguous()), R, _ptr(g)))
+        return g
+
+    def grad_k(self, u, lam, thetas) -> float:
+        th = np.ascontiguousarray(np.atleast_1d(thetas), dtype=np.float64)
+        out = C.c_double()
+        self._check(self.lib.ddh_grad_k(self.h, _ptr(u.contiguous()), _ptr(lam.contiguous()), th.ctypes.data,
+                                        int(th.size), C.byref(out)))
+        return out.value
+
+    def eval_points(self, xy, u):
+        """u(x_i) for points xy [n, 2]; u: [R, n_local] -> [R, n] complex."""
+        pts = np.ascontiguousarray(xy, dtype=np.float64)
+        R = u.shape[0]
+        out = self.torch.zeros((R, pts.shape[0]), dtype=self.torch.complex128, device=f"cuda:{self.device}")
+        self._check(self.lib.ddh_eval_points(self.h, pts.ctypes.data, pts.shape[0], R, _ptr(u.contiguous()), _ptr(out), 0))
+        return out
+
+    def inject_points(self, xy, w):
+        """Transpose of eval_points: w [R, n] -> local vector [R, n_local]."""
+        pts = np.ascontiguousarray(xy, dtype=np.float64)
+        R = w.shape[0]
+        out = self._vec(R)
+        self._check(self.lib.ddh_eval_points(self.h, pts.ctypes.data, pts.shape[0], R, _ptr(w.contiguous()), _ptr(out), 1))
+        return out
 
     def primal_residual(self, b, u) -> np.ndarray:
         R = b.shape[0]
