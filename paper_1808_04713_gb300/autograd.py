@@ -15,9 +15,11 @@ class PlaneWaveSolve(torch.autograd.Function):
         solver.set_coefficients(solver_k(solver), eps.detach().cpu().double().numpy())
         solver.factor(**(factor_opts or {}))
         b = solver.rhs_planewave(thetas)
-        u, _ = solver.solve(b, tol=tol)
+        u, st = solver.solve(b, tol=tol, allow_noconv=True)
+        ctx.stats = st
         ctx.solver = solver
         ctx.tol = tol
+        ctx.eps_device = eps.device
         ctx.save_for_backward(u)
         return u
 
@@ -25,9 +27,9 @@ class PlaneWaveSolve(torch.autograd.Function):
     def backward(ctx, grad_u):
         (u,) = ctx.saved_tensors
         s = ctx.solver
-        lam, _ = s.solve(torch.conj(grad_u).resolve_conj().contiguous(), tol=ctx.tol)
+        lam, _ = s.solve(torch.conj(grad_u).resolve_conj().contiguous(), tol=ctx.tol, allow_noconv=True)
         g = s.grad_eps(u, lam)
-        return g.to(torch.float64), None, None, None, None
+        return g.to(device=ctx.eps_device, dtype=torch.float64), None, None, None, None
 
 
 def solver_k(solver) -> float:

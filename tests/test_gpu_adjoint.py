@@ -65,10 +65,10 @@ def test_grad_k_matches_finite_differences():
     s = make_solver(0, w.base_n, w.leaves, w.p, w.k, w.eps)
     s.factor(tol=1e-13)
     b = s.rhs_planewave(w.thetas)
-    u, _ = s.solve(b, tol=1e-13)
+    u, _ = s.solve(b, tol=1e-13, allow_noconv=True)
     y = s.eval_points(PTS, u)
     G = 2.0 * y
-    lam, _ = s.solve(s.inject_points(PTS, torch.conj(G).resolve_conj()), tol=1e-13)
+    lam, _ = s.solve(s.inject_points(PTS, torch.conj(G).resolve_conj()), tol=1e-13, allow_noconv=True)
     gk = s.grad_k(u, lam, w.thetas)
     s.close()
     step = 1e-6
@@ -100,7 +100,7 @@ def test_lens_48_gradient_against_finite_differences():
             ep[e] += sgn * 1e-6
             s.set_coefficients(w.k, ep)
             s.factor(tol=1e-13, **opts)
-            uu, _ = s.solve(s.rhs_planewave(w.thetas), tol=1e-13)
+            uu, _ = s.solve(s.rhs_planewave(w.thetas), tol=1e-13, allow_noconv=True)
             Js.append(float((s.eval_points(w.points, uu).abs() ** 2).sum()))
         fd = (Js[0] - Js[1]) / 2e-6
         assert abs(g[e] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g).max()), (e, g[e], fd)
