@@ -176,6 +176,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         geo[3 * e] = El.x0; geo[3 * e + 1] = El.y0; geo[3 * e + 2] = El.h;
     }
     d.pmax = pmax;
+    for (int e = 0; e < E; ++e) d.maxE1 = std::max(d.maxE1, m.el[e].nE1);
     if ((st = upload(ctx, p, &d.p))) return st;
     if ((st = upload(ctx, off, &d.off))) return st;
     if ((st = upload(ctx, e1o, &d.e1_off))) return st;
@@ -407,7 +408,14 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, w, &a))) return st;
         ctx->gw = (double*)a;
     }
-    set_smem_limits(pmax);
+    // device error word (bounded waits record failures here)
+    {
+        std::vector<int> z0(4, 0);
+        const int* q;
+        if ((st = upload(ctx, z0, &q))) return st;
+        d.err = (int*)q;
+    }
+    set_smem_limits(pmax, d.maxE1);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(ctx->stream));
     return DDH_OK;

@@ -28,6 +28,8 @@ template <class T> __device__ __forceinline__ void fma_r(cpx<T>& a, T s, cpx<T> 
 // Element and slot tables on the device (all arrays device-resident, owned by the context).
 struct DevModel {
     int E = 0, l = 0, pmax = 0;
+    int maxE1 = 0;                      // largest number of type-1 edge slots of an element
+    int* err = nullptr;                 // device error word (0 = ok), read by the host after solves
     int64_t n_local = 0;
     int nE1_tot = 0, nT_tot = 0, n_coarse = 0, n_dual = 0, n_conf = 0;
     // per element

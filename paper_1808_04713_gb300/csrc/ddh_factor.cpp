@@ -300,8 +300,10 @@ bool factor(Model& m, int nthreads, std::string& err) {
     build_slap_tables(m);
     // Sinv storage
     int64_t so = 0;
-    for (auto& El : m.el) { El.sinv_off = so; so += (int64_t)El.nE1 * El.nE1; }
-    m.sinv.assign((size_t)so, cd(0));
+    // blocks rounded to an even number of entries: every block (also of the complex64 copy)
+    // starts 16-byte aligned for the bulk copies into shared memory
+    for (auto& El : m.el) { El.sinv_off = so; const int64_t s2 = (int64_t)El.nE1 * El.nE1; so += s2 + (s2 & 1); }
+    m.sinv.assign((size_t)so + 2, cd(0));
     std::vector<ElemFactor> ef(E);
     parallel_for(E, nthreads, [&](int e) {
         const Elem& El = m.el[e];

@@ -70,9 +70,9 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
                                                const double2* __restrict__ z, double zsign,
                                                const double2* __restrict__ bt, int has_bI, int R,
                                                cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
-                                               const int* __restrict__ done, int ntask, int per_warp) {
+                                               const int* __restrict__ done, int ntask, int stage_off) {
     if (done && *done) return;
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
     const int task = blockIdx.x;
     if (task >= ntask) return;
@@ -80,7 +80,13 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
     const int cnt = min(RB, R - r0);
     const int p = dm.p[e], N = p + 1, n = p - 1;
     ElemSmem<T> s = carve<T>(smem, dm.pmax, 0);
-    (void)per_warp;
+    // S_E^-1 of this element: bulk copy into shared memory, overlapped with the setup below
+    const cpx<T>* S = sinv + dm.sinv_off[e];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_off);
+    cpx<T>* S_s = reinterpret_cast<cpx<T>*>(smem + stage_off + 128);
+    const int nE0 = dm.nE1[e];
+    if (stage_off > 0 && nE0 > 0 && threadIdx.x == 0)
+        bulk_load_start(bar, S_s, S, (uint32_t)(((size_t)nE0 * nE0 * sizeof(cpx<T>) + 15) & ~(size_t)15));
     const int stride = 4 * N;
     cpx<T>* rE = s.vec;                     // [RB][4N]
     cpx<T>* xE = s.vec + RB * stride;       // [RB][4N]
@@ -112,7 +118,11 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
             g.sync();
         }
     }
-    sinv_apply_batched<T, RB>(g, sinv + dm.sinv_off[e], nE, cnt, rE, stride, xE);
+    if (stage_off > 0 && nE > 0) {
+        if (!bulk_wait_all(bar, dm.err)) return;
+        S = S_s;
+    }
+    sinv_apply_batched<T, RB>(g, S, nE, cnt, rE, stride, xE);
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
         const int q = idx / nE, i = idx % nE;
         xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = xE[q * stride + i];
@@ -276,9 +286,9 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
                                                cpx<T>* __restrict__ xE_out, int recover,
                                                const double2* __restrict__ bt, int has_bI, int R,
                                                double2* __restrict__ phi_out, const int* __restrict__ done,
-                                               int ntask, int per_warp) {
+                                               int ntask, int stage_off) {
     if (done && *done) return;
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
     const int task = blockIdx.x;
     if (task >= ntask) return;
@@ -286,7 +296,12 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
     const int cnt = min(RB, R - r0);
     const int p = dm.p[e], N = p + 1, n = p - 1;
     ElemSmem<T> s = carve<T>(smem, dm.pmax, 0);
-    (void)per_warp;
+    const cpx<T>* S = sinv + dm.sinv_off[e];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_off);
+    cpx<T>* S_s = reinterpret_cast<cpx<T>*>(smem + stage_off + 128);
+    const int nE0 = dm.nE1[e];
+    if (stage_off > 0 && nE0 > 0 && threadIdx.x == 0)
+        bulk_load_start(bar, S_s, S, (uint32_t)(((size_t)nE0 * nE0 * sizeof(cpx<T>) + 15) & ~(size_t)15));
     const int stride = 4 * N;
     cpx<T>* rE = s.vec;                       // [RB][4N]
     cpx<T>* sE = s.vec + RB * stride;         // [RB][4N]
@@ -325,7 +340,11 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
         }
         g.sync();
     }
-    sinv_apply_batched<T, RB>(g, sinv + dm.sinv_off[e], nE, cnt, rE, stride, sE);
+    if (stage_off > 0 && nE > 0) {
+        if (!bulk_wait_all(bar, dm.err)) return;
+        S = S_s;
+    }
+    sinv_apply_batched<T, RB>(g, S, nE, cnt, rE, stride, sE);
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
         const int q = idx / nE, i = idx % nE;
         const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
@@ -422,11 +441,19 @@ template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __restrict__ v, cpx<T>* __restrict__ outE,
                                                   int R, const int* __restrict__ done) {
     if (done && *done) return;
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const int e = blockIdx.x, r0 = blockIdx.y * RB;
     const int cnt = min(RB, R - r0);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e];
-    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);     // [RB][nE]
+    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);                 // [RB][nE]
+    T* Ss = reinterpret_cast<T*>(smem + sizeof(cpx<T>) * RB * dm.maxE1);   // [nE][nE]
+    const int t = dm.ptab[e];
+    const int p = dm.p[e], ne = 4 * (p - 1);
+    const double* S = dm.slap_all + dm.tab_slap[t];
+    for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x) {
+        const int i = idx / nE, j = idx % nE;
+        Ss[idx] = (T)S[(int64_t)dm.e1_eall[e1o + i] * ne + dm.e1_eall[e1o + j]];
+    }
     for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
         const int q = idx / nE, i = idx % nE;
         const int row = dm.e1_row[e1o + i];
@@ -435,16 +462,12 @@ __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __
         in[q * nE + i] = val;
     }
     __syncthreads();
-    const int t = dm.ptab[e];
-    const int p = dm.p[e], ne = 4 * (p - 1);
-    const double* S = dm.slap_all + dm.tab_slap[t];
     for (int i = threadIdx.x; i < nE; i += blockDim.x) {
         cpx<T> acc[RB];
 #pragma unroll
         for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
-        const int gi = dm.e1_eall[e1o + i];
         for (int j = 0; j < nE; ++j) {
-            const T sv = (T)S[(int64_t)gi * ne + dm.e1_eall[e1o + j]];
+            const T sv = Ss[i * nE + j];
 #pragma unroll
             for (int q = 0; q < RB; ++q)
                 if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
@@ -569,7 +592,7 @@ __global__ void k_basis(DevModel dm, const double2* __restrict__ x, double2* __r
 // (A phi) per element in FP64 (interpolatory basis), out = b - A phi (b may be null)
 __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2* __restrict__ phi,
                                                      const double2* __restrict__ b, double2* __restrict__ out) {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const int e = blockIdx.x, r = blockIdx.y;
     const int p = dm.p[e], N = p + 1;
     const CtaGroup g;
@@ -623,7 +646,7 @@ __global__ void k_conf_gather(DevModel dm, const double2* __restrict__ x, double
 __global__ void __launch_bounds__(128) k_grad_elem(DevModel dm, const double2* __restrict__ ut,
                                                    const double2* __restrict__ lt, int R, double k, int mode,
                                                    double* __restrict__ out) {
-    extern __shared__ __align__(16) char smem[];
+    extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
     const int e = blockIdx.x;
     const int p = dm.p[e], N = p + 1;
@@ -969,25 +992,35 @@ static inline int rhs_block(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ?
 
 template <class T>
 static size_t pass_smem_t(int pmax, int rb) { return (elem_smem_bytes<T>(pmax, 3 * rb * 4 * (pmax + 1)) + 127) & ~(size_t)127; }
-// warps (elements) per CTA: up to 4 while the per-warp shared memory fits in 200 KB
-// one CTA of 128 threads per (element, RHS block): measured faster than one warp per element
+// shared-memory staging of S_E^-1 when it fits: returns the staging offset (0 = no staging)
 template <class T>
-static int pass_wpc(int, int) { return 1; }
+static int pass_stage_off(int pmax, int rb, int maxE1) {
+    const size_t base = pass_smem_t<T>(pmax, rb);
+    const size_t st = 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+    return (maxE1 > 0 && base + st <= 200 * 1024) ? (int)base : 0;
+}
+template <class T>
+static size_t pass_smem_total(int pmax, int rb, int maxE1) {
+    const int off = pass_stage_off<T>(pmax, rb, maxE1);
+    if (!off) return pass_smem_t<T>(pmax, rb);
+    return (size_t)off + 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+}
+// warps (elements) per CTA: up to 4 while the per-warp shared memory fits in 200 KB
 
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
     const int rb = rhs_block(R);
-    const int per = (int)pass_smem_t<T>(dm.pmax, rb), wpc = pass_wpc<T>(dm.pmax, rb);
+    const int so = pass_stage_off<T>(dm.pmax, rb, dm.maxE1);
     const int ntask = dm.E * ((R + rb - 1) / rb);
-    const dim3 g((ntask + wpc - 1) / wpc);
-    const size_t sm = (size_t)per * wpc;
+    const dim3 g(ntask);
+    const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     switch (rb) {
-        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
-        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
-        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per); break;
-        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, per);
+        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
     }
 }
 template <class T>
@@ -999,18 +1032,18 @@ template <class T>
 void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const void* xE_in, void* xE_out,
                   int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st) {
     const int rb = rhs_block(R);
-    const int per = (int)pass_smem_t<T>(dm.pmax, rb), wpc = pass_wpc<T>(dm.pmax, rb);
+    const int so = pass_stage_off<T>(dm.pmax, rb, dm.maxE1);
     const int ntask = dm.E * ((R + rb - 1) / rb);
-    const dim3 g((ntask + wpc - 1) / wpc);
-    const size_t sm = (size_t)per * wpc;
+    const dim3 g(ntask);
+    const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     const cpx<T>* xi = (const cpx<T>*)xE_in;
     cpx<T>* xo = (cpx<T>*)xE_out;
     switch (rb) {
-        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
-        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
-        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per); break;
-        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, per);
+        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
     }
 }
 template <class T>
@@ -1025,7 +1058,7 @@ void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, d
     k_dinv<<<gr, 128, 0, st>>>(dm, v, vd, lumped, done);
     const int rb = rhs_block(R);
     const dim3 g(dm.E, (R + rb - 1) / rb);
-    const size_t sm = sizeof(cpx<T>) * (size_t)rb * (4 * (dm.pmax - 1) + 8);
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + sizeof(T) * (size_t)dm.maxE1 * dm.maxE1 + 16;
     switch (rb) {
         case 8: k_pre_elem<T, 8><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
         case 4: k_pre_elem<T, 4><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
@@ -1137,17 +1170,27 @@ size_t pass_smem(int pmax, bool fp64) {
     return fp64 ? pass_smem_t<double>(pmax, 8) : pass_smem_t<float>(pmax, 8);
 }
 template <class T, int RB>
-static void set_pass_limits(int pmax) {
-    const int b = (int)pass_smem_t<T>(pmax, RB) * pass_wpc<T>(pmax, RB);
+static void set_pass_limits(int pmax, int maxE1) {
+    const int b = (int)pass_smem_total<T>(pmax, RB, maxE1);
     cudaFuncSetAttribute(k_pass1<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(k_pass2<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
-void set_smem_limits(int pmax) {
-    set_pass_limits<double, 1>(pmax); set_pass_limits<double, 2>(pmax);
-    set_pass_limits<double, 4>(pmax); set_pass_limits<double, 8>(pmax);
-    set_pass_limits<float, 1>(pmax); set_pass_limits<float, 2>(pmax);
-    set_pass_limits<float, 4>(pmax); set_pass_limits<float, 8>(pmax);
+void set_smem_limits(int pmax, int maxE1) {
+    set_pass_limits<double, 1>(pmax, maxE1); set_pass_limits<double, 2>(pmax, maxE1);
+    set_pass_limits<double, 4>(pmax, maxE1); set_pass_limits<double, 8>(pmax, maxE1);
+    set_pass_limits<float, 1>(pmax, maxE1); set_pass_limits<float, 2>(pmax, maxE1);
+    set_pass_limits<float, 4>(pmax, maxE1); set_pass_limits<float, 8>(pmax, maxE1);
     cudaFuncSetAttribute(k_elem_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
+    const int pre64 = (int)(sizeof(cpx<double>) * 8 * (size_t)maxE1 + sizeof(double) * (size_t)maxE1 * maxE1 + 16);
+    const int pre32 = (int)(sizeof(cpx<float>) * 8 * (size_t)maxE1 + sizeof(float) * (size_t)maxE1 * maxE1 + 16);
+    cudaFuncSetAttribute(k_pre_elem<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
     cudaFuncSetAttribute(k_grad_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
 }
 

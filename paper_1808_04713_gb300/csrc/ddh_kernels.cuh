@@ -18,6 +18,43 @@
 
 namespace ddh {
 
+// ---- 1-D bulk copy global -> shared (cp.async.bulk + mbarrier transaction count)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Issued by one thread: init the barrier, expect `bytes`, start the copy (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load_start(uint64_t* bar, void* dst, const void* src, uint32_t bytes) {
+    const uint32_t b = smem_u32(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase 0 of the barrier.  On time-out the CTA records an error code, waits
+// once more (bounded) for its copy in flight and every thread gets `false` (block-wide vote),
+// so the caller can return without touching the shared buffer.
+__device__ __forceinline__ bool bulk_wait_all(uint64_t* bar, int* err) {
+    bool ok = false;
+    for (int it = 0; it < (1 << 20) && !ok; ++it) ok = mbar_try_wait(bar, 0);
+    const int bad = __syncthreads_or(!ok);
+    if (bad) {
+        if (threadIdx.x == 0 && err) atomicExch(err, 2);
+        for (int it = 0; it < (1 << 20) && !ok; ++it) ok = mbar_try_wait(bar, 0);
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
 // Thread group executing one element: the whole CTA, or one warp of it.
 struct CtaGroup {
     __device__ __forceinline__ int t() const { return threadIdx.x; }

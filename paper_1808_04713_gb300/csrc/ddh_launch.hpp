@@ -59,6 +59,6 @@ void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, 
 void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st);
 void launch_readback(const DevModel& dm, const double2* phi, double2* z, int R, cudaStream_t st);
 size_t pass_smem(int pmax, bool fp64);
-void set_smem_limits(int pmax);
+void set_smem_limits(int pmax, int maxE1);
 
 }  // namespace ddh
