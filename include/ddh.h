@@ -177,6 +177,21 @@ ddh_status ddh_eval_points(ddh_ctx* ctx, const double* xy, int32_t n, int32_t R,
 ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
                                double* out_host);
 
+/* Allocation-free variant of ddh_primal_residual (the paper has no counterpart: this is a
+ * service of the library).  Some callers cannot allocate device memory where they need the
+ * residual -- code running while its stream is captured into a CUDA graph, where cudaMalloc is
+ * not allowed, and applications that fix their device-memory budget at start-up.  This call
+ * allocates nothing: it works in one file-scope device scratch array of 32 MiB that every GPU
+ * loading the library holds until the process exits.  It needs 16 R (4 n_local + n_conforming)
+ * bytes plus 2 x 256-byte-aligned norm slots; larger problems (and R > 512) are rejected with
+ * DDH_ERR_INVALID_ARG and a message naming the limit.  The first call on a device looks up the
+ * scratch address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the one array (it keeps the last call's
+ * contents; the accumulators are cleared on entry), so calls that overlap on the GPU -- from
+ * several streams or threads -- race.  Same arguments and result as ddh_primal_residual. */
+ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
+                                       double* out_host);
+
 /* Time the components of one interface-operator application F = C^ A^-1 C^T and of the
  * preconditioner on the context stream with CUDA events, each launched `reps` times on the
  * buffers of the last solve (call after a ddh_solve with the same R and precision).

@@ -89,6 +89,16 @@ struct ddh_ctx {
     KState kin, kout;
 };
 
+// accessors for translation units that do not see the context definition
+namespace ddh {
+const DevModel* ctx_devmodel(ddh_ctx* c) { return &c->dm; }
+cudaStream_t ctx_stream(ddh_ctx* c) { return c->stream; }
+int ctx_device(ddh_ctx* c) { return c->device; }
+bool ctx_factored(ddh_ctx* c) { return c->factored; }
+void ctx_set_error(ddh_ctx* c, const char* msg) { c->err = msg; }
+void ctx_add_launches(ddh_ctx* c, int n) { c->launches += n; }
+}  // namespace ddh
+
 #define CK(call)                                                                 \
     do {                                                                         \
         cudaError_t e_ = (call);                                                 \
