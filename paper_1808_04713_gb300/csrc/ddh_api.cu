@@ -568,7 +568,7 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     ks.release();
     KrylovDev& K = ks.K;
     K.nd = nd; K.m = m; K.R = R;
-    K.nchunk = std::max(1, std::min(296, (nd + 63) / 64));
+    K.nchunk = std::max(1, std::min(296, (nd + 255) / 256));
     auto al = [&](size_t bytes, void** p) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
         cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), ctx->stream);
@@ -609,6 +609,8 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
 struct KrylovOps {
     std::function<void(const double2*, double2*, const int*)> op;
     std::function<ddh_status(const double2*, double2*, const int*)> prec;
+    // optional: fetch V[j] + precondition + store Zb[j] in one go (replaces fetch/prec/store)
+    std::function<void(const KrylovDev&)> prec_krylov;
     bool graph = false;     // the body may be captured as a CUDA graph
     int key = 0;            // graph cache key (precision of the element kernels)
 };
@@ -617,13 +619,17 @@ struct KrylovOps {
 static ddh_status iteration_body(ddh_ctx* ctx, KState& ks, const KrylovOps& ops) {
     KrylovDev& K = ks.K;
     const int* done = K.ctl + 1;
-    launch_fetch(K, ctx->stream);
-    ddh_status st = ops.prec(K.vin, K.zw, done);
-    if (st) return st;
-    launch_store(K, ctx->stream);
+    if (ops.prec_krylov) {
+        ops.prec_krylov(K);
+    } else {
+        launch_fetch(K, ctx->stream);
+        ddh_status st = ops.prec(K.vin, K.zw, done);
+        if (st) return st;
+        launch_store(K, ctx->stream);
+    }
     ops.op(K.zw, K.w, done);
     launch_krylov_iter_tail(K, ctx->stream);
-    ctx->launches += 2 + 6;
+    ctx->launches += (ops.prec_krylov ? 0 : 2) + 7;
     return DDH_OK;
 }
 
@@ -782,6 +788,13 @@ static KrylovOps dual_ops(ddh_ctx* ctx, const Work& w) {
         apply_prec<T>(ctx, w, in, out, ctx->kin.K.R, done);
         return DDH_OK;
     };
+    // conforming meshes with the Dirichlet preconditioner: fetch + precondition + store fused
+    if (ctx->opt.precond == DDH_PRECOND_DIRICHLET && ctx->m.hblk_row0.empty()) {
+        o.prec_krylov = [ctx, w](const KrylovDev& K) {
+            launch_pre_krylov<T>(ctx->dm, K, w.outE, K.R, ctx->stream);
+            ctx->launches += 2;
+        };
+    }
     o.graph = true;
     o.key = (std::is_same<T, double>::value ? 0 : 1) + (ctx->coarse32 ? 2 : 0) + (ctx->refine_active ? 4 : 0);
     return o;

@@ -28,20 +28,43 @@ __device__ __forceinline__ void elem_gam(const DevModel& dm, int e, T* g) {
 template <class T, int RB, class G>
 __device__ inline void sinv_apply_batched(const G& g, const cpx<T>* __restrict__ sinv, int nE, int cnt, const cpx<T>* r,
                                           int rstride, cpx<T>* out) {
-    for (int i = g.t(); i < nE; i += g.n()) {
-        cpx<T> acc[RB];
+    // tpr adjacent threads share one output row (columns split in tpr contiguous ranges,
+    // summed with warp shuffles); each thread keeps two accumulator sets for ILP
+    const int tpr = nE <= 32 ? 4 : (nE <= 64 ? 2 : 1);
+    const int nt = g.n();
+    const int iters = (nE * tpr + nt - 1) / nt;
+    const int chunk = (nE + tpr - 1) / tpr;
+    for (int it = 0; it < iters; ++it) {
+        const int slot = it * nt + g.t();
+        const int i = slot / tpr, part = slot % tpr;
+        cpx<T> a0[RB], a1[RB];
 #pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
-#pragma unroll 4
-        for (int j = 0; j < nE; ++j) {
-            const cpx<T> s = sinv[(int64_t)j * nE + i];
+        for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
+        if (i < nE) {
+            const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
+                const cpx<T> s0 = sinv[(int64_t)j * nE + i], s1 = sinv[(int64_t)(j + 1) * nE + i];
 #pragma unroll
-            for (int q = 0; q < RB; ++q)
-                if (q < cnt) fma_c(acc[q], s, r[q * rstride + j]);
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) { fma_c(a0[q], s0, r[q * rstride + j]); fma_c(a1[q], s1, r[q * rstride + j + 1]); }
+            }
+            if (j < j1) {
+                const cpx<T> s0 = sinv[(int64_t)j * nE + i];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) fma_c(a0[q], s0, r[q * rstride + j]);
+            }
         }
 #pragma unroll
-        for (int q = 0; q < RB; ++q)
-            if (q < cnt) out[q * rstride + i] = acc[q];
+        for (int q = 0; q < RB; ++q) {
+            cpx<T> v = a0[q] + a1[q];
+            for (int o = 1; o < tpr; o <<= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+            }
+            if (part == 0 && i < nE && q < cnt) out[q * rstride + i] = v;
+        }
     }
     g.sync();
 }
@@ -478,6 +501,69 @@ __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __
     }
 }
 
+// Conforming meshes (no hanging rows: D = 2 I, no C2 K C2^T term), fused with the Krylov
+// fetch: v = V[r][j] read directly (j = ctl[0]), D^-1 = 1/2 applied in the gather.
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pre_elem_kry(DevModel dm, KrylovDev K, cpx<T>* __restrict__ outE, int R) {
+    if (K.ctl[1]) return;
+    const int jj = K.ctl[0];
+    extern __shared__ __align__(128) char smem[];
+    const int e = blockIdx.x, r0 = blockIdx.y * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e];
+    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);
+    T* Ss = reinterpret_cast<T*>(smem + sizeof(cpx<T>) * RB * dm.maxE1);
+    const int t = dm.ptab[e];
+    const int p = dm.p[e], ne = 4 * (p - 1);
+    const double* S = dm.slap_all + dm.tab_slap[t];
+    for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x) {
+        const int i = idx / nE, j = idx % nE;
+        Ss[idx] = (T)S[(int64_t)dm.e1_eall[e1o + i] * ne + dm.e1_eall[e1o + j]];
+    }
+    for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
+        const int q = idx / nE, i = idx % nE;
+        const int row = dm.e1_row[e1o + i];
+        cpx<T> val = mk<T>(0, 0);
+        if (row >= 0) {
+            const double2* v = K.V + ((int64_t)(r0 + q) * (K.m + 1) + jj) * K.nd;
+            val = (T)(0.5 * dm.e1_sign[e1o + i]) * ld<T>(v, row);
+        }
+        in[q * nE + i] = val;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
+        cpx<T> acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
+        for (int j = 0; j < nE; ++j) {
+            const T sv = Ss[i * nE + j];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (q < cnt) outE[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = acc[q];
+    }
+}
+
+// z = D^-1 (outE[c] - outE[f]) with D = 2 I, written to zw and to the Krylov store Zb[r][j]
+template <class T>
+__global__ void k_pre_rows_kry(DevModel dm, KrylovDev K, const cpx<T>* __restrict__ outE) {
+    if (K.ctl[1]) return;
+    const int jj = K.ctl[0];
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (row >= dm.n_dual) return;
+    double sx = 0, sy = 0;
+    const int c = dm.row_c[row], f = dm.row_f[row];
+    if (c >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + c]; sx += (double)a.x; sy += (double)a.y; }
+    { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
+    const double2 z = make_double2(0.5 * sx, 0.5 * sy);
+    K.zw[(int64_t)r * K.nd + row] = z;
+    K.Zb[((int64_t)r * K.m + jj) * K.nd + row] = z;
+}
+
 // m[row] = outE[c] - outE[f] + (C2 K^Lap C2^T v)[row]
 template <class T>
 __global__ void k_pre_rows(DevModel dm, const cpx<T>* __restrict__ outE, const double2* __restrict__ v,
@@ -866,31 +952,33 @@ __global__ void __launch_bounds__(256) k_axpy(KrylovDev K, int pass) {
     }
 }
 
-// Hessenberg column j, Givens rotations, residual estimate, convergence flags. One thread/RHS.
+// Hessenberg column j, Givens rotations, residual estimate, convergence flags.  One CTA
+// per right-hand side: the column is rotated in shared memory and written back once.
 __global__ void k_givens(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
-    const int r = threadIdx.x;
-    __shared__ int alldone;
-    if (r == 0) alldone = 1;
+    const int r = blockIdx.x;
+    __shared__ double2 Hc[256];
+    __shared__ double hn_s;
+    if (threadIdx.x < 32) {
+        double s = 0;
+        for (int c = threadIdx.x; c < K.nchunk; c += 32) s += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) hn_s = sqrt(s);
+    }
+    const double2* hc = K.hcol + (int64_t)r * (K.m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hc[i] = hc[i];
     __syncthreads();
-    if (r < K.R) {
-        double nrm2 = 0;
-        for (int c = 0; c < K.nchunk; ++c) nrm2 += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
-        const double hn = sqrt(nrm2);
-        K.hcol[(int64_t)r * (K.m + 1) + j + 1] = make_double2(hn, 0.0);
-        K.partial[((int64_t)r * K.nchunk) * (K.m + 1) + K.m].y = hn;   // for the normalisation
+    if (threadIdx.x == 0) {
+        const double hn = hn_s;
+        Hc[j + 1] = make_double2(hn, 0.0);
         if (!K.rdone[r]) {
-            double2* Hc = K.H + ((int64_t)r * K.m + j) * (K.m + 1);
-            double2* hc = K.hcol + (int64_t)r * (K.m + 1);
-            for (int i = 0; i <= j + 1; ++i) Hc[i] = hc[i];
-            double* cs = K.cs + (int64_t)r * K.m;
-            double2* sn = K.sn + (int64_t)r * K.m;
+            const double* cs = K.cs + (int64_t)r * K.m;
+            const double2* sn = K.sn + (int64_t)r * K.m;
             for (int i = 0; i < j; ++i) {
                 const double2 a = Hc[i], b = Hc[i + 1];
                 const double c = cs[i];
                 const double2 s = sn[i];
-                // t0 = c a + s b ; t1 = -conj(s) a + c b
                 const double2 t0 = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
                 const double2 t1 = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
                 Hc[i] = t0; Hc[i + 1] = t1;
@@ -907,41 +995,55 @@ __global__ void k_givens(KrylovDev K) {
                 sx = (a.x / aa) * bb / den;
                 sy = (a.y / aa) * bb / den;
             }
-            cs[j] = c; sn[j] = make_double2(sx, sy);
+            K.cs[(int64_t)r * K.m + j] = c;
+            K.sn[(int64_t)r * K.m + j] = make_double2(sx, sy);
             Hc[j] = make_double2(c * a.x + sx * bb, c * a.y + sy * bb);
             Hc[j + 1] = make_double2(0, 0);
             double2* g = K.g + (int64_t)r * (K.m + 1);
             const double2 gj = g[j];
             g[j] = make_double2(c * gj.x, c * gj.y);
-            // g[j+1] = -conj(s) g_j
             g[j + 1] = make_double2(-(sx * gj.x + sy * gj.y), -(sx * gj.y - sy * gj.x));
             const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / K.bnorm[r];
             K.resid[r] = res;
             K.iters[r] = j + 1;
             if (res <= K.tol || hn == 0.0) K.rdone[r] = 1;
         }
-        if (!K.rdone[r]) atomicAnd(&alldone, 0);
     }
     __syncthreads();
-    if (r == 0) {
-        if (alldone) K.ctl[1] = 1;
-        if (j + 1 >= K.m) K.ctl[1] = 1;       // restart boundary: host takes over
-        K.ctl[0] = j + 1;
-    }
+    // columns past a right-hand side's convergence are never read back
+    double2* Hcol = K.H + ((int64_t)r * K.m + j) * (K.m + 1);
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hcol[i] = Hc[i];
 }
 
-// V[j+1] = w / h_{j+1,j}  (runs before k_givens advances j? no: reads hn from partial)
+// advance the column counter once every RHS has been rotated; stop at convergence of all or
+// at the restart boundary
+__global__ void k_advance(KrylovDev K) {
+    if (K.ctl[1]) return;
+    const int j = K.ctl[0];
+    int all = 1;
+    for (int r = 0; r < K.R; ++r) all &= K.rdone[r];
+    if (all || j + 1 >= K.m) K.ctl[1] = 1;
+    K.ctl[0] = j + 1;
+}
+
+// V[j+1] = w / h_{j+1,j}, the norm reduced once per CTA from the chunk partials
 __global__ void k_normalize(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
-    const int q = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
-    if (q >= K.nd) return;
-    double s = 0;
-    for (int c = 0; c < K.nchunk; ++c) s += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
-    const double hn = sqrt(s);
-    const double inv = hn > 0 ? 1.0 / hn : 0.0;
-    const double2 w = K.w[(int64_t)r * K.nd + q];
-    K.V[((int64_t)r * (K.m + 1) + j + 1) * K.nd + q] = make_double2(w.x * inv, w.y * inv);
+    const int r = blockIdx.y;
+    __shared__ double inv_s;
+    if (threadIdx.x < 32) {
+        double s = 0;
+        for (int c = threadIdx.x; c < K.nchunk; c += 32) s += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) { const double hn = sqrt(s); inv_s = hn > 0 ? 1.0 / hn : 0.0; }
+    }
+    __syncthreads();
+    const double inv = inv_s;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < K.nd; q += gridDim.x * blockDim.x) {
+        const double2 w = K.w[(int64_t)r * K.nd + q];
+        K.V[((int64_t)r * (K.m + 1) + j + 1) * K.nd + q] = make_double2(w.x * inv, w.y * inv);
+    }
 }
 
 // nu[r] += sum_i y[r][i] Zb[r][i] (i < iters_r)
@@ -1128,14 +1230,31 @@ void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b
 void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st) {
     k_conf_gather<<<dim3((dm.n_conf + 255) / 256, R), 256, 0, st>>>(dm, x, norm2);
 }
+template <class T>
+void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const dim3 g(dm.E, (R + rb - 1) / rb);
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + sizeof(T) * (size_t)dm.maxE1 * dm.maxE1 + 16;
+    switch (rb) {
+        case 8: k_pre_elem_kry<T, 8><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        case 4: k_pre_elem_kry<T, 4><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        case 2: k_pre_elem_kry<T, 2><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        default: k_pre_elem_kry<T, 1><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R);
+    }
+    k_pre_rows_kry<T><<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, K, (const cpx<T>*)outE);
+}
+template void launch_pre_krylov<double>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
+template void launch_pre_krylov<float>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
+
 void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st) {
     const dim3 gv((K.nd + 255) / 256, K.R), gc(K.nchunk, K.R);
     for (int pass = 0; pass < 2; ++pass) {
         k_dots<<<gc, 256, 0, st>>>(K);
         k_axpy<<<gc, 256, 0, st>>>(K, pass);
     }
-    k_normalize<<<gv, 256, 0, st>>>(K);
-    k_givens<<<1, ((K.R + 31) / 32) * 32, 0, st>>>(K);
+    k_normalize<<<dim3(std::min(152, (K.nd + 255) / 256), K.R), 256, 0, st>>>(K);
+    k_givens<<<K.R, 64, 0, st>>>(K);
+    k_advance<<<1, 1, 0, st>>>(K);
 }
 void launch_fetch(const KrylovDev& K, cudaStream_t st) {
     k_fetch<<<dim3((K.nd + 255) / 256, K.R), 256, 0, st>>>(K);
@@ -1191,6 +1310,14 @@ void set_smem_limits(int pmax, int maxE1) {
     cudaFuncSetAttribute(k_pre_elem<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
     cudaFuncSetAttribute(k_pre_elem<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
     cudaFuncSetAttribute(k_pre_elem<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
     cudaFuncSetAttribute(k_grad_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
 }
 

@@ -49,6 +49,8 @@ void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in,
 void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st);
 void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st);
 void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st);
+template <class T>
+void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R, cudaStream_t st);
 void launch_fetch(const KrylovDev& K, cudaStream_t st);
 void launch_store(const KrylovDev& K, cudaStream_t st);
 void launch_update(const double2* Zb, const double2* y, const int* nit, double2* nu, int nd, int m, int R, cudaStream_t st);
