@@ -84,8 +84,8 @@ typedef struct {
     int64_t n_dual;        /* dual rows (interface unknowns nu) */
     int64_t n_coarse;      /* coarse (type-2) unknowns, size of K */
     int64_t n_conforming;  /* global conforming DoF */
-    int32_t n_coarse_blocks;
-    int32_t max_block;     /* largest diagonal block of the coarse factorisation */
+    int32_t n_coarse_blocks; /* fronts of the nested-dissection coarse factor (1 when K^-1 is dense) */
+    int32_t max_block;     /* largest front (fully summed + boundary unknowns); n_coarse when dense */
     double min_resonance_gap; /* min over elements of min |D_ab| / max |D_ab| of the FDM */
     double factor_seconds; /* wall time of the last ddh_factor */
 } ddh_info;
@@ -116,7 +116,7 @@ ddh_status ddh_set_coefficients(ddh_ctx* ctx, double k, const double* eps_r);
 
 /* Build every table and factor: per-element edge Schur complements of A11 through the
  * fast-diagonalisation solver (Sec. 2.2.1 fast solver; Sec. 2.3.3 block inversion), the
- * coarse matrix K = A22 - A12^T A11^-1 A12 and its block-tridiagonal LU, the preconditioner
+ * coarse matrix K = A22 - A12^T A11^-1 A12 and its nested-dissection factor, the preconditioner
  * pieces.  Returns DDH_WARN_NEAR_RESONANT when an element is within 1e-6 of a resonance of
  * A11 (the factorisation is still usable).  opt may be NULL (defaults). */
 ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt);
@@ -218,8 +218,9 @@ ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);
 
 /* Host-only setup and factorisation (no device work) of a mesh, for checks of the host
  * logic without a GPU.  sizes_out[8]: n_local, n_dual, n_coarse, n_conforming, type-1 edge
- * slots, type-2 slots, coarse blocks, largest block (0 blocks when the coarse inverse is
- * dense); seconds_out[5]: classification and factorisation wall time, the relative residual
+ * slots, type-2 slots, fronts of the nested-dissection coarse factor, largest front (the
+ * factor is built also when the device would use the dense K^-1 made from it);
+ * seconds_out[5]: classification and factorisation wall time, the relative residual
  * ||K x - t||/||t|| of one coarse solve with a seeded random t, max_e ||S_E S_E^-1 - I||_max, and
  * the minimum relative resonance gap of the interior blocks; l_out: l in use. */
 ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem,

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddh.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CPP_SRCS = ["ddh_tables.cpp", "ddh_mesh.cpp", "ddh_factor.cpp"]
+CPP_SRCS = ["ddh_tables.cpp", "ddh_mesh.cpp", "ddh_factor.cpp", "ddh_coarse.cpp"]
 CU_SRCS = ["ddh_kernels.cu", "ddh_api.cu", "ddh_noalloc.cu"]
 
 

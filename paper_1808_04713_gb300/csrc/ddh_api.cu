@@ -65,19 +65,21 @@ struct ddh_ctx {
     std::vector<void*> model_allocs;
     void* sinv64 = nullptr;
     void* sinv32 = nullptr;
-    double2* Kinv = nullptr;                       // dense coarse inverse (new order)
+    double2* Kinv = nullptr;                       // dense coarse inverse (elimination order)
     float2* Kinv32 = nullptr;
-    std::vector<double2*> bt_Dinv, bt_Lo, bt_Up;   // block-tridiagonal factors
-    std::vector<float2*> bt_Dinv32, bt_Lo32, bt_Up32;
+    // nested-dissection factor: complex128 matrices, their complex64 copy (nd32.G/M null
+    // unless mixed precision with coarse_fp32), and per tree level the work items
+    NDDev nd64, nd32;
+    const int4* nd_items = nullptr;
+    void* nd_u = nullptr;                          // forward updates [R][u_len] (work buffer)
+    std::vector<int> nd_fwd_off, nd_fwd_n, nd_fwd_rows;   // per level: first item, items, staged rows
+    std::vector<int> nd_bwd_off, nd_bwd_n, nd_bwd_rows;
     bool coarse32 = false;                         // current inner solves use the complex64 copy
     bool refine_coarse = false;                    // one FP64 refinement step per coarse solve
     bool refine_active = false;                    // refinement used by the current solves
-    const double2* const* Kd_dev = nullptr;        // device arrays of block pointers
-    const double2* const* Kl_dev = nullptr;
-    const double2* const* Ku_dev = nullptr;
-    const int* blk_start_dev = nullptr;
-    const int* row_blk_dev = nullptr;
-    std::vector<int> blk_start, blk_size;
+    const int* kc_ptr = nullptr;                   // assembled K (CSR, elimination order)
+    const int* kc_col = nullptr;
+    const double2* kc_val = nullptr;
     // gauss rule for loads
     double* gx = nullptr;
     double* gw = nullptr;
@@ -136,9 +138,14 @@ static void free_model(ddh_ctx* ctx) {
     ctx->Kinv = nullptr;
     ctx->Kinv32 = nullptr;
     ctx->refine_coarse = false;
-    ctx->Kd_dev = ctx->Kl_dev = ctx->Ku_dev = nullptr;
-    ctx->bt_Dinv.clear(); ctx->bt_Lo.clear(); ctx->bt_Up.clear();
-    ctx->bt_Dinv32.clear(); ctx->bt_Lo32.clear(); ctx->bt_Up32.clear();
+    ctx->nd64 = NDDev();
+    ctx->nd32 = NDDev();
+    ctx->nd_items = nullptr;
+    ctx->nd_u = nullptr;
+    ctx->nd_fwd_off.clear(); ctx->nd_fwd_n.clear(); ctx->nd_fwd_rows.clear();
+    ctx->nd_bwd_off.clear(); ctx->nd_bwd_n.clear(); ctx->nd_bwd_rows.clear();
+    ctx->kc_ptr = ctx->kc_col = nullptr;
+    ctx->kc_val = nullptr;
     ctx->gx = ctx->gw = nullptr;
 }
 
@@ -165,9 +172,8 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     ddh_status st;
     const int E = (int)m.el.size();
     const int nc = m.n_coarse;
-    // new (block-permuted) coarse index
-    std::vector<int> newidx(nc);
-    for (int g = 0; g < nc; ++g) newidx[g] = m.blk_start[m.blk_of[g]] + m.pos_in_blk[g];
+    // device coarse index = elimination position of the nested-dissection order
+    const std::vector<int>& newidx = m.cpos;
     DevModel& d = ctx->dm;
     d = DevModel();
     d.E = E; d.l = m.l; d.n_local = m.n_local;
@@ -327,85 +333,132 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         ctx->sinv32 = (void*)b;
     }
     // coarse factor
-    ctx->blk_start = m.blk_start;
-    ctx->blk_size = m.blk_size;
+    auto conv = [](const std::vector<cd>& v) {
+        std::vector<double2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
+        return o;
+    };
+    auto conv32 = [](const std::vector<double2>& v) {
+        std::vector<float2> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].x, (float)v[i].y);
+        return o;
+    };
+    const bool want32 = ctx->opt.precision == DDH_PREC_MIXED_FP32 && ctx->opt.coarse_fp32;
     if (m.dense_coarse) {
-        std::vector<double2> Kn((size_t)nc * nc);
-        for (int g = 0; g < nc; ++g)
-            for (int h = 0; h < nc; ++h) {
-                const cd v = m.Kinv[(size_t)g * nc + h];
-                Kn[(size_t)newidx[g] * nc + newidx[h]] = make_double2(v.real(), v.imag());
-            }
+        const std::vector<double2> Kn = conv(m.Kinv);
         const double2* a;
         if ((st = upload(ctx, Kn, &a))) return st;
         ctx->Kinv = (double2*)a;
-        std::vector<float2> K32(Kn.size());
-        for (size_t i = 0; i < Kn.size(); ++i) K32[i] = make_float2((float)Kn[i].x, (float)Kn[i].y);
         const float2* a32;
-        if ((st = upload(ctx, K32, &a32))) return st;
+        if ((st = upload(ctx, conv32(Kn), &a32))) return st;
         ctx->Kinv32 = (float2*)a32;
     } else {
-        auto conv = [](const std::vector<cd>& v) {
-            std::vector<double2> o(v.size());
-            for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
-            return o;
-        };
-        auto conv32 = [](const std::vector<cd>& v) {
-            std::vector<float2> o(v.size());
-            for (size_t i = 0; i < v.size(); ++i) o[i] = make_float2((float)v[i].real(), (float)v[i].imag());
-            return o;
-        };
-        for (int b = 0; b < m.nb; ++b) {
-            const double2* a;
-            const float2* a32;
-            if ((st = upload(ctx, conv(m.Dinv[b]), &a))) return st;
-            ctx->bt_Dinv.push_back((double2*)a);
-            if ((st = upload(ctx, conv(m.Lo[b]), &a))) return st;
-            ctx->bt_Lo.push_back((double2*)a);
-            if ((st = upload(ctx, conv(m.Up[b]), &a))) return st;
-            ctx->bt_Up.push_back((double2*)a);
-            if (ctx->opt.precision == DDH_PREC_MIXED_FP32 && ctx->opt.coarse_fp32) {
-                if ((st = upload(ctx, conv32(m.Dinv[b]), &a32))) return st;
-                ctx->bt_Dinv32.push_back((float2*)a32);
-                if ((st = upload(ctx, conv32(m.Lo[b]), &a32))) return st;
-                ctx->bt_Lo32.push_back((float2*)a32);
-                if ((st = upload(ctx, conv32(m.Up[b]), &a32))) return st;
-                ctx->bt_Up32.push_back((float2*)a32);
+        const int nn = (int)m.cnode.size();
+        std::vector<int> f0(nn), nF(nn), nB(nn), bidx;
+        std::vector<int64_t> b_off(nn), g_off(nn), m_off(nn), u_off(nn);
+        std::vector<double2> Gall, Mall;
+        int64_t ul = 0;
+        auto z = [](const cd& v) { return make_double2(v.real(), v.imag()); };
+        for (int id = 0; id < nn; ++id) {
+            const auto& N = m.cnode[id];
+            const int nb_ = (int)N.B.size(), n = N.nF + nb_;
+            f0[id] = N.f0; nF[id] = N.nF; nB[id] = nb_;
+            b_off[id] = (int64_t)bidx.size();
+            bidx.insert(bidx.end(), N.B.begin(), N.B.end());
+            u_off[id] = ul;
+            ul += nb_;
+            // G (nB x nF): column-major when its rows are short
+            g_off[id] = (int64_t)Gall.size();
+            const bool gs = N.nF <= kNDShortRow;
+            for (int a = 0; a < (gs ? N.nF : nb_); ++a)
+                for (int b = 0; b < (gs ? nb_ : N.nF); ++b)
+                    Gall.push_back(z(gs ? N.G[(size_t)b * N.nF + a] : N.G[(size_t)a * N.nF + b]));
+            // M = [W | -H] (nF x n): column-major when its rows are short
+            auto Mij = [&](int i, int j) { return j < N.nF ? N.W[(size_t)i * N.nF + j] : -N.H[(size_t)i * nb_ + (j - N.nF)]; };
+            m_off[id] = (int64_t)Mall.size();
+            const bool ms = n <= kNDShortRow;
+            for (int a = 0; a < (ms ? n : N.nF); ++a)
+                for (int b = 0; b < (ms ? N.nF : n); ++b) Mall.push_back(z(ms ? Mij(b, a) : Mij(a, b)));
+        }
+        // update entries subtracting into each position (from every node whose boundary has it)
+        std::vector<int> ct_ptr(nc + 1, 0);
+        for (int id = 0; id < nn; ++id) for (int b : m.cnode[id].B) ct_ptr[b + 1]++;
+        for (int i = 0; i < nc; ++i) ct_ptr[i + 1] += ct_ptr[i];
+        std::vector<int64_t> ct_idx(std::max(1, ct_ptr[nc]));
+        {
+            std::vector<int> fill(ct_ptr.begin(), ct_ptr.end() - 1);
+            for (int id = 0; id < nn; ++id) {
+                const auto& B = m.cnode[id].B;
+                for (size_t k = 0; k < B.size(); ++k) ct_idx[fill[B[k]]++] = u_off[id] + (int64_t)k;
             }
         }
+        // work items per level: 4 rows per CTA; a forward item also for nodes with no boundary
+        std::vector<int4> items;
+        const int L = m.c_depth + 1;
+        ctx->nd_fwd_off.assign(L, 0); ctx->nd_fwd_n.assign(L, 0); ctx->nd_fwd_rows.assign(L, 0);
+        ctx->nd_bwd_off.assign(L, 0); ctx->nd_bwd_n.assign(L, 0); ctx->nd_bwd_rows.assign(L, 0);
+        for (int lv = 0; lv < L; ++lv) {
+            ctx->nd_fwd_off[lv] = (int)items.size();
+            for (int id = 0; id < nn; ++id) {
+                const auto& N = m.cnode[id];
+                if (N.depth != lv || N.nF == 0) continue;
+                const int rows = (int)N.B.size();
+                const int sh = N.nF <= kNDShortRow, step = sh ? 128 : 4;
+                for (int r0 = 0; r0 == 0 || r0 < rows; r0 += step) items.push_back(make_int4(id, r0, std::min(step, rows - r0), sh));
+                ctx->nd_fwd_rows[lv] = std::max(ctx->nd_fwd_rows[lv], N.nF);
+            }
+            ctx->nd_fwd_n[lv] = (int)items.size() - ctx->nd_fwd_off[lv];
+            ctx->nd_bwd_off[lv] = (int)items.size();
+            for (int id = 0; id < nn; ++id) {
+                const auto& N = m.cnode[id];
+                if (N.depth != lv || N.nF == 0) continue;
+                const int sh = N.nF + (int)N.B.size() <= kNDShortRow, step = sh ? 128 : 4;
+                for (int r0 = 0; r0 < N.nF; r0 += step) items.push_back(make_int4(id, r0, std::min(step, N.nF - r0), sh));
+                ctx->nd_bwd_rows[lv] = std::max(ctx->nd_bwd_rows[lv], N.nF + (int)N.B.size());
+            }
+            ctx->nd_bwd_n[lv] = (int)items.size() - ctx->nd_bwd_off[lv];
+        }
+        for (int lv = 0; lv < L; ++lv)
+            if (ctx->nd_bwd_rows[lv] > 12800) return fail(ctx, DDH_ERR_INVALID_ARG, "coarse front too large for shared memory");
+        NDDev& D = ctx->nd64;
+        D.nc = nc;
+        D.u_len = std::max<int64_t>(1, ul);
+        if ((st = upload(ctx, f0, &D.f0))) return st;
+        if ((st = upload(ctx, nF, &D.nF))) return st;
+        if ((st = upload(ctx, nB, &D.nB))) return st;
+        if ((st = upload(ctx, b_off, &D.b_off))) return st;
+        if ((st = upload(ctx, bidx, &D.bidx))) return st;
+        if ((st = upload(ctx, g_off, &D.g_off))) return st;
+        if ((st = upload(ctx, m_off, &D.m_off))) return st;
+        if ((st = upload(ctx, u_off, &D.u_off))) return st;
+        if ((st = upload(ctx, ct_ptr, &D.ct_ptr))) return st;
+        if ((st = upload(ctx, ct_idx, &D.ct_idx))) return st;
+        const double2* a;
+        if ((st = upload(ctx, Gall, &a))) return st;
+        D.G = a;
+        if ((st = upload(ctx, Mall, &a))) return st;
+        D.M = a;
+        const int4* it;
+        if ((st = upload(ctx, items, &it))) return st;
+        ctx->nd_items = it;
+        ctx->nd32 = D;
+        ctx->nd32.G = ctx->nd32.M = nullptr;
+        if (want32) {
+            const float2* a32;
+            if ((st = upload(ctx, conv32(Gall), &a32))) return st;
+            ctx->nd32.G = a32;
+            if ((st = upload(ctx, conv32(Mall), &a32))) return st;
+            ctx->nd32.M = a32;
+        }
+        for (auto& N : m.cnode) { std::vector<cd>().swap(N.W); std::vector<cd>().swap(N.G); std::vector<cd>().swap(N.H); }
+        nd_set_smem_limits();
     }
-    // assembled blocks for the refinement step of an unstable block factorisation
+    // assembled K for the refinement step when the factorisation's self-check is loose
     ctx->refine_coarse = !m.dense_coarse && m.coarse_refine;
     if (ctx->refine_coarse) {
-        auto conv = [](const std::vector<cd>& v) {
-            std::vector<double2> o(std::max<size_t>(1, v.size()));
-            for (size_t i = 0; i < v.size(); ++i) o[i] = make_double2(v[i].real(), v[i].imag());
-            return o;
-        };
-        std::vector<const double2*> pd(m.nb), pl(m.nb), pu(m.nb);
-        for (int b = 0; b < m.nb; ++b) {
-            const double2* a;
-            if ((st = upload(ctx, conv(m.Kd[b]), &a))) return st;
-            pd[b] = a;
-            if (b > 0) { if ((st = upload(ctx, conv(m.Kl[b]), &a))) return st; pl[b] = a; } else pl[b] = nullptr;
-            pu[b] = ctx->bt_Up[b];
-        }
-        const double2* const* q;
-        if ((st = upload(ctx, pd, (const double2* const**)&q))) return st;
-        ctx->Kd_dev = q;
-        if ((st = upload(ctx, pl, (const double2* const**)&q))) return st;
-        ctx->Kl_dev = q;
-        if ((st = upload(ctx, pu, (const double2* const**)&q))) return st;
-        ctx->Ku_dev = q;
-        std::vector<int> rb(nc);
-        for (int b = 0; b < m.nb; ++b)
-            for (int i = m.blk_start[b]; i < m.blk_start[b + 1]; ++i) rb[i] = b;
-        const int* qi;
-        if ((st = upload(ctx, m.blk_start, &qi))) return st;
-        ctx->blk_start_dev = qi;
-        if ((st = upload(ctx, rb, &qi))) return st;
-        ctx->row_blk_dev = qi;
-        m.Kd.clear(); m.Kl.clear();
+        if ((st = upload(ctx, m.kc_ptr, &ctx->kc_ptr))) return st;
+        if ((st = upload(ctx, m.kc_col, &ctx->kc_col))) return st;
+        if ((st = upload(ctx, conv(m.kc_val), &ctx->kc_val))) return st;
     }
     // Gauss rule for the boundary loads
     {
@@ -453,6 +506,10 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     w.x2 = (double2*)p;
     if ((st = get_work(ctx, "ctmp", sizeof(double2) * (size_t)4 * R * d.n_coarse, &p))) return st;
     w.ctmp = (double2*)p;
+    if (!ctx->Kinv) {
+        if ((st = get_work(ctx, "ndu", sizeof(double2) * (size_t)R * ctx->nd64.u_len, &p))) return st;
+        ctx->nd_u = p;
+    }
     if ((st = get_work(ctx, "vd", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.vd = (double2*)p;
     if ((st = get_work(ctx, "mvec", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
@@ -460,28 +517,25 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     return DDH_OK;
 }
 
-// x2 = K^-1 t (vectors FP64), t is overwritten in block-tridiagonal mode.  The factor is
-// complex128, or its complex64 copy while ctx->coarse32 is set (mixed-precision inner solves).
-static void coarse_solve_once(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done);
+// x2 = K^-1 t (vectors FP64; t is left intact).  The factor is complex128, or its complex64
+// copy while ctx->coarse32 is set (mixed-precision inner solves).  tmp holds 4 R n_coarse.
+static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done);
 
-static void coarse_solve(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done) {
+static void coarse_solve(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done) {
     if (!(ctx->refine_active && ctx->refine_coarse && !ctx->coarse32)) { coarse_solve_once(ctx, t, x2, tmp, R, done); return; }
-    // x = BT(t); r = t - K x; x += BT(r)   (t is overwritten by the block sweep: keep a copy)
+    // x = K^-1 t;  r = t - K x;  x += K^-1 r
     const int nc = ctx->dm.n_coarse;
     cudaStream_t s = ctx->stream;
-    double2* t0 = tmp + (size_t)R * nc;
     double2* r = tmp + (size_t)2 * R * nc;
     double2* dx = tmp + (size_t)3 * R * nc;
-    cudaMemcpyAsync(t0, t, sizeof(double2) * (size_t)R * nc, cudaMemcpyDeviceToDevice, s);
     coarse_solve_once(ctx, t, x2, tmp, R, done);
-    launch_coarse_residual(ctx->Kd_dev, ctx->Kl_dev, ctx->Ku_dev, ctx->blk_start_dev, ctx->row_blk_dev,
-                           (int)ctx->blk_size.size(), nc, x2, t0, r, R, done, s);
+    launch_csr_residual(ctx->kc_ptr, ctx->kc_col, ctx->kc_val, nc, x2, t, r, R, done, s);
     coarse_solve_once(ctx, r, dx, tmp, R, done);
     launch_axpby(x2, 1.0, dx, 1.0, x2, (int64_t)R * nc, s);
     ctx->launches += 2;
 }
 
-static void coarse_solve_once(ddh_ctx* ctx, double2* t, double2* x2, double2* tmp, int R, const int* done) {
+static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done) {
     const int nc = ctx->dm.n_coarse;
     cudaStream_t s = ctx->stream;
     const bool f32 = ctx->coarse32;
@@ -491,22 +545,23 @@ static void coarse_solve_once(ddh_ctx* ctx, double2* t, double2* x2, double2* tm
         ctx->launches++;
         return;
     }
-    const int nb = (int)ctx->blk_size.size();
-    const auto& bs = ctx->blk_start;
-    const auto& sz = ctx->blk_size;
-    auto D = [&](int b) { return f32 ? (const void*)ctx->bt_Dinv32[b] : (const void*)ctx->bt_Dinv[b]; };
-    auto L = [&](int b) { return f32 ? (const void*)ctx->bt_Lo32[b] : (const void*)ctx->bt_Lo[b]; };
-    auto U = [&](int b) { return f32 ? (const void*)ctx->bt_Up32[b] : (const void*)ctx->bt_Up[b]; };
-    for (int b = 1; b < nb; ++b) {
-        launch_gemv(L(b), f32, sz[b], sz[b - 1], t + bs[b - 1], t + bs[b], nullptr, 1, nc, nc, R, done, s);
+    // nested dissection: forward from the deepest level, backward from the root
+    const bool f32nd = f32 && ctx->nd32.G;
+    const NDDev& D = f32nd ? ctx->nd32 : ctx->nd64;
+    double2* y = tmp;
+    double2* u = (double2*)ctx->nd_u;
+    const int L = (int)ctx->nd_fwd_n.size();
+    for (int lv = L - 1; lv >= 0; --lv) {
+        if (!ctx->nd_fwd_n[lv]) continue;
+        launch_nd_forward(D, f32nd, ctx->nd_items + ctx->nd_fwd_off[lv], ctx->nd_fwd_n[lv], ctx->nd_fwd_rows[lv], t, y, u,
+                          R, done, s);
         ctx->launches++;
     }
-    launch_gemv(D(nb - 1), f32, sz[nb - 1], sz[nb - 1], t + bs[nb - 1], x2 + bs[nb - 1], nullptr, 0, nc, nc, R, done, s);
-    ctx->launches++;
-    for (int b = nb - 2; b >= 0; --b) {
-        launch_gemv(U(b), f32, sz[b], sz[b + 1], x2 + bs[b + 1], tmp + bs[b], t + bs[b], 2, nc, nc, R, done, s);
-        launch_gemv(D(b), f32, sz[b], sz[b], tmp + bs[b], x2 + bs[b], nullptr, 0, nc, nc, R, done, s);
-        ctx->launches += 2;
+    for (int lv = 0; lv < L; ++lv) {
+        if (!ctx->nd_bwd_n[lv]) continue;
+        launch_nd_backward(D, f32nd, ctx->nd_items + ctx->nd_bwd_off[lv], ctx->nd_bwd_n[lv], ctx->nd_bwd_rows[lv], y, x2,
+                           R, done, s);
+        ctx->launches++;
     }
 }
 
@@ -568,7 +623,8 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     ks.release();
     KrylovDev& K = ks.K;
     K.nd = nd; K.m = m; K.R = R;
-    K.nchunk = std::max(1, std::min(296, (nd + 255) / 256));
+    K.chunk = nd <= 16384 ? 128 : 256;   // rows per CTA in the orthogonalisation kernels
+    K.nchunk = (nd + K.chunk - 1) / K.chunk;
     auto al = [&](size_t bytes, void** p) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
         cudaMemsetAsync(*p, 0, std::max<size_t>(bytes, 16), ctx->stream);
@@ -590,6 +646,9 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     ok &= al(sizeof(int) * (size_t)R, &p); K.iters = (int*)p;
     ok &= al(sizeof(double2) * (size_t)R * K.nchunk * (m + 1), &p); K.partial = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * (m + 1), &p); K.hcol = (double2*)p;
+    ok &= al(sizeof(double2) * (size_t)R * (m + 1), &p); K.h2 = (double2*)p;
+    ok &= al(sizeof(double) * (size_t)R, &p); K.hn = (double*)p;
+    ok &= al(sizeof(int) * (size_t)(R + 1), &p); K.cnt = (int*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.w = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.vin = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.zw = (double2*)p;
@@ -629,7 +688,7 @@ static ddh_status iteration_body(ddh_ctx* ctx, KState& ks, const KrylovOps& ops)
     }
     ops.op(K.zw, K.w, done);
     launch_krylov_iter_tail(K, ctx->stream);
-    ctx->launches += (ops.prec_krylov ? 0 : 2) + 7;
+    ctx->launches += (ops.prec_krylov ? 0 : 2) + 3;
     return DDH_OK;
 }
 
@@ -1081,9 +1140,9 @@ ddh_status ddh_get_info(const ddh_ctx* ctx, ddh_info* out) {
     out->n_dual = m.n_dual;
     out->n_coarse = m.n_coarse;
     out->n_conforming = m.n_conf;
-    out->n_coarse_blocks = m.dense_coarse ? 1 : m.nb;
     int mx = 0;
-    for (int b : m.blk_size) mx = std::max(mx, b);
+    for (const auto& N : m.cnode) mx = std::max(mx, N.nF + (int)N.B.size());
+    out->n_coarse_blocks = m.dense_coarse ? 1 : (int32_t)m.cnode.size();
     out->max_block = m.dense_coarse ? m.n_coarse : mx;
     out->min_resonance_gap = m.min_gap;
     out->factor_seconds = ctx->factor_seconds;
@@ -1341,10 +1400,10 @@ ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t*
     if (!factor(m, std::max(1u, std::thread::hardware_concurrency()), err)) return DDH_ERR_SINGULAR;
     auto t2 = std::chrono::steady_clock::now();
     int mx = 0;
-    for (int b : m.blk_size) mx = std::max(mx, b);
+    for (const auto& N : m.cnode) mx = std::max(mx, N.nF + (int)N.B.size());
     sizes[0] = m.n_local; sizes[1] = m.n_dual; sizes[2] = m.n_coarse; sizes[3] = m.n_conf;
     sizes[4] = (int64_t)m.e1_slot.size(); sizes[5] = (int64_t)m.t_slot.size();
-    sizes[6] = m.dense_coarse ? 0 : m.nb; sizes[7] = mx;
+    sizes[6] = (int64_t)m.cnode.size(); sizes[7] = mx;
     secs[0] = std::chrono::duration<double>(t1 - t0).count();
     secs[1] = std::chrono::duration<double>(t2 - t1).count();
     secs[2] = m.coarse_check;

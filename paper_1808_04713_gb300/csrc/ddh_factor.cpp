@@ -5,8 +5,8 @@
 //    element's edges and vertices), with A_II^-1 = (V (x) V) D^-1 (V (x) V)^T from the
 //    fast-diagonalisation table (the element fast solver of Sec. 2.2.1), and S_E^-1;
 //  * the local coarse Schur complements A_TT - A_T1 A11^-1 A_1T assembled through the
-//    slaving weights into K = A22 - A12^T A11^-1 A12, factored block-tridiagonally over
-//    base-grid rows (or inverted densely when small);
+//    slaving weights into K = A22 - A12^T A11^-1 A12 (factored by nested dissection in
+//    ddh_coarse.cpp);
 //  * the Dirichlet-preconditioner pieces built from the stiffness part only.
 #include <algorithm>
 #include <atomic>
@@ -170,6 +170,14 @@ static void gemm(int M, int K, int N, const cd* A, const cd* B, cd* C, bool subt
             for (int j = 0; j < N; ++j) c[j] += av * b[j];
         }
     });
+}
+
+void host_parallel(int n, int nthreads, const std::function<void(int)>& f) { parallel_for(n, nthreads, f); }
+bool host_invert(int n, const std::vector<cd>& A, std::vector<cd>& inv, double& minpiv, int nthreads) {
+    return invert(n, A, inv, minpiv, nthreads);
+}
+void host_gemm(int M, int K, int N, const cd* A, const cd* B, cd* C, bool subtract, int nthreads) {
+    gemm(M, K, N, A, B, C, subtract, nthreads);
 }
 
 // interior cross: interior slots (a, b >= 2) with a <= 3 or b <= 3
@@ -359,187 +367,44 @@ bool factor(Model& m, int nthreads, std::string& err) {
         if (!ef[e].ok) { err = "singular edge Schur complement in element " + std::to_string(e) + " (resonant element)"; return false; }
         m.min_gap = std::min(m.min_gap, ef[e].gap);
     }
-    // ---- coarse blocks (base-grid row bands)
+    // ---- assemble K = sum_e Z_e^T S_e Z_e (slaving weights) in CSR over coarse dofs
     const int nc = m.n_coarse;
-    const int64_t H2 = (int64_t)2 << m.maxlev;
-    m.nb = m.base_n;
-    m.blk_of.assign(nc, 0);
-    m.blk_size.assign(m.nb, 0);
-    for (int g = 0; g < nc; ++g) {
-        int b = (int)std::min<int64_t>(m.coarse_Y2[g] / H2, m.nb - 1);
-        m.blk_of[g] = b;
-    }
-    m.pos_in_blk.assign(nc, 0);
-    for (int g = 0; g < nc; ++g) m.pos_in_blk[g] = m.blk_size[m.blk_of[g]]++;
-    // drop empty blocks (cannot happen on a tiled square, but keep the code total)
-    m.blk_start.assign(m.nb + 1, 0);
-    for (int b = 0; b < m.nb; ++b) m.blk_start[b + 1] = m.blk_start[b] + m.blk_size[b];
-    m.perm.assign(nc, 0);
-    for (int g = 0; g < nc; ++g) m.perm[m.blk_start[m.blk_of[g]] + m.pos_in_blk[g]] = g;
-    std::vector<std::vector<cd>> Kd(m.nb), Kl(m.nb);
-    for (int b = 0; b < m.nb; ++b) {
-        Kd[b].assign((size_t)m.blk_size[b] * m.blk_size[b], cd(0));
-        if (b > 0) Kl[b].assign((size_t)m.blk_size[b] * m.blk_size[b - 1], cd(0));
-    }
-    for (int e = 0; e < E; ++e) {
-        const Elem& El = m.el[e];
-        const int nT = El.nT;
-        const auto& Se = ef[e].Se;
-        for (int t = 0; t < nT; ++t)
-            for (int u = 0; u < nT; ++u) {
-                const cd s = Se[(size_t)t * nT + u];
-                if (s == cd(0)) continue;
-                const int ti = El.t_off + t, ui = El.t_off + u;
-                for (int a = m.t_ptr[ti]; a < m.t_ptr[ti + 1]; ++a)
-                    for (int bq = m.t_ptr[ui]; bq < m.t_ptr[ui + 1]; ++bq) {
-                        const int g = m.t_col[a], h = m.t_col[bq];
-                        const cd v = m.t_w[a] * s * m.t_w[bq];
-                        const int bg = m.blk_of[g], bh = m.blk_of[h];
-                        if (bg == bh) Kd[bg][(size_t)m.pos_in_blk[g] * m.blk_size[bg] + m.pos_in_blk[h]] += v;
-                        else if (bg == bh + 1) Kl[bg][(size_t)m.pos_in_blk[g] * m.blk_size[bh] + m.pos_in_blk[h]] += v;
-                        else if (bh == bg + 1) { /* transpose of a lower entry */ }
-                        else { err = "coarse coupling outside the block-tridiagonal band"; return false; }
-                    }
-            }
-    }
-    // ---- block LU: D'_0 = K_00, Lo_j = K_{j,j-1} D'_{j-1}^-1, D'_j = K_jj - Lo_j K_{j-1,j}
-    m.Dinv.assign(m.nb, {}); m.Lo.assign(m.nb, {}); m.Up.assign(m.nb, {});
-    int maxb = 0;
-    for (int b = 0; b < m.nb; ++b) maxb = std::max(maxb, m.blk_size[b]);
-    for (int b = 0; b < m.nb; ++b) {
-        const int nbk = m.blk_size[b];
-        std::vector<cd> D = Kd[b];
-        if (b > 0) {
-            const int np = m.blk_size[b - 1];
-            m.Lo[b].assign((size_t)nbk * np, cd(0));
-            gemm(nbk, np, np, Kl[b].data(), m.Dinv[b - 1].data(), m.Lo[b].data(), false, nthreads);
-            // K_{j-1,j} = K_{j,j-1}^T
-            std::vector<cd> KlT((size_t)np * nbk);
-            for (int i = 0; i < nbk; ++i)
-                for (int j = 0; j < np; ++j) KlT[(size_t)j * nbk + i] = Kl[b][(size_t)i * np + j];
-            gemm(nbk, np, nbk, m.Lo[b].data(), KlT.data(), D.data(), true, nthreads);
-            m.Up[b - 1] = KlT;          // K_{b-1,b}  (np x nbk)
-        }
-        double mp;
-        if (!invert(nbk, D, m.Dinv[b], mp, nthreads)) { err = "singular coarse matrix block"; return false; }
-    }
+    std::vector<int32_t> kn_ptr(nc + 1, 0), kn_col;
+    std::vector<cd> kn_val;
     {
-        // self-check: x = K^-1 t by the block factorisation, then ||K x - t|| / ||t|| with the
-        // assembled blocks for a seeded random t
-        std::vector<std::vector<cd>> t(m.nb), w(m.nb), x(m.nb);
-        uint64_t st = 12345;
-        for (int b = 0; b < m.nb; ++b) {
-            t[b].resize(m.blk_size[b]);
-            for (auto& v : t[b]) {
-                st = st * 6364136223846793005ULL + 1442695040888963407ULL;
-                const double re = (double)(st >> 11) / 9007199254740992.0 - 0.5;
-                st = st * 6364136223846793005ULL + 1442695040888963407ULL;
-                const double im = (double)(st >> 11) / 9007199254740992.0 - 0.5;
-                v = cd(re, im);
-            }
-            w[b] = t[b];
-        }
-        auto mv = [](const std::vector<cd>& A, int r, int c, const std::vector<cd>& v, std::vector<cd>& out, double sg) {
-            for (int i = 0; i < r; ++i) { cd s = 0; for (int j = 0; j < c; ++j) s += A[(size_t)i * c + j] * v[j]; out[i] += sg * s; }
-        };
-        for (int b = 1; b < m.nb; ++b) mv(m.Lo[b], m.blk_size[b], m.blk_size[b - 1], w[b - 1], w[b], -1.0);
-        for (int b = m.nb - 1; b >= 0; --b) {
-            std::vector<cd> r = w[b];
-            if (b + 1 < m.nb) mv(m.Up[b], m.blk_size[b], m.blk_size[b + 1], x[b + 1], r, -1.0);
-            x[b].assign(m.blk_size[b], cd(0));
-            mv(m.Dinv[b], m.blk_size[b], m.blk_size[b], r, x[b], 1.0);
-        }
-        double num = 0, den = 0;
-        for (int b = 0; b < m.nb; ++b) {
-            std::vector<cd> y(m.blk_size[b], cd(0));
-            mv(Kd[b], m.blk_size[b], m.blk_size[b], x[b], y, 1.0);
-            if (b > 0) mv(Kl[b], m.blk_size[b], m.blk_size[b - 1], x[b - 1], y, 1.0);
-            if (b + 1 < m.nb) {
-                // K_{b,b+1} = Kl[b+1]^T
-                const int nn = m.blk_size[b + 1];
-                for (int i = 0; i < m.blk_size[b]; ++i) {
-                    cd s = 0;
-                    for (int j = 0; j < nn; ++j) s += Kl[b + 1][(size_t)j * m.blk_size[b] + i] * x[b + 1][j];
-                    y[i] += s;
+        std::vector<std::vector<std::pair<int, cd>>> rows(nc);
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            const int nT = El.nT;
+            const auto& Se = ef[e].Se;
+            for (int t = 0; t < nT; ++t)
+                for (int u = 0; u < nT; ++u) {
+                    const cd s = Se[(size_t)t * nT + u];
+                    if (s == cd(0)) continue;
+                    const int ti = El.t_off + t, ui = El.t_off + u;
+                    for (int a = m.t_ptr[ti]; a < m.t_ptr[ti + 1]; ++a)
+                        for (int bq = m.t_ptr[ui]; bq < m.t_ptr[ui + 1]; ++bq)
+                            rows[m.t_col[a]].push_back({m.t_col[bq], m.t_w[a] * s * m.t_w[bq]});
                 }
-            }
-            for (int i = 0; i < m.blk_size[b]; ++i) { num += std::norm(y[i] - t[b][i]); den += std::norm(t[b][i]); }
+            ef[e].Se.clear();
+            ef[e].Se.shrink_to_fit();
         }
-        m.coarse_check = std::sqrt(num / den);
+        for (int g = 0; g < nc; ++g) {
+            auto& r = rows[g];
+            std::sort(r.begin(), r.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+            for (size_t i = 0; i < r.size();) {
+                cd v = 0;
+                size_t j = i;
+                for (; j < r.size() && r[j].first == r[i].first; ++j) v += r[j].second;
+                kn_col.push_back(r[i].first);
+                kn_val.push_back(v);
+                i = j;
+            }
+            kn_ptr[g + 1] = (int32_t)kn_col.size();
+            std::vector<std::pair<int, cd>>().swap(r);
+        }
     }
-    m.coarse_refine = m.coarse_check > 1e-12;
-    if (m.coarse_refine) { m.Kd = Kd; m.Kl = Kl; } else { m.Kd.clear(); m.Kl.clear(); }
-    // dense inverse for small coarse problems: K^-1 e_g by block-tridiagonal solves
-    m.dense_coarse = nc <= 6144;
-    if (m.dense_coarse) {
-        m.Kinv.assign((size_t)nc * nc, cd(0));
-        parallel_for(nc, nthreads, [&](int col) {
-            std::vector<std::vector<cd>> w(m.nb);
-            for (int b = 0; b < m.nb; ++b) w[b].assign(m.blk_size[b], cd(0));
-            w[m.blk_of[col]][m.pos_in_blk[col]] = 1.0;
-            for (int b = 1; b < m.nb; ++b) {
-                const int nbk = m.blk_size[b], np = m.blk_size[b - 1];
-                for (int i = 0; i < nbk; ++i) {
-                    cd s = 0;
-                    for (int j = 0; j < np; ++j) s += m.Lo[b][(size_t)i * np + j] * w[b - 1][j];
-                    w[b][i] -= s;
-                }
-            }
-            std::vector<std::vector<cd>> x(m.nb);
-            for (int b = m.nb - 1; b >= 0; --b) {
-                const int nbk = m.blk_size[b];
-                std::vector<cd> r = w[b];
-                if (b + 1 < m.nb) {
-                    const int nn = m.blk_size[b + 1];
-                    for (int i = 0; i < nbk; ++i) {
-                        cd s = 0;
-                        for (int j = 0; j < nn; ++j) s += m.Up[b][(size_t)i * nn + j] * x[b + 1][j];
-                        r[i] -= s;
-                    }
-                }
-                x[b].assign(nbk, cd(0));
-                for (int i = 0; i < nbk; ++i) {
-                    cd s = 0;
-                    for (int j = 0; j < nbk; ++j) s += m.Dinv[b][(size_t)i * nbk + j] * r[j];
-                    x[b][i] = s;
-                }
-            }
-            if (m.coarse_refine) {
-                // one refinement step: r = e_col - K x, x += BT(r)
-                std::vector<std::vector<cd>> r(m.nb), dx(m.nb);
-                for (int b = 0; b < m.nb; ++b) {
-                    const int nbk = m.blk_size[b];
-                    r[b].assign(nbk, cd(0));
-                    if (b == m.blk_of[col]) r[b][m.pos_in_blk[col]] = 1.0;
-                    for (int i = 0; i < nbk; ++i) {
-                        cd s = 0;
-                        for (int j = 0; j < nbk; ++j) s += Kd[b][(size_t)i * nbk + j] * x[b][j];
-                        if (b > 0) for (int j = 0; j < m.blk_size[b - 1]; ++j) s += Kl[b][(size_t)i * m.blk_size[b - 1] + j] * x[b - 1][j];
-                        if (b + 1 < m.nb) for (int j = 0; j < m.blk_size[b + 1]; ++j) s += Kl[b + 1][(size_t)j * nbk + i] * x[b + 1][j];
-                        r[b][i] -= s;
-                    }
-                }
-                for (int b = 1; b < m.nb; ++b) {
-                    const int nbk = m.blk_size[b], np = m.blk_size[b - 1];
-                    for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < np; ++j) s += m.Lo[b][(size_t)i * np + j] * r[b - 1][j]; r[b][i] -= s; }
-                }
-                for (int b = m.nb - 1; b >= 0; --b) {
-                    const int nbk = m.blk_size[b];
-                    std::vector<cd> q = r[b];
-                    if (b + 1 < m.nb) {
-                        const int nn = m.blk_size[b + 1];
-                        for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < nn; ++j) s += m.Up[b][(size_t)i * nn + j] * dx[b + 1][j]; q[i] -= s; }
-                    }
-                    dx[b].assign(nbk, cd(0));
-                    for (int i = 0; i < nbk; ++i) { cd s = 0; for (int j = 0; j < nbk; ++j) s += m.Dinv[b][(size_t)i * nbk + j] * q[j]; dx[b][i] = s; }
-                }
-                for (int b = 0; b < m.nb; ++b) for (int i = 0; i < m.blk_size[b]; ++i) x[b][i] += dx[b][i];
-            }
-            for (int b = 0; b < m.nb; ++b)
-                for (int i = 0; i < m.blk_size[b]; ++i)
-                    m.Kinv[(size_t)m.perm[m.blk_start[b] + i] * nc + col] = x[b][i];
-        });
-    }
+    if (!coarse_factor(m, kn_ptr, kn_col, kn_val, nthreads, err)) return false;
     // ---- hanging-row preconditioner term C2 K^Lap C2^T (Remark on edge errors)
     m.mh_ptr.assign(m.n_dual + 1, 0); m.mh_col.clear(); m.mh_val.clear();
     if (!m.hblk_row0.empty()) {

@@ -4,6 +4,7 @@
 #pragma once
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -53,7 +54,7 @@ struct MasterEdge {
     struct Sub { int elem, side; double a, b; };
     std::vector<Sub> subs;        // conforming: 1 entry (a=1, b=0); hanging: fine sides
     int degree = 0;               // trace degree d (min incident degree)
-    int64_t Y2 = 0;               // twice the y coordinate of the edge midpoint (block ordering)
+    int64_t X2 = 0, Y2 = 0;       // twice the coordinates of the edge midpoint (coarse ordering)
 };
 
 struct Model {
@@ -71,7 +72,7 @@ struct Model {
     std::vector<std::pair<int, int>> side_edge;   // [4e+s] -> (edge, role 0 b / 1 c / 2 f)
     int64_t n_local = 0;
     int32_t n_vert = 0, n_coarse = 0;
-    std::vector<int64_t> coarse_Y2;               // twice the y of each coarse dof
+    std::vector<int64_t> coarse_X2, coarse_Y2;    // twice the x and y of each coarse dof
     // slots
     std::vector<int32_t> e1_slot, e1_row, e1_eall;
     std::vector<double> e1_sign;
@@ -95,23 +96,27 @@ struct Model {
     // factor
     std::vector<cd> sinv;                         // per element nE1^2, column-major
     double min_gap = 1e300;
-    // coarse factorisation (block tridiagonal over base rows)
-    int nb = 0;
-    std::vector<int32_t> blk_of;                  // coarse dof -> block
-    std::vector<int32_t> pos_in_blk;              // coarse dof -> position inside its block
-    std::vector<int32_t> blk_size, blk_start;     // block sizes and start in the permuted order
-    std::vector<int32_t> perm;                    // permuted position -> coarse dof
-    std::vector<std::vector<cd>> Dinv, Lo, Up;    // per block dense row-major
-    bool dense_coarse = false;                    // use a dense K^-1 instead
+    // coarse factorisation: nested dissection over base-grid lines, multifrontal elimination
+    struct CNode {
+        int f0 = 0, nF = 0;                       // fully summed unknowns: elimination positions [f0, f0+nF)
+        int depth = 0, parent = -1;               // tree level (root 0), parent node (-1 for roots)
+        std::vector<int> B;                       // boundary unknowns (elimination positions, ascending)
+        std::vector<cd> W, G, H;                  // A_FF^-1 (nF^2), A_BF W (nB x nF), W A_FB (nF x nB)
+    };
+    std::vector<CNode> cnode;                     // postorder: children before parents
+    std::vector<int32_t> cperm, cpos;             // elimination position <-> coarse dof
+    int c_depth = 0;                              // deepest level
+    std::vector<int32_t> kc_ptr, kc_col;          // K in CSR over elimination positions
+    std::vector<cd> kc_val;
+    bool dense_coarse = false;                    // use a dense K^-1 instead (elimination order)
     std::vector<cd> Kinv;                         // n_coarse^2 row-major when dense_coarse
     // diagnostics: relative residual ||K x - t|| / ||t|| of one coarse solve with a seeded
     // random t, and max_e ||S_E S_E^-1 - I||_max (computed when check_factor is set)
     bool check_factor = false;
     double coarse_check = -1, sinv_check = -1;
-    // block factorisation without pivoting across blocks: when the self-check residual exceeds
-    // 1e-12 the FP64 solves apply one step of iterative refinement with the assembled blocks
+    // pivoting stays inside each front: when the self-check residual exceeds 1e-12 the FP64
+    // solves apply one step of iterative refinement with the assembled K
     bool coarse_refine = false;
-    std::vector<std::vector<cd>> Kd, Kl;          // K_bb and K_{b,b-1} (kept for refinement)
     std::string err;
 };
 
@@ -123,6 +128,17 @@ void set_coefficients(Model& m, double k, const double* eps);
 int dispersion_l(const Model& m);
 bool classify(Model& m, int l, std::string& err);
 bool factor(Model& m, int nthreads, std::string& err);
+// nested-dissection factorisation of K given in CSR over coarse dofs (natural numbering)
+bool coarse_factor(Model& m, const std::vector<int32_t>& kn_ptr, const std::vector<int32_t>& kn_col,
+                   const std::vector<cd>& kn_val, int nthreads, std::string& err);
+// x = K^-1 t with the factor (vectors in elimination order)
+void coarse_solve_host(const Model& m, const std::vector<cd>& t, std::vector<cd>& x);
+
+// dense helpers of the factorisation (row-major complex); nthreads > 1 runs on the
+// factorisation's worker pool, which must not be re-entered from inside host_parallel
+void host_parallel(int n, int nthreads, const std::function<void(int)>& f);
+bool host_invert(int n, const std::vector<cd>& A, std::vector<cd>& inv, double& minpiv, int nthreads);
+void host_gemm(int M, int K, int N, const cd* A, const cd* B, cd* C, bool subtract, int nthreads);
 
 // entry of the element operator (interpolatory basis) for element e:
 // A[(a,b),(c,d)] = Kt[a,c] Mt[b,d] + Mt[a,c] Kt[b,d] + c_e Mt[a,c] Mt[b,d] + Robin.

@@ -259,42 +259,193 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
     }
 }
 
-// Coarse residual with the assembled blocks, all blocks at once (one warp per row):
-// r_b = t_b - (K_bb x_b + K_{b,b-1} x_{b-1} + K_{b,b+1} x_{b+1}); blocks row-major, vectors FP64.
-struct BlockK {
-    const double2* const* Kd;    // [nb] K_bb
-    const double2* const* Kl;    // [nb] K_{b,b-1} (b >= 1)
-    const double2* const* Ku;    // [nb] K_{b,b+1} (b < nb-1)
-    const int* start;            // [nb+1]
-    const int* row_blk;          // [n] block of each row
-    int nb, n;
-};
-__global__ void k_coarse_residual(BlockK B, const double2* __restrict__ x, const double2* __restrict__ t,
-                                  double2* __restrict__ r, int R, const int* __restrict__ done) {
+// ------------------------------------------------------------------ coarse solve
+// Nested-dissection solve of K x = t, one launch per tree level (see NDDev).  A CTA of 128
+// threads takes rows of one node's matrix for a block of RB right-hand sides, after staging
+// the node's input vector in shared memory: up to 4 rows (one warp per row, row-major
+// matrix) or, for rows of at most kNDShortRow entries, up to 128 rows (one thread per row,
+// column-major matrix); item.w selects the second form.
+__device__ __forceinline__ double2 ld_mat(const double2* a) { return __ldg(a); }
+__device__ __forceinline__ double2 ld_mat(const float2* a) {
+    const float2 v = __ldg(a);
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// forward level: y_F = t_F - (updates of the node's descendants), u_N = G_N y_F
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
+                                                    const double2* __restrict__ t, double2* __restrict__ y,
+                                                    double2* __restrict__ u, int R, const int* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][nF]: lanes read consecutive entries
+    const int4 it = items[blockIdx.x];
+    const int node = it.x, row0 = it.y, nrows = it.z;
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    const int f0 = d.f0[node], nF = d.nF[node];
+    const int64_t nc = d.nc, ul = d.u_len;
+    for (int i = threadIdx.x; i < nF; i += blockDim.x) {
+        const int pos = f0 + i;
+        const int c0 = d.ct_ptr[pos], c1 = d.ct_ptr[pos + 1];
+        for (int r = 0; r < RB; ++r) {
+            double2 v = make_double2(0.0, 0.0);
+            if (r < nr) {
+                v = t[(r0 + r) * nc + pos];
+                for (int a = c0; a < c1; ++a) {
+                    const double2 c = u[(r0 + r) * ul + d.ct_idx[a]];
+                    v.x -= c.x; v.y -= c.y;
+                }
+                if (row0 == 0) y[(r0 + r) * nc + pos] = v;
+            }
+            nd_sm[r * nF + i] = v;
+        }
+    }
+    __syncthreads();
+    const MT* G = (const MT*)d.G + d.g_off[node];
+    if (it.w) {
+        // short rows: one thread per row, G stored column-major (coalesced across threads)
+        const int row = row0 + threadIdx.x;
+        if (row >= row0 + nrows) return;
+        const int nB = d.nB[node];
+        double ax[RB], ay[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        for (int j = 0; j < nF; ++j) {
+            const double2 a = ld_mat(G + (int64_t)j * nB + row);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double2 v = nd_sm[r * nF + j];
+                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
+                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+            }
+        }
+        const int64_t uo = d.u_off[node] + row;
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            if (r < nr) u[(r0 + r) * ul + uo] = make_double2(ax[r], ay[r]);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
+        double ax[RB], ay[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        const MT* g = G + (int64_t)row * nF;
+        for (int j = lane; j < nF; j += 32) {
+            const double2 a = ld_mat(g + j);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double2 v = nd_sm[r * nF + j];
+                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
+                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            for (int o = 16; o > 0; o >>= 1) {
+                ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
+                ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
+            }
+        if (lane == 0) {
+            const int64_t uo = d.u_off[node] + row;
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < nr) u[(r0 + r) * ul + uo] = make_double2(ax[r], ay[r]);
+        }
+    }
+}
+
+// backward level: x_F = W y_F - H x_B = [W | -H] [y_F; x_B]
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __restrict__ items,
+                                                     const double2* __restrict__ y, double2* __restrict__ x, int R,
+                                                     const int* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][nF + nB]
+    const int4 it = items[blockIdx.x];
+    const int node = it.x, row0 = it.y, nrows = it.z;
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], n = nF + nB;
+    const int64_t nc = d.nc;
+    const int* bi = d.bidx + d.b_off[node];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int pos = i < nF ? f0 + i : bi[i - nF];
+        const double2* src = i < nF ? y : x;
+        for (int r = 0; r < RB; ++r) nd_sm[r * n + i] = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const MT* M = (const MT*)d.M + d.m_off[node];
+    if (it.w) {
+        // short rows: one thread per row, M stored column-major
+        const int row = row0 + threadIdx.x;
+        if (row >= row0 + nrows) return;
+        double ax[RB], ay[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        for (int j = 0; j < n; ++j) {
+            const double2 a = ld_mat(M + (int64_t)j * nF + row);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double2 v = nd_sm[r * n + j];
+                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
+                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax[r], ay[r]);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
+        double ax[RB], ay[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        const MT* mr = M + (int64_t)row * n;
+        for (int j = lane; j < n; j += 32) {
+            const double2 a = ld_mat(mr + j);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const double2 v = nd_sm[r * n + j];
+                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
+                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            for (int o = 16; o > 0; o >>= 1) {
+                ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
+                ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
+            }
+        if (lane == 0) {
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+                if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax[r], ay[r]);
+        }
+    }
+}
+
+// r = t - K x with K in CSR (one warp per row, all right-hand sides)
+__global__ void k_csr_residual(const int* __restrict__ ptr, const int* __restrict__ col,
+                               const double2* __restrict__ val, int n, const double2* __restrict__ x,
+                               const double2* __restrict__ t, double2* __restrict__ r, int R,
+                               const int* __restrict__ done) {
     if (done && *done) return;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (row >= B.n) return;
-    const int b = B.row_blk[row];
-    const int s0 = B.start[b], nb0 = B.start[b + 1] - s0, i = row - s0;
+    if (row >= n) return;
+    const int a0 = ptr[row], a1 = ptr[row + 1];
     for (int rr = 0; rr < R; ++rr) {
-        const double2* xr = x + (int64_t)rr * B.n;
+        const double2* xr = x + (int64_t)rr * n;
         double sx = 0, sy = 0;
-        auto acc = [&](const double2* M, int ncol, int c0) {
-            const double2* a = M + (int64_t)i * ncol;
-            for (int j = lane; j < ncol; j += 32) {
-                const double2 av = a[j], xv = xr[c0 + j];
-                sx = fma(av.x, xv.x, fma(-av.y, xv.y, sx));
-                sy = fma(av.x, xv.y, fma(av.y, xv.x, sy));
-            }
-        };
-        acc(B.Kd[b], nb0, s0);
-        if (b > 0) acc(B.Kl[b], B.start[b] - B.start[b - 1], B.start[b - 1]);
-        if (b + 1 < B.nb) acc(B.Ku[b], B.start[b + 2] - B.start[b + 1], B.start[b + 1]);
+        for (int a = a0 + lane; a < a1; a += 32) {
+            const double2 av = val[a], xv = xr[col[a]];
+            sx = fma(av.x, xv.x, fma(-av.y, xv.y, sx));
+            sy = fma(av.x, xv.y, fma(av.y, xv.x, sy));
+        }
         for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
         if (lane == 0) {
-            const double2 tv = t[(int64_t)rr * B.n + row];
-            r[(int64_t)rr * B.n + row] = make_double2(tv.x - sx, tv.y - sy);
+            const double2 tv = t[(int64_t)rr * n + row];
+            r[(int64_t)rr * n + row] = make_double2(tv.x - sx, tv.y - sy);
         }
     }
 }
@@ -877,22 +1028,26 @@ __global__ void k_store(KrylovDev K) {
     K.Zb[((int64_t)r * K.m + j) * K.nd + i] = K.zw[(int64_t)r * K.nd + i];
 }
 
-// CGS2 building blocks.  The rows of a length-nd vector are split into nchunk contiguous
-// chunks (one CTA each).  k_dots: partial[r][chunk][i] = sum_{rows in chunk} conj(V_i) w for
-// every i <= j, one warp per basis vector i.
-__global__ void __launch_bounds__(256) k_dots(KrylovDev K) {
-    if (K.ctl[1]) return;
-    const int j = K.ctl[0];
-    const int chunk = blockIdx.x, r = blockIdx.y;
-    const int rows = (K.nd + K.nchunk - 1) / K.nchunk;
-    const int r0 = chunk * rows, r1 = min(K.nd, r0 + rows);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double2* w = K.w + (int64_t)r * K.nd;
-    for (int i = warp; i <= j; i += (blockDim.x >> 5)) {
-        const double2* v = K.V + ((int64_t)r * (K.m + 1) + i) * K.nd;
+// CGS2 orthogonalisation of w against V_0..V_j, normalisation of V_{j+1} and the Givens
+// update of the Hessenberg column, in three kernels.  Each CTA owns one chunk of blockDim.x
+// consecutive rows of one right-hand side (grid nchunk x R); the cross-chunk sums are taken
+// by the last CTA of each right-hand side to finish (a counter per right-hand side, reset by
+// that CTA), so no kernel re-reduces the chunk partials of another.
+//   k_cgs_first:  h1 = V^H w
+//   k_cgs_second: w1 = w - V h1;  h2 = V^H w1, ||w1||^2
+//   k_cgs_final:  V_{j+1} = (w1 - V h2) / h_{j+1,j};  Givens rotation of column j
+// h_{j+1,j} starts from ||w1||^2 - ||h2||^2 (exact for orthonormal V) and is then corrected
+// with the exact norm of the stored vector, so V_{j+1} has unit norm to rounding either way.
+
+// warp-per-basis-vector partial dots of the chunk: partial[r][chunk][i] = sum conj(V_i) ws
+__device__ __forceinline__ void cgs_chunk_dots(const KrylovDev& K, int j, int r, int chunk, int q0, int rows,
+                                               const double2* ws) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i <= j; i += nw) {
+        const double2* v = K.V + ((int64_t)r * (K.m + 1) + i) * K.nd + q0;
         double sx = 0, sy = 0;
-        for (int q = r0 + lane; q < r1; q += 32) {
-            const double2 a = v[q], b = w[q];
+        for (int t = lane; t < rows; t += 32) {
+            const double2 a = v[t], b = ws[t];
             sx = fma(a.x, b.x, fma(a.y, b.y, sx));
             sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
         }
@@ -901,35 +1056,86 @@ __global__ void __launch_bounds__(256) k_dots(KrylovDev K) {
     }
 }
 
-// w -= sum_{i<=j} V_i h_i with h = the chunk sums of the partial dots (every CTA reduces them
-// itself); CTA 0 accumulates h into the Hessenberg column (pass 0 sets, pass 1 adds).  In
-// pass 1 each CTA also writes the partial squared norm of the new w to partial[..][m].
-__global__ void __launch_bounds__(256) k_axpy(KrylovDev K, int pass) {
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    __syncthreads();
+    return t;
+}
+
+// true in every thread of the CTA that finishes last among the nchunk CTAs of right-hand side r
+__device__ __forceinline__ bool cgs_last_chunk(const KrylovDev& K, int r, int* flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = (atomicAdd(K.cnt + r, 1) == K.nchunk - 1);
+    __syncthreads();
+    const bool last = *flag;
+    if (last) {
+        __threadfence();
+        if (threadIdx.x == 0) K.cnt[r] = 0;
+    }
+    return last;
+}
+
+// true in every thread of the CTA that finishes last among the R per-right-hand-side winners
+__device__ __forceinline__ bool cgs_last_chunk_all(const KrylovDev& K, int* flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = (atomicAdd(K.cnt + K.R, 1) == K.R - 1);
+    __syncthreads();
+    const bool last = *flag;
+    if (last) {
+        __threadfence();
+        if (threadIdx.x == 0) K.cnt[K.R] = 0;
+    }
+    return last;
+}
+
+// out[i] = sum over chunks of partial[r][c][i], i <= j (and slot m when with_m), one warp per i
+__device__ __forceinline__ void cgs_reduce(const KrylovDev& K, int j, int r, double2* out, bool with_m) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int top = with_m ? j + 1 : j;
+    for (int ii = warp; ii <= top; ii += nw) {
+        const int i = ii <= j ? ii : K.m;
+        double sx = 0, sy = 0;
+        for (int c = lane; c < K.nchunk; c += 32) {
+            const double2 v = __ldcg(K.partial + ((int64_t)r * K.nchunk + c) * (K.m + 1) + i);
+            sx += v.x; sy += v.y;
+        }
+        for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
+        if (lane == 0) out[ii] = make_double2(sx, sy);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_cgs_first(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
-    __shared__ double2 h[256];
-    __shared__ double red[8];
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        double sx = 0, sy = 0;
-        for (int c = 0; c < K.nchunk; ++c) {
-            const double2 v = K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + i];
-            sx += v.x; sy += v.y;
-        }
-        h[i] = make_double2(sx, sy);
-    }
+    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
+    __shared__ double2 ws[256];
+    __shared__ int last_f;
+    if ((int)threadIdx.x < rows) ws[threadIdx.x] = K.w[(int64_t)r * K.nd + q0 + threadIdx.x];
     __syncthreads();
-    if (chunk == 0) {
-        double2* hc = K.hcol + (int64_t)r * (K.m + 1);
-        for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-            if (pass == 0) hc[i] = h[i];
-            else { hc[i].x += h[i].x; hc[i].y += h[i].y; }
-        }
-    }
-    const int rows = (K.nd + K.nchunk - 1) / K.nchunk;
-    const int r0 = chunk * rows, r1 = min(K.nd, r0 + rows);
+    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
+}
+
+__global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
+    if (K.ctl[1]) return;
+    const int j = K.ctl[0];
+    const int chunk = blockIdx.x, r = blockIdx.y;
+    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
+    __shared__ double2 ws[256], h[256];
+    __shared__ double red[8];
+    __shared__ int last_f;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = K.hcol[(int64_t)r * (K.m + 1) + i];
+    __syncthreads();
     double nrm = 0;
-    for (int q = r0 + threadIdx.x; q < r1; q += blockDim.x) {
+    if ((int)threadIdx.x < rows) {
+        const int64_t q = q0 + threadIdx.x;
         double2 w = K.w[(int64_t)r * K.nd + q];
         for (int i = 0; i <= j; ++i) {
             const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
@@ -938,111 +1144,135 @@ __global__ void __launch_bounds__(256) k_axpy(KrylovDev K, int pass) {
             w.y -= v.x * hh.y + v.y * hh.x;
         }
         K.w[(int64_t)r * K.nd + q] = w;
-        nrm += w.x * w.x + w.y * w.y;
+        ws[threadIdx.x] = w;
+        nrm = w.x * w.x + w.y * w.y;
     }
-    if (pass == 1) {
-        for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    nrm = block_sum(nrm, red);          // also orders the ws writes before the dots
+    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nrm, 0.0);
+    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    if (cgs_last_chunk(K, r, &last_f)) {
+        double2* h2 = K.h2 + (int64_t)r * (K.m + 1);
+        cgs_reduce(K, j, r, h2, true);           // h2[0..j]; h2[j+1] = (||w1||^2, 0)
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-            K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m].x = t;
+            double s = h2[j + 1].x;
+            for (int i = 0; i <= j; ++i) s -= h2[i].x * h2[i].x + h2[i].y * h2[i].y;
+            K.hn[r] = s > 0 ? sqrt(s) : 0.0;
         }
     }
 }
 
-// Hessenberg column j, Givens rotations, residual estimate, convergence flags.  One CTA
-// per right-hand side: the column is rotated in shared memory and written back once.
-__global__ void k_givens(KrylovDev K) {
+__global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
-    const int r = blockIdx.x;
-    __shared__ double2 Hc[256];
+    const int chunk = blockIdx.x, r = blockIdx.y;
+    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
+    __shared__ double2 h[256];
+    __shared__ double red[8];
+    __shared__ int last_f;
     __shared__ double hn_s;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = K.h2[(int64_t)r * (K.m + 1) + i];
+    __syncthreads();
+    const double hp = K.hn[r];
+    const double sc = hp > 0 ? 1.0 / hp : 1.0;
+    double2* vnew = K.V + ((int64_t)r * (K.m + 1) + j + 1) * K.nd;
+    double nv = 0;
+    if ((int)threadIdx.x < rows) {
+        const int64_t q = q0 + threadIdx.x;
+        double2 w = K.w[(int64_t)r * K.nd + q];
+        for (int i = 0; i <= j; ++i) {
+            const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
+            const double2 hh = h[i];
+            w.x -= v.x * hh.x - v.y * hh.y;
+            w.y -= v.x * hh.y + v.y * hh.x;
+        }
+        w.x *= sc; w.y *= sc;
+        vnew[q] = w;
+        nv = w.x * w.x + w.y * w.y;
+    }
+    nv = block_sum(nv, red);
+    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nv, 0.0);
+    if (!cgs_last_chunk(K, r, &last_f)) return;
+
+    // ---- last CTA of right-hand side r: exact norm, Hessenberg column, Givens
+    __shared__ double2 Hc[256];
+    __shared__ double2 nvs;
     if (threadIdx.x < 32) {
         double s = 0;
-        for (int c = threadIdx.x; c < K.nchunk; c += 32) s += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
+        for (int c = threadIdx.x; c < K.nchunk; c += 32) s += __ldcg(K.partial + ((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m).x;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) hn_s = sqrt(s);
+        if (threadIdx.x == 0) nvs = make_double2(s, 0.0);
     }
-    const double2* hc = K.hcol + (int64_t)r * (K.m + 1);
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hc[i] = hc[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double hn = hn_s;
-        Hc[j + 1] = make_double2(hn, 0.0);
-        if (!K.rdone[r]) {
-            const double* cs = K.cs + (int64_t)r * K.m;
-            const double2* sn = K.sn + (int64_t)r * K.m;
-            for (int i = 0; i < j; ++i) {
-                const double2 a = Hc[i], b = Hc[i + 1];
-                const double c = cs[i];
-                const double2 s = sn[i];
-                const double2 t0 = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
-                const double2 t1 = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
-                Hc[i] = t0; Hc[i + 1] = t1;
-            }
-            const double2 a = Hc[j];
-            const double bb = Hc[j + 1].x;            // real, >= 0
-            double c, sx, sy;
-            const double aa = sqrt(a.x * a.x + a.y * a.y);
-            if (bb == 0.0) { c = 1; sx = 0; sy = 0; }
-            else if (aa == 0.0) { c = 0; sx = 1; sy = 0; }
-            else {
-                const double den = sqrt(aa * aa + bb * bb);
-                c = aa / den;
-                sx = (a.x / aa) * bb / den;
-                sy = (a.y / aa) * bb / den;
-            }
-            K.cs[(int64_t)r * K.m + j] = c;
-            K.sn[(int64_t)r * K.m + j] = make_double2(sx, sy);
-            Hc[j] = make_double2(c * a.x + sx * bb, c * a.y + sy * bb);
-            Hc[j + 1] = make_double2(0, 0);
-            double2* g = K.g + (int64_t)r * (K.m + 1);
-            const double2 gj = g[j];
-            g[j] = make_double2(c * gj.x, c * gj.y);
-            g[j + 1] = make_double2(-(sx * gj.x + sy * gj.y), -(sx * gj.y - sy * gj.x));
-            const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / K.bnorm[r];
-            K.resid[r] = res;
-            K.iters[r] = j + 1;
-            if (res <= K.tol || hn == 0.0) K.rdone[r] = 1;
+    const double nvt = nvs.x;
+    const double hn = nvt > 0 ? sqrt(nvt) / sc : 0.0;
+    if (nvt > 0 && fabs(nvt - 1.0) > 1e-12) {
+        // the Pythagorean estimate was off (near breakdown): rescale V_{j+1} to unit norm
+        const double f = 1.0 / sqrt(nvt);
+        for (int q = threadIdx.x; q < K.nd; q += blockDim.x) {
+            double2 v = __ldcg(vnew + q);
+            v.x *= f; v.y *= f;
+            vnew[q] = v;
         }
+    }
+    const double2* h1 = K.hcol + (int64_t)r * (K.m + 1);
+    const double2* h2 = K.h2 + (int64_t)r * (K.m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        const double2 a = __ldcg(h1 + i), b = __ldcg(h2 + i);
+        Hc[i] = make_double2(a.x + b.x, a.y + b.y);
+    }
+    if (threadIdx.x == 0) { Hc[j + 1] = make_double2(hn, 0.0); hn_s = hn; }
+    __syncthreads();
+    if (threadIdx.x == 0 && !K.rdone[r]) {
+        const double* cs = K.cs + (int64_t)r * K.m;
+        const double2* sn = K.sn + (int64_t)r * K.m;
+        for (int i = 0; i < j; ++i) {
+            const double2 a = Hc[i], b = Hc[i + 1];
+            const double c = cs[i];
+            const double2 s = sn[i];
+            // t0 = c a + s b ; t1 = -conj(s) a + c b
+            const double2 t0 = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+            const double2 t1 = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+            Hc[i] = t0; Hc[i + 1] = t1;
+        }
+        const double2 a = Hc[j];
+        const double bb = Hc[j + 1].x;            // real, >= 0
+        double c, sx, sy;
+        const double aa = sqrt(a.x * a.x + a.y * a.y);
+        if (bb == 0.0) { c = 1; sx = 0; sy = 0; }
+        else if (aa == 0.0) { c = 0; sx = 1; sy = 0; }
+        else {
+            const double den = sqrt(aa * aa + bb * bb);
+            c = aa / den;
+            sx = (a.x / aa) * bb / den;
+            sy = (a.y / aa) * bb / den;
+        }
+        K.cs[(int64_t)r * K.m + j] = c;
+        K.sn[(int64_t)r * K.m + j] = make_double2(sx, sy);
+        Hc[j] = make_double2(c * a.x + sx * bb, c * a.y + sy * bb);
+        Hc[j + 1] = make_double2(0, 0);
+        double2* g = K.g + (int64_t)r * (K.m + 1);
+        const double2 gj = g[j];
+        g[j] = make_double2(c * gj.x, c * gj.y);
+        // g[j+1] = -conj(s) g_j
+        g[j + 1] = make_double2(-(sx * gj.x + sy * gj.y), -(sx * gj.y - sy * gj.x));
+        const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / K.bnorm[r];
+        K.resid[r] = res;
+        K.iters[r] = j + 1;
+        if (res <= K.tol || hn_s == 0.0) K.rdone[r] = 1;
     }
     __syncthreads();
     // columns past a right-hand side's convergence are never read back
     double2* Hcol = K.H + ((int64_t)r * K.m + j) * (K.m + 1);
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hcol[i] = Hc[i];
-}
 
-// advance the column counter once every RHS has been rotated; stop at convergence of all or
-// at the restart boundary
-__global__ void k_advance(KrylovDev K) {
-    if (K.ctl[1]) return;
-    const int j = K.ctl[0];
-    int all = 1;
-    for (int r = 0; r < K.R; ++r) all &= K.rdone[r];
-    if (all || j + 1 >= K.m) K.ctl[1] = 1;
-    K.ctl[0] = j + 1;
-}
-
-// V[j+1] = w / h_{j+1,j}, the norm reduced once per CTA from the chunk partials
-__global__ void k_normalize(KrylovDev K) {
-    if (K.ctl[1]) return;
-    const int j = K.ctl[0];
-    const int r = blockIdx.y;
-    __shared__ double inv_s;
-    if (threadIdx.x < 32) {
-        double s = 0;
-        for (int c = threadIdx.x; c < K.nchunk; c += 32) s += K.partial[((int64_t)r * K.nchunk + c) * (K.m + 1) + K.m].x;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) { const double hn = sqrt(s); inv_s = hn > 0 ? 1.0 / hn : 0.0; }
-    }
-    __syncthreads();
-    const double inv = inv_s;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < K.nd; q += gridDim.x * blockDim.x) {
-        const double2 w = K.w[(int64_t)r * K.nd + q];
-        K.V[((int64_t)r * (K.m + 1) + j + 1) * K.nd + q] = make_double2(w.x * inv, w.y * inv);
+    // the last right-hand side to finish advances the column counter; it stops the
+    // iteration once every right-hand side has converged or at the restart boundary
+    if (cgs_last_chunk_all(K, &last_f) && threadIdx.x == 0) {
+        int all = 1;
+        for (int rr = 0; rr < K.R; ++rr) all &= __ldcg(K.rdone + rr);
+        if (all || j + 1 >= K.m) K.ctl[1] = 1;
+        K.ctl[0] = j + 1;
     }
 }
 
@@ -1182,11 +1412,66 @@ template void launch_jump_gather<float>(const DevModel&, const void*, const doub
 template void launch_pre<double>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
 template void launch_pre<float>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
 
-void launch_coarse_residual(const double2* const* Kd, const double2* const* Kl, const double2* const* Ku,
-                            const int* start, const int* row_blk, int nb, int n, const double2* x, const double2* t,
-                            double2* r, int R, const int* done, cudaStream_t st) {
-    BlockK B{Kd, Kl, Ku, start, row_blk, nb, n};
-    k_coarse_residual<<<(n + 3) / 4, 128, 0, st>>>(B, x, t, r, R, done);
+static constexpr int kNDSmemMax = 200 * 1024;
+int nd_rhs_block(int smem_rows, int R) {
+    int rb = 8;
+    while (rb > 1 && (rb >= 2 * R || (size_t)smem_rows * rb * sizeof(double2) > (size_t)kNDSmemMax)) rb >>= 1;
+    return rb;
+}
+template <class MT, int RB>
+static void nd_attr() {
+    cudaFuncSetAttribute(k_nd_forward<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
+    cudaFuncSetAttribute(k_nd_backward<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
+}
+void nd_set_smem_limits() {
+    nd_attr<double2, 1>(); nd_attr<double2, 2>(); nd_attr<double2, 4>(); nd_attr<double2, 8>();
+    nd_attr<float2, 1>(); nd_attr<float2, 2>(); nd_attr<float2, 4>(); nd_attr<float2, 8>();
+}
+template <class MT, int RB>
+static void nd_fwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* t, double2* y,
+                     double2* u, int R, const int* done, cudaStream_t st) {
+    const size_t sm = std::max<size_t>(16, (size_t)smem_rows * RB * sizeof(double2));
+    k_nd_forward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, t, y, u, R, done);
+}
+template <class MT, int RB>
+static void nd_bwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* y, double2* x,
+                     int R, const int* done, cudaStream_t st) {
+    const size_t sm = std::max<size_t>(16, (size_t)smem_rows * RB * sizeof(double2));
+    k_nd_backward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, y, x, R, done);
+}
+void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st) {
+    if (nitems <= 0) return;
+    const int rb = nd_rhs_block(smem_rows, R);
+#define ND_F(RBV)                                                                             \
+    if (f32) nd_fwd_t<float2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);        \
+    else nd_fwd_t<double2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);
+    switch (rb) {
+        case 8: ND_F(8) break;
+        case 4: ND_F(4) break;
+        case 2: ND_F(2) break;
+        default: ND_F(1)
+    }
+#undef ND_F
+}
+void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
+                        double2* x, int R, const int* done, cudaStream_t st) {
+    if (nitems <= 0) return;
+    const int rb = nd_rhs_block(smem_rows, R);
+#define ND_B(RBV)                                                                          \
+    if (f32) nd_bwd_t<float2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);        \
+    else nd_bwd_t<double2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);
+    switch (rb) {
+        case 8: ND_B(8) break;
+        case 4: ND_B(4) break;
+        case 2: ND_B(2) break;
+        default: ND_B(1)
+    }
+#undef ND_B
+}
+void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
+                         const double2* t, double2* r, int R, const int* done, cudaStream_t st) {
+    k_csr_residual<<<(n + 3) / 4, 128, 0, st>>>(ptr, col, val, n, x, t, r, R, done);
 }
 void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st) {
     k_dinv<<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, x, y, 1, done);
@@ -1247,14 +1532,10 @@ template void launch_pre_krylov<double>(const DevModel&, const KrylovDev&, void*
 template void launch_pre_krylov<float>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
 
 void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st) {
-    const dim3 gv((K.nd + 255) / 256, K.R), gc(K.nchunk, K.R);
-    for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<gc, 256, 0, st>>>(K);
-        k_axpy<<<gc, 256, 0, st>>>(K, pass);
-    }
-    k_normalize<<<dim3(std::min(152, (K.nd + 255) / 256), K.R), 256, 0, st>>>(K);
-    k_givens<<<K.R, 64, 0, st>>>(K);
-    k_advance<<<1, 1, 0, st>>>(K);
+    const dim3 gc(K.nchunk, K.R);
+    k_cgs_first<<<gc, K.chunk, 0, st>>>(K);
+    k_cgs_second<<<gc, K.chunk, 0, st>>>(K);
+    k_cgs_final<<<gc, K.chunk, 0, st>>>(K);
 }
 void launch_fetch(const KrylovDev& K, cudaStream_t st) {
     k_fetch<<<dim3((K.nd + 255) / 256, K.R), 256, 0, st>>>(K);

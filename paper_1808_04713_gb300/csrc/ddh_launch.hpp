@@ -14,7 +14,8 @@ struct KrylovDev {
     double2* V; double2* Zb; double2* H; double* cs; double2* sn; double2* g; double* bnorm;
     double* resid; int* ctl; int* rdone; int* iters; double2* partial; double2* hcol; double2* w;
     double2* vin; double2* zw;
-    int nd, m, R, nchunk; double tol;
+    double2* h2; double* hn; int* cnt;   // second CGS projection, norm estimate, chunk counters
+    int nd, m, R, nchunk, chunk; double tol;
 };
 
 template <class T>
@@ -33,9 +34,39 @@ template <class T>
 void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, double2* m, double2* z, int lumped,
                 int R, const int* done, cudaStream_t st);
 
-void launch_coarse_residual(const double2* const* Kd, const double2* const* Kl, const double2* const* Ku,
-                            const int* start, const int* row_blk, int nb, int n, const double2* x, const double2* t,
-                            double2* r, int R, const int* done, cudaStream_t st);
+// Nested-dissection factor of the coarse matrix on the device (elimination order).  Per
+// node: fully summed positions [f0, f0+nF), boundary positions bidx[b_off .. b_off+nB),
+// G (nB x nF) at g_off and M = [W | -H] (nF x (nF+nB)) at m_off, row-major, of element type
+// double2 or float2; the forward updates G y_F of node N live at u[u_off[N] ..] ([R][u_len]).
+// ct_ptr/ct_idx list, per position, the update entries that subtract into it.
+struct NDDev {
+    const int* f0 = nullptr;
+    const int* nF = nullptr;
+    const int* nB = nullptr;
+    const int64_t* b_off = nullptr;
+    const int* bidx = nullptr;
+    const int64_t* g_off = nullptr;
+    const int64_t* m_off = nullptr;
+    const int64_t* u_off = nullptr;
+    const int* ct_ptr = nullptr;
+    const int64_t* ct_idx = nullptr;
+    const void* G = nullptr;
+    const void* M = nullptr;
+    int64_t u_len = 0;
+    int nc = 0;
+};
+// one tree level: items {node, first row, row count, short-row form}; a node whose rows have
+// at most kNDShortRow entries stores that matrix column-major and takes 128 rows per CTA
+constexpr int kNDShortRow = 64;
+void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st);
+void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
+                        double2* x, int R, const int* done, cudaStream_t st);
+int nd_rhs_block(int smem_rows, int R);
+void nd_set_smem_limits();   // once per device before the first (captured) launch
+// r = t - K x, K in CSR (R right-hand sides, [R][n])
+void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
+                         const double2* t, double2* r, int R, const int* done, cudaStream_t st);
 void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st);
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st);

@@ -147,9 +147,10 @@ bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, 
     for (int e = 0; e < n_elem; ++e)
         for (int s = 0; s < 4; ++s)
             if (m.side_edge[4 * e + s].first < 0) { err = "unmatched element side"; return false; }
-    // edge midpoints (twice y) for the coarse block ordering
+    // edge midpoints (twice the coordinates) for the coarse ordering
     for (auto& ed : m.edges) {
         const Elem& E = m.el[ed.elem];
+        ed.X2 = ed.side < 2 ? (ed.side == 0 ? 2 * E.X0 : 2 * E.X1) : (E.X0 + E.X1);
         ed.Y2 = ed.side < 2 ? (E.Y0 + E.Y1) : (ed.side == 2 ? 2 * E.Y0 : 2 * E.Y1);
     }
     return true;
@@ -277,7 +278,7 @@ int edge_top(const MasterEdge& ed, int lcut) { return ed.kind == 2 ? ed.degree :
 // Number the coarse dofs and compute the slot expressions for constraint count lcut.
 // Fills, per element, the list of type-1 edge slots and the expression of every other
 // non-interior slot.  Returns the number of coarse dofs.
-int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* Y2) {
+int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* X2, std::vector<int64_t>* Y2) {
     std::unordered_set<uint64_t> hanging;
     for (auto& ed : m.edges) {
         if (ed.kind != 2) continue;
@@ -306,6 +307,7 @@ int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* Y2) {
                 const uint64_t key = pt_key(xs[a], ys[b]);
                 if (hanging.count(key) || sl.vert.count(key)) continue;
                 sl.vert[key] = nd++;
+                if (X2) X2->push_back(2 * xs[a]);
                 if (Y2) Y2->push_back(2 * ys[b]);
             }
     }
@@ -316,6 +318,7 @@ int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* Y2) {
         sl.edof[ei].assign(ed.degree + 1, -1);
         for (int k = 2; k <= edge_top(ed, sl.lcut); ++k) {
             sl.edof[ei][k] = nd++;
+            if (X2) X2->push_back(ed.X2);
             if (Y2) Y2->push_back(ed.Y2);
         }
     }
@@ -328,8 +331,9 @@ bool classify(Model& m, int l, std::string& err) {
         m.l = l;
         const int E = (int)m.el.size();
         Slaver sl(m, l);
+        m.coarse_X2.clear();
         m.coarse_Y2.clear();
-        m.n_coarse = number_coarse(m, sl, &m.coarse_Y2);
+        m.n_coarse = number_coarse(m, sl, &m.coarse_X2, &m.coarse_Y2);
         // per-element slots
         m.e1_slot.clear(); m.e1_row.clear(); m.e1_eall.clear(); m.e1_sign.clear();
         m.t_slot.clear(); m.t_ptr.assign(1, 0); m.t_col.clear(); m.t_w.clear();
@@ -451,7 +455,7 @@ bool classify(Model& m, int l, std::string& err) {
         // conforming numbering (every constraint primal) for the FP64 primal residual:
         // vertices, all edge bubbles 2..d, interior bubbles
         Slaver sc(m, 1 << 30);
-        int nconf = number_coarse(m, sc, nullptr);
+        int nconf = number_coarse(m, sc, nullptr, nullptr);
         m.cf_ptr.assign(1, 0); m.cf_col.clear(); m.cf_w.clear();
         for (int e = 0; e < E; ++e) {
             const Elem& El = m.el[e];
