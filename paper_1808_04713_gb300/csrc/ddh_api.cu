@@ -380,17 +380,33 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             for (int a = 0; a < (ms ? n : N.nF); ++a)
                 for (int b = 0; b < (ms ? N.nF : n); ++b) Mall.push_back(z(ms ? Mij(b, a) : Mij(a, b)));
         }
-        // update entries subtracting into each position (from every node whose boundary has it)
-        std::vector<int> ct_ptr(nc + 1, 0);
-        for (int id = 0; id < nn; ++id) for (int b : m.cnode[id].B) ct_ptr[b + 1]++;
-        for (int i = 0; i < nc; ++i) ct_ptr[i + 1] += ct_ptr[i];
-        std::vector<int64_t> ct_idx(std::max(1, ct_ptr[nc]));
+        // the children's forward amounts for every front entry (F first, then B)
+        std::vector<int64_t> s_off(nn), src;
         {
-            std::vector<int> fill(ct_ptr.begin(), ct_ptr.end() - 1);
+            std::vector<std::vector<int>> kids(nn);
+            for (int id = 0; id < nn; ++id)
+                if (m.cnode[id].parent >= 0) kids[m.cnode[id].parent].push_back(id);
             for (int id = 0; id < nn; ++id) {
-                const auto& B = m.cnode[id].B;
-                for (size_t k = 0; k < B.size(); ++k) ct_idx[fill[B[k]]++] = u_off[id] + (int64_t)k;
+                const auto& N = m.cnode[id];
+                const int nI = N.nF + (int)N.B.size();
+                s_off[id] = (int64_t)src.size() / 2;
+                src.resize(src.size() + 2 * (size_t)nI, -1);
+                int64_t* sp = src.data() + 2 * s_off[id];
+                for (int c : kids[id]) {
+                    const auto& Bc = m.cnode[c].B;
+                    for (size_t k = 0; k < Bc.size(); ++k) {
+                        const int pos = Bc[k];
+                        int i;
+                        if (pos >= N.f0 && pos < N.f0 + N.nF) i = pos - N.f0;
+                        else i = N.nF + (int)(std::lower_bound(N.B.begin(), N.B.end(), pos) - N.B.begin());
+                        int64_t* slot = sp + 2 * i;
+                        if (slot[0] < 0) slot[0] = u_off[c] + (int64_t)k;
+                        else if (slot[1] < 0) slot[1] = u_off[c] + (int64_t)k;
+                        else return fail(ctx, DDH_ERR_INVALID_ARG, "coarse tree node with more than two children");
+                    }
+                }
             }
+            if (src.empty()) src.assign(2, -1);
         }
         // work items per level: 4 rows per CTA; a forward item also for nodes with no boundary
         std::vector<int4> items;
@@ -401,7 +417,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             ctx->nd_fwd_off[lv] = (int)items.size();
             for (int id = 0; id < nn; ++id) {
                 const auto& N = m.cnode[id];
-                if (N.depth != lv || N.nF == 0) continue;
+                if (N.depth != lv || N.nF + (int)N.B.size() == 0) continue;
                 const int rows = (int)N.B.size();
                 const int sh = N.nF <= kNDShortRow, step = sh ? 128 : 4;
                 for (int r0 = 0; r0 == 0 || r0 < rows; r0 += step) items.push_back(make_int4(id, r0, std::min(step, rows - r0), sh));
@@ -431,8 +447,8 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, g_off, &D.g_off))) return st;
         if ((st = upload(ctx, m_off, &D.m_off))) return st;
         if ((st = upload(ctx, u_off, &D.u_off))) return st;
-        if ((st = upload(ctx, ct_ptr, &D.ct_ptr))) return st;
-        if ((st = upload(ctx, ct_idx, &D.ct_idx))) return st;
+        if ((st = upload(ctx, s_off, &D.s_off))) return st;
+        if ((st = upload(ctx, src, &D.src))) return st;
         const double2* a;
         if ((st = upload(ctx, Gall, &a))) return st;
         D.G = a;

@@ -261,70 +261,70 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
 
 // ------------------------------------------------------------------ coarse solve
 // Nested-dissection solve of K x = t, one launch per tree level (see NDDev).  A CTA of 128
-// threads takes rows of one node's matrix for a block of RB right-hand sides, after staging
-// the node's input vector in shared memory: up to 4 rows (one warp per row, row-major
-// matrix) or, for rows of at most kNDShortRow entries, up to 128 rows (one thread per row,
-// column-major matrix); item.w selects the second form.
+// threads takes rows of one node's matrix for a block of RB right-hand sides after staging
+// the node's input vector in shared memory ([RB][stride], odd stride against bank
+// conflicts).  Long rows: one warp per row, lanes across the row.  Short rows: each lane
+// owns one (row, right-hand side) pair and runs along the row, so that every lane of the
+// (narrow) FP64 pipe does useful work even when rows are few and short.
 __device__ __forceinline__ double2 ld_mat(const double2* a) { return __ldg(a); }
 __device__ __forceinline__ double2 ld_mat(const float2* a) {
     const float2 v = __ldg(a);
     return make_double2((double)v.x, (double)v.y);
 }
+__device__ __forceinline__ double2 nd_pull(const double2* u, int64_t base, const int64_t* src, int64_t i) {
+    const int64_t a = src[2 * i], b = src[2 * i + 1];
+    double2 s = make_double2(0.0, 0.0);
+    if (a >= 0) { const double2 v = u[base + a]; s.x += v.x; s.y += v.y; }
+    if (b >= 0) { const double2 v = u[base + b]; s.x += v.x; s.y += v.y; }
+    return s;
+}
 
-// forward level: y_F = t_F - (updates of the node's descendants), u_N = G_N y_F
+// forward level: y_F = t_F - w_F, u_N = w_B + G_N y_F (w = the children's amounts)
 template <class MT, int RB>
 __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
                                                     const double2* __restrict__ t, double2* __restrict__ y,
                                                     double2* __restrict__ u, int R, const int* __restrict__ done) {
     if (done && *done) return;
-    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][nF]: lanes read consecutive entries
+    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][sF]
     const int4 it = items[blockIdx.x];
     const int node = it.x, row0 = it.y, nrows = it.z;
     const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
-    const int f0 = d.f0[node], nF = d.nF[node];
-    const int64_t nc = d.nc, ul = d.u_len;
+    const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], sF = nF | 1;
+    const int64_t nc = d.nc, ul = d.u_len, so = d.s_off[node], uo = d.u_off[node];
     for (int i = threadIdx.x; i < nF; i += blockDim.x) {
         const int pos = f0 + i;
-        const int c0 = d.ct_ptr[pos], c1 = d.ct_ptr[pos + 1];
         for (int r = 0; r < RB; ++r) {
             double2 v = make_double2(0.0, 0.0);
             if (r < nr) {
+                const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + i);
                 v = t[(r0 + r) * nc + pos];
-                for (int a = c0; a < c1; ++a) {
-                    const double2 c = u[(r0 + r) * ul + d.ct_idx[a]];
-                    v.x -= c.x; v.y -= c.y;
-                }
+                v.x -= w.x; v.y -= w.y;
                 if (row0 == 0) y[(r0 + r) * nc + pos] = v;
             }
-            nd_sm[r * nF + i] = v;
+            nd_sm[r * sF + i] = v;
         }
     }
     __syncthreads();
     const MT* G = (const MT*)d.G + d.g_off[node];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (it.w) {
-        // short rows: one thread per row, G stored column-major (coalesced across threads)
-        const int row = row0 + threadIdx.x;
-        if (row >= row0 + nrows) return;
-        const int nB = d.nB[node];
-        double ax[RB], ay[RB];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
-        for (int j = 0; j < nF; ++j) {
-            const double2 a = ld_mat(G + (int64_t)j * nB + row);
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * nF + j];
-                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
-                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+        constexpr int RPW = 32 / RB;                      // rows per warp and pass
+        const int r = lane % RB;
+        for (int row = row0 + warp * RPW + lane / RB; row < row0 + nrows; row += 4 * RPW) {
+            double ax = 0.0, ay = 0.0;
+            for (int j = 0; j < nF; ++j) {
+                const double2 a = ld_mat(G + (int64_t)j * nB + row);
+                const double2 v = nd_sm[r * sF + j];
+                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+            }
+            if (r < nr) {
+                const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + nF + row);
+                u[(r0 + r) * ul + uo + row] = make_double2(w.x + ax, w.y + ay);
             }
         }
-        const int64_t uo = d.u_off[node] + row;
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-            if (r < nr) u[(r0 + r) * ul + uo] = make_double2(ax[r], ay[r]);
         return;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
         double ax[RB], ay[RB];
 #pragma unroll
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
             const double2 a = ld_mat(g + j);
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * nF + j];
+                const double2 v = nd_sm[r * sF + j];
                 ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
                 ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
             }
@@ -345,11 +345,14 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
                 ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
                 ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
             }
-        if (lane == 0) {
-            const int64_t uo = d.u_off[node] + row;
+        if (lane < nr) {
+            // lane r writes right-hand side r (register arrays indexed by a constant only)
+            double sx = 0.0, sy = 0.0;
 #pragma unroll
             for (int r = 0; r < RB; ++r)
-                if (r < nr) u[(r0 + r) * ul + uo] = make_double2(ax[r], ay[r]);
+                if (r == lane) { sx = ax[r]; sy = ay[r]; }
+            const double2 w = nd_pull(u, (r0 + lane) * ul, d.src, so + nF + row);
+            u[(r0 + lane) * ul + uo + row] = make_double2(w.x + sx, w.y + sy);
         }
     }
 }
@@ -360,42 +363,36 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
                                                      const double2* __restrict__ y, double2* __restrict__ x, int R,
                                                      const int* __restrict__ done) {
     if (done && *done) return;
-    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][nF + nB]
+    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][sn]
     const int4 it = items[blockIdx.x];
     const int node = it.x, row0 = it.y, nrows = it.z;
     const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
-    const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], n = nF + nB;
+    const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], n = nF + nB, sn = n | 1;
     const int64_t nc = d.nc;
     const int* bi = d.bidx + d.b_off[node];
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int pos = i < nF ? f0 + i : bi[i - nF];
         const double2* src = i < nF ? y : x;
-        for (int r = 0; r < RB; ++r) nd_sm[r * n + i] = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
+        for (int r = 0; r < RB; ++r) nd_sm[r * sn + i] = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
     }
     __syncthreads();
     const MT* M = (const MT*)d.M + d.m_off[node];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (it.w) {
-        // short rows: one thread per row, M stored column-major
-        const int row = row0 + threadIdx.x;
-        if (row >= row0 + nrows) return;
-        double ax[RB], ay[RB];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
-        for (int j = 0; j < n; ++j) {
-            const double2 a = ld_mat(M + (int64_t)j * nF + row);
-#pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * n + j];
-                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
-                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
+        constexpr int RPW = 32 / RB;
+        const int r = lane % RB;
+        for (int row = row0 + warp * RPW + lane / RB; row < row0 + nrows; row += 4 * RPW) {
+            double ax = 0.0, ay = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double2 a = ld_mat(M + (int64_t)j * nF + row);
+                const double2 v = nd_sm[r * sn + j];
+                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
             }
+            if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax, ay);
         }
-#pragma unroll
-        for (int r = 0; r < RB; ++r)
-            if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax[r], ay[r]);
         return;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
         double ax[RB], ay[RB];
 #pragma unroll
@@ -405,7 +402,7 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
             const double2 a = ld_mat(mr + j);
 #pragma unroll
             for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * n + j];
+                const double2 v = nd_sm[r * sn + j];
                 ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
                 ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
             }
@@ -416,10 +413,12 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
                 ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
                 ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
             }
-        if (lane == 0) {
+        if (lane < nr) {
+            double sx = 0.0, sy = 0.0;
 #pragma unroll
             for (int r = 0; r < RB; ++r)
-                if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax[r], ay[r]);
+                if (r == lane) { sx = ax[r]; sy = ay[r]; }
+            x[(r0 + lane) * nc + f0 + row] = make_double2(sx, sy);
         }
     }
 }
@@ -1415,7 +1414,7 @@ template void launch_pre<float>(const DevModel&, const double2*, double2*, void*
 static constexpr int kNDSmemMax = 200 * 1024;
 int nd_rhs_block(int smem_rows, int R) {
     int rb = 8;
-    while (rb > 1 && (rb >= 2 * R || (size_t)smem_rows * rb * sizeof(double2) > (size_t)kNDSmemMax)) rb >>= 1;
+    while (rb > 1 && (rb >= 2 * R || (size_t)(smem_rows | 1) * rb * sizeof(double2) > (size_t)kNDSmemMax)) rb >>= 1;
     return rb;
 }
 template <class MT, int RB>
@@ -1430,13 +1429,13 @@ void nd_set_smem_limits() {
 template <class MT, int RB>
 static void nd_fwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* t, double2* y,
                      double2* u, int R, const int* done, cudaStream_t st) {
-    const size_t sm = std::max<size_t>(16, (size_t)smem_rows * RB * sizeof(double2));
+    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(double2));
     k_nd_forward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, t, y, u, R, done);
 }
 template <class MT, int RB>
 static void nd_bwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* y, double2* x,
                      int R, const int* done, cudaStream_t st) {
-    const size_t sm = std::max<size_t>(16, (size_t)smem_rows * RB * sizeof(double2));
+    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(double2));
     k_nd_backward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, y, x, R, done);
 }
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,

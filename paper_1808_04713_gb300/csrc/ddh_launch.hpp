@@ -36,9 +36,11 @@ void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, d
 
 // Nested-dissection factor of the coarse matrix on the device (elimination order).  Per
 // node: fully summed positions [f0, f0+nF), boundary positions bidx[b_off .. b_off+nB),
-// G (nB x nF) at g_off and M = [W | -H] (nF x (nF+nB)) at m_off, row-major, of element type
-// double2 or float2; the forward updates G y_F of node N live at u[u_off[N] ..] ([R][u_len]).
-// ct_ptr/ct_idx list, per position, the update entries that subtract into it.
+// G (nB x nF) at g_off and M = [W | -H] (nF x (nF+nB)) at m_off, of element type double2 or
+// float2, row-major (column-major for short rows, see kNDShortRow).  The forward pass leaves
+// at u[u_off[N] + k] ([R][u_len]) the total amount node N's subtree subtracts from boundary
+// entry k; it is passed up the tree: src[2 (s_off[N] + i) + {0,1}] are the offsets in u of
+// the (at most two) children's amounts for front entry i (F first, then B), or -1.
 struct NDDev {
     const int* f0 = nullptr;
     const int* nF = nullptr;
@@ -48,15 +50,17 @@ struct NDDev {
     const int64_t* g_off = nullptr;
     const int64_t* m_off = nullptr;
     const int64_t* u_off = nullptr;
-    const int* ct_ptr = nullptr;
-    const int64_t* ct_idx = nullptr;
+    const int64_t* s_off = nullptr;
+    const int64_t* src = nullptr;
     const void* G = nullptr;
     const void* M = nullptr;
     int64_t u_len = 0;
     int nc = 0;
 };
-// one tree level: items {node, first row, row count, short-row form}; a node whose rows have
-// at most kNDShortRow entries stores that matrix column-major and takes 128 rows per CTA
+// one tree level: items {node, first row, row count, short-row form}.  A long-row item has
+// up to 4 rows (one warp per row); a node whose rows have at most kNDShortRow entries
+// stores that matrix column-major, and its items have up to 128 rows, each lane of a warp
+// taking one (row, right-hand side) pair.
 constexpr int kNDShortRow = 64;
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
                        double2* y, double2* u, int R, const int* done, cudaStream_t st);
