@@ -26,7 +26,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Helmholtz DD solves/sec at rel. residual 1e-10"
+METRIC = "Helmholtz DD solves/sec at rel. residual 1e-10; mixed+batched vs plain FP64"
+COMPARE_WORKLOAD = "random_eps_64"
 UNIT = "solves/s"
 WORKLOAD = "plane_16x16"
 
@@ -110,6 +111,48 @@ def algorithmic_work(info, R: int, p: int, nE: float, nT: float, fp64: bool):
     flops_coarse = 8.0 * nc * nc * R
     bytes_coarse = 16.0 * nc * nc + 32.0 * nc * R
     return {0: (flops_pass1, bytes_pass1), 2: (flops_coarse, bytes_coarse), 3: (flops_pass2, bytes_pass2)}
+
+
+def _mixed_vs_plain(local: int, stream, steps: int) -> dict:
+    """Mixed precision (complex64 inner DD, FP64 outer FGMRES on the conforming system) against
+    the plain FP64 method on the batched 64x64 workload (p = 20, k = 400, random eps, 8 plane
+    waves), both to the same FP64 primal relative residual 1e-10; CUDA events on the library
+    stream, right-hand sides resident (the 231 MB of local vectors exceed L2)."""
+    import torch
+    import workloads as W
+    from paper_1808_04713_gb300 import ddh
+    w = W.WORKLOADS[COMPARE_WORKLOAD]()
+    R = w.n_rhs
+    res = {"workload": COMPARE_WORKLOAD, "rhs": R, "tol": 1e-10, "steps": steps}
+    for name, prec in (("plain_fp64", ddh.PREC_FP64), ("mixed", ddh.PREC_MIXED_FP32)):
+        s = ddh.DDH(local, stream=stream)
+        s.set_mesh(w.base_n, w.leaves, w.p)
+        s.set_coefficients(w.k, w.eps)
+        s.factor(tol=1e-10, precision=prec)
+        with torch.cuda.stream(stream):
+            b = s.rhs_planewave(w.thetas)
+            u = torch.empty_like(b)
+        _, st = s.solve(b, tol=1e-10, out=u)
+        ts = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            _, st = s.solve(b, tol=1e-10, out=u)
+            with torch.cuda.stream(stream):
+                e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        pr = s.primal_residual(b, u)
+        res[name] = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT,
+                     "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3),
+                     "iterations": max(x.iterations for x in st),
+                     "inner_iterations": max(x.inner_iterations for x in st),
+                     "max_primal_residual": float(max(pr))}
+        s.close()
+    res["mixed_over_plain"] = round(res["mixed"]["value"] / res["plain_fp64"]["value"], 3)
+    return res
 
 
 def run_ours(args):
@@ -202,6 +245,9 @@ def run_ours(args):
             "component_ms": {"pass1": comp[0], "coarse_assemble": comp[1], "coarse_solve": comp[2],
                              "pass2": comp[3], "jump_gather": comp[4], "precond": comp[5]}}
     clocks = clk.summary()
+    compare = None
+    if not args.no_compare:
+        compare = _mixed_vs_plain(local, stream, 2)
     out = None
     if rank == 0:
         cpu = None
@@ -225,7 +271,8 @@ def run_ours(args):
                "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
                        "h2d_bytes_per_step": int(16 * R * info.n_local),
                        "d2h_bytes_per_step": int(16 * R * info.n_local)},
-               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+               "mixed_vs_plain": compare}
         print(json.dumps(out))
     s.close()
     if ws > 1:
@@ -260,6 +307,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the mixed-vs-plain comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

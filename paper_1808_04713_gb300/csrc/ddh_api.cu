@@ -204,6 +204,21 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, c, &d.c))) return st;
     if ((st = upload(ctx, gam, &d.gam))) return st;
     if ((st = upload(ctx, geo, &d.geo))) return st;
+    {
+        // 1 / (mu_a + mu_b + c_e mu_a mu_b): the divide of the element fast solver
+        std::vector<int64_t> doff(E);
+        std::vector<double> dv;
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            const auto& mu = m.tabs[El.ptab].mu;
+            const int n = El.p - 1;
+            doff[e] = (int64_t)dv.size();
+            for (int a = 0; a < n; ++a)
+                for (int b = 0; b < n; ++b) dv.push_back(1.0 / (mu[a] + mu[b] + El.c * mu[a] * mu[b]));
+        }
+        if ((st = upload(ctx, dv, &d.dinv_all))) return st;
+        if ((st = upload(ctx, doff, &d.dinv_off))) return st;
+    }
     // tables
     std::vector<int> tp;
     std::vector<int64_t> tM, tV, tmu, tS;

@@ -44,6 +44,8 @@ struct DevModel {
     const double* c = nullptr;          // -k^2 eps (h/2)^2
     const double* gam = nullptr;        // [E][4] imaginary part of gamma_eff (real part 0)
     const double* geo = nullptr;        // [E][3] x0, y0, h
+    const double* dinv_all = nullptr;   // per element n^2: 1 / (mu_a + mu_b + c_e mu_a mu_b)
+    const int64_t* dinv_off = nullptr;
     // per degree table t
     const int* tab_p = nullptr;
     const int64_t* tab_Mt = nullptr;    // offsets into Mt_all ((p+1)^2)

@@ -80,7 +80,7 @@ __device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, con
     }
     g.sync();
     spec_from_full<T>(g, s, n);
-    spec_divide<T>(g, s, n, ce);
+    spec_divide<T>(g, s, n);
     cross_from_spec<T>(g, s, n);
 }
 
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
         // y_I = A_II^-1 (b_I - A_IE x_E) on the cross: the coupling part first ...
         cross_coupling<T>(g, s, p, ce, (T)-1);
         spec_from_cross<T>(g, s, n, false);
-        spec_divide<T>(g, s, n, ce);
+        spec_divide<T>(g, s, n);
         cross_from_spec<T>(g, s, n);
         cross_to_tile<T>(g, s, p, (T)1);
         if (bt && has_bI) {
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
         // w_I = A_II^-1 (A_IT u_T) on the cross; r'_E = A_ET u_T - A_EI w_I
         cross_coupling<T>(g, s, p, ce, (T)1);
         spec_from_cross<T>(g, s, n, false);
-        spec_divide<T>(g, s, n, ce);
+        spec_divide<T>(g, s, n);
         cross_from_spec<T>(g, s, n);
         cross_to_tile<T>(g, s, p, (T)-1);
         for (int i = g.t(); i < nE; i += g.n()) {
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
         }
         g.sync();
         spec_from_full<T>(g, s, n);
-        spec_divide<T>(g, s, n, ce);
+        spec_divide<T>(g, s, n);
         full_from_spec<T>(g, s, n);
         const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
         for (int idx = g.t(); idx < N * N; idx += g.n()) {

@@ -72,6 +72,7 @@ struct ElemSmem {
     T* Mt;          // N*N
     T* V;           // n*n
     T* mu;          // n
+    T* dinv;        // n*n: 1 / D of the fast-diagonalisation divide
     cpx<T>* tile;   // N*N
     cpx<T>* spec;   // n*n
     cpx<T>* tmp;    // n*n
@@ -86,7 +87,7 @@ template <class T>
 __host__ __device__ inline size_t elem_smem_bytes(int pmax, int nvec) {
     const int N = pmax + 1, n = pmax - 1;
     size_t b = 0;
-    b += sizeof(T) * (size_t)(N * N + n * n + n);
+    b += sizeof(T) * (size_t)(N * N + 2 * n * n + n);
     b = (b + 15) & ~(size_t)15;
     b += sizeof(cpx<T>) * (size_t)(N * N + 2 * n * n + 8 * n + nvec);
     return b + 64;
@@ -100,6 +101,7 @@ __device__ inline ElemSmem<T> carve(char* base, int pmax, int nvec) {
     s.Mt = r; r += N * N;
     s.V = r; r += n * n;
     s.mu = r; r += n;
+    s.dinv = r; r += n * n;
     size_t off = (reinterpret_cast<char*>(r) - base + 15) & ~(size_t)15;
     cpx<T>* c = reinterpret_cast<cpx<T>*>(base + off);
     s.tile = c; c += N * N;
@@ -124,6 +126,8 @@ __device__ inline void load_tables(const G& g, const DevModel& dm, int e, const 
     for (int i = g.t(); i < N * N; i += g.n()) s.Mt[i] = (T)Mt[i];
     for (int i = g.t(); i < n * n; i += g.n()) s.V[i] = (T)V[i];
     for (int i = g.t(); i < n; i += g.n()) s.mu[i] = (T)mu[i];
+    const double* dv = dm.dinv_all + dm.dinv_off[e];
+    for (int i = g.t(); i < n * n; i += g.n()) s.dinv[i] = (T)dv[i];
 }
 
 __device__ __forceinline__ int cand_list(int a, int p, int* c) {
@@ -247,16 +251,10 @@ __device__ inline void spec_from_cross(const G& g, const ElemSmem<T>& s, int n, 
     g.sync();
 }
 
-// spec /= D,  D[al][be] = mu_al + mu_be + c mu_al mu_be
+// spec /= D,  D[al][be] = mu_al + mu_be + c mu_al mu_be  (1/D precomputed per element in FP64)
 template <class T, class G>
-__device__ inline void spec_divide(const G& g, const ElemSmem<T>& s, int n, T ce) {
-    for (int idx = g.t(); idx < n * n; idx += g.n()) {
-        const int al = idx / n, be = idx % n;
-        const T ma = s.mu[al], mb = s.mu[be];
-        const T D = ma + mb + ce * ma * mb;
-        const T inv = (T)1 / D;
-        s.spec[idx] = inv * s.spec[idx];
-    }
+__device__ inline void spec_divide(const G& g, const ElemSmem<T>& s, int n) {
+    for (int idx = g.t(); idx < n * n; idx += g.n()) s.spec[idx] = s.dinv[idx] * s.spec[idx];
     g.sync();
 }
 
