@@ -1,0 +1,47 @@
+"""Time the components of one interface-operator application on a named workload.
+
+    python -m paper_1808_04713_gb300.profile_op <workload> [R] [fp64|mixed] [reps]
+
+Factors the workload, runs one solve with R right-hand sides (which sizes the work buffers
+and captures the iteration graph), then prints the average milliseconds per application of
+pass 1, coarse assembly, coarse solve, pass 2, jump gather and preconditioner, each timed with
+CUDA events on the library stream (ddh_profile_op).  A short fixed command for profilers.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main(argv=None) -> None:
+    import torch
+    import workloads as W
+    from paper_1808_04713_gb300 import ddh
+
+    argv = sys.argv[1:] if argv is None else argv
+    name = argv[0] if argv else "plane_16x16"
+    w = W.WORKLOADS[name]()
+    R = int(argv[1]) if len(argv) > 1 else w.n_rhs
+    prec = ddh.PREC_MIXED_FP32 if len(argv) > 2 and argv[2] == "mixed" else ddh.PREC_FP64
+    reps = int(argv[3]) if len(argv) > 3 else 3
+    s = ddh.DDH(0)
+    s.set_mesh(w.base_n, w.leaves, w.p)
+    s.set_coefficients(w.k, w.eps)
+    s.factor(tol=1e-10, precision=prec)
+    b = s.rhs_planewave(w.thetas[:R])
+    _, st = s.solve(b, tol=1e-10, allow_noconv=True)
+    torch.cuda.synchronize()
+    ms = s.profile_op(R, 0 if prec == ddh.PREC_FP64 else 1, reps)
+    info = s.info()
+    keys = ["pass1", "coarse_assemble", "coarse_solve", "pass2", "jump_gather", "precond"]
+    print(json.dumps({"workload": name, "rhs": R, "precision": "fp64" if prec == ddh.PREC_FP64 else "mixed",
+                      "iterations": max(x.iterations for x in st), "coarse_fronts": info.n_coarse_blocks,
+                      "ms": {k: round(float(v), 5) for k, v in zip(keys, ms)}}))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()
