@@ -238,8 +238,12 @@ def run_ours(args):
     fl, by = work[dom]
     fp64_peak = 1250.0         # GFLOP/s... expressed in TFLOP/s below
     achieved_tf = fl / (comp[dom] * 1e-3) / 1e12
+    # dram__bytes_read + dram__bytes_write of one k_gemv launch (dense K^-1, plane_16x16) from the
+    # ncu capture summarised in profiles/launches_plane16x16_fp64.md; unknown for other kernels
+    traffic = 59087360 + 512 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
     roof = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved_tf, 4),
-            "peak": 1.25, "unit": "TFLOP/s", "frac": round(achieved_tf / 1.25, 4), "traffic": None,
+            "peak": 1.25, "unit": "TFLOP/s", "frac": round(achieved_tf / 1.25, 4), "traffic": traffic,
+            "algorithmic_bytes": int(by),
             "peak_source": "fallback: nominal GB300 FP64 1.25 TFLOP/s (measured DGEMM 1.10)",
             "achieved_hbm_GBs": round(by / (comp[dom] * 1e-3) / 1e9, 1),
             "component_ms": {"pass1": comp[0], "coarse_assemble": comp[1], "coarse_solve": comp[2],
