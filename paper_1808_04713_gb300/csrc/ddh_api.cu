@@ -423,7 +423,8 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             }
             if (src.empty()) src.assign(2, -1);
         }
-        // work items per level: 4 rows per CTA; a forward item also for nodes with no boundary
+        // work items per level: 4 long rows or 16 short rows per item; a forward item also for
+        // nodes with no boundary
         std::vector<int4> items;
         const int L = m.c_depth + 1;
         ctx->nd_fwd_off.assign(L, 0); ctx->nd_fwd_n.assign(L, 0); ctx->nd_fwd_rows.assign(L, 0);
@@ -434,8 +435,9 @@ static ddh_status upload_model(ddh_ctx* ctx) {
                 const auto& N = m.cnode[id];
                 if (N.depth != lv || N.nF + (int)N.B.size() == 0) continue;
                 const int rows = (int)N.B.size();
-                const int sh = N.nF <= kNDShortRow, step = sh ? 128 : 4;
-                for (int r0 = 0; r0 == 0 || r0 < rows; r0 += step) items.push_back(make_int4(id, r0, std::min(step, rows - r0), sh));
+                const int sh = N.nF <= kNDShortRow, step = sh ? 16 : 4;
+                for (int r0 = 0; r0 == 0 || r0 < rows; r0 += step)
+                    items.push_back(make_int4(id, r0, std::max(0, std::min(step, rows - r0)), sh));
                 ctx->nd_fwd_rows[lv] = std::max(ctx->nd_fwd_rows[lv], N.nF);
             }
             ctx->nd_fwd_n[lv] = (int)items.size() - ctx->nd_fwd_off[lv];
@@ -443,7 +445,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             for (int id = 0; id < nn; ++id) {
                 const auto& N = m.cnode[id];
                 if (N.depth != lv || N.nF == 0) continue;
-                const int sh = N.nF + (int)N.B.size() <= kNDShortRow, step = sh ? 128 : 4;
+                const int sh = N.nF + (int)N.B.size() <= kNDShortRow, step = sh ? 16 : 4;
                 for (int r0 = 0; r0 < N.nF; r0 += step) items.push_back(make_int4(id, r0, std::min(step, N.nF - r0), sh));
                 ctx->nd_bwd_rows[lv] = std::max(ctx->nd_bwd_rows[lv], N.nF + (int)N.B.size());
             }
@@ -581,7 +583,7 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
     const NDDev& D = f32nd ? ctx->nd32 : ctx->nd64;
     double2* y = tmp;
     double2* u = (double2*)ctx->nd_u;
-    const int L = (int)ctx->nd_fwd_n.size();
+    const int L = (int)ctx->nd_fwd_rows.size();
     for (int lv = L - 1; lv >= 0; --lv) {
         if (!ctx->nd_fwd_n[lv]) continue;
         launch_nd_forward(D, f32nd, ctx->nd_items + ctx->nd_fwd_off[lv], ctx->nd_fwd_n[lv], ctx->nd_fwd_rows[lv], t, y, u,

@@ -263,9 +263,11 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
 // Nested-dissection solve of K x = t, one launch per tree level (see NDDev).  A CTA of 128
 // threads takes rows of one node's matrix for a block of RB right-hand sides after staging
 // the node's input vector in shared memory ([RB][stride], odd stride against bank
-// conflicts).  Long rows: one warp per row, lanes across the row.  Short rows: each lane
-// owns one (row, right-hand side) pair and runs along the row, so that every lane of the
-// (narrow) FP64 pipe does useful work even when rows are few and short.
+// conflicts).  Long rows: up to 4 rows per item, one warp per row, lanes across the row.
+// Short rows (column-major matrix): up to 16 rows per item; a warp takes 4 rows at a time,
+// each row's 8 lanes split into RB right-hand sides x 8/RB column slices, so every lane of
+// the (narrow) FP64 pipe does useful work whatever the block size, and small items spread a
+// level over all SMs (GB300 completes about one warp-wide FP64 FMA per SM every 16 cycles).
 __device__ __forceinline__ double2 ld_mat(const double2* a) { return __ldg(a); }
 __device__ __forceinline__ double2 ld_mat(const float2* a) {
     const float2 v = __ldg(a);
@@ -308,17 +310,26 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
     const MT* G = (const MT*)d.G + d.g_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (it.w) {
-        constexpr int RPW = 32 / RB;                      // rows per warp and pass
-        const int r = lane % RB;
-        for (int row = row0 + warp * RPW + lane / RB; row < row0 + nrows; row += 4 * RPW) {
+        // lane = (row of 4, column slice of S, right-hand side of RB), S * RB = 8
+        constexpr int S = 8 / RB;
+        const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
+        for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
+            const int row = base + rl;
+            const bool ok = row < row0 + nrows;
             double ax = 0.0, ay = 0.0;
-            for (int j = 0; j < nF; ++j) {
-                const double2 a = ld_mat(G + (int64_t)j * nB + row);
-                const double2 v = nd_sm[r * sF + j];
-                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+            if (ok)
+                for (int j = s; j < nF; j += S) {
+                    const double2 a = ld_mat(G + (int64_t)j * nB + row);
+                    const double2 v = nd_sm[r * sF + j];
+                    ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                    ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+                }
+#pragma unroll
+            for (int o = RB; o < 8; o <<= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
             }
-            if (r < nr) {
+            if (ok && s == 0 && r < nr) {
                 const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + nF + row);
                 u[(r0 + r) * ul + uo + row] = make_double2(w.x + ax, w.y + ay);
             }
@@ -379,17 +390,26 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
     const MT* M = (const MT*)d.M + d.m_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (it.w) {
-        constexpr int RPW = 32 / RB;
-        const int r = lane % RB;
-        for (int row = row0 + warp * RPW + lane / RB; row < row0 + nrows; row += 4 * RPW) {
+        // lane = (row of 4, column slice of S, right-hand side of RB), S * RB = 8
+        constexpr int S = 8 / RB;
+        const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
+        for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
+            const int row = base + rl;
+            const bool ok = row < row0 + nrows;
             double ax = 0.0, ay = 0.0;
-            for (int j = 0; j < n; ++j) {
-                const double2 a = ld_mat(M + (int64_t)j * nF + row);
-                const double2 v = nd_sm[r * sn + j];
-                ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+            if (ok)
+                for (int j = s; j < n; j += S) {
+                    const double2 a = ld_mat(M + (int64_t)j * nF + row);
+                    const double2 v = nd_sm[r * sn + j];
+                    ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+                    ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+                }
+#pragma unroll
+            for (int o = RB; o < 8; o <<= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
             }
-            if (r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax, ay);
+            if (ok && s == 0 && r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax, ay);
         }
         return;
     }

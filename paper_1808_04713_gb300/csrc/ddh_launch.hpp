@@ -58,10 +58,10 @@ struct NDDev {
     int nc = 0;
 };
 // one tree level: items {node, first row, row count, short-row form}.  A long-row item has
-// up to 4 rows (one warp per row); a node whose rows have at most kNDShortRow entries
-// stores that matrix column-major, and its items have up to 128 rows, each lane of a warp
-// taking one (row, right-hand side) pair.
-constexpr int kNDShortRow = 64;
+// up to 4 rows (one warp per row); a node whose rows have at most kNDShortRow
+// entries stores that matrix column-major, and its items have up to 16 rows (8 lanes per
+// row, split over right-hand sides and column slices).
+constexpr int kNDShortRow = 128;
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
                        double2* y, double2* u, int R, const int* done, cudaStream_t st);
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
