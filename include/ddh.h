@@ -61,6 +61,15 @@ typedef enum {
 
 typedef enum { DDH_PRECOND_DIRICHLET = 0, DDH_PRECOND_LUMPED = 1, DDH_PRECOND_NONE = 2 } ddh_precond;
 
+/* How the Krylov-loop local solves y1 = A11^-1 [r_E; 0] are applied (Sec. 2.3.3, eq.
+ * block_matrix_inversion).  The jump operator only reads type-1 edge values and the coarse
+ * system only type-2 values, so the loop needs just x_E = S_E^-1 r_E and the edge part
+ * Y = [A11^-1 A_1T]_E of the coupling to the coarse unknowns:
+ *   DDH_LOCAL_EDGE  x_E = S_E^-1 r_E, t_T = Y^T r_E, x1_E = x_E - Y u_T (Y formed at factor time)
+ *   DDH_LOCAL_FDM   the same through the fast-diagonalisation solver on the interior cross.
+ * The RHS pass and the recovery of the interior always use the FDM. */
+typedef enum { DDH_LOCAL_EDGE = 0, DDH_LOCAL_FDM = 1 } ddh_local_form;
+
 typedef struct {
     double tol;            /* relative residual target (default 1e-10) */
     int32_t maxit;         /* total Krylov iterations per RHS (default 300) */
@@ -75,6 +84,9 @@ typedef struct {
     int32_t coarse_fp32;   /* mixed precision only: 1 = apply a complex64 copy of the coarse
                               factor inside the inner (preconditioner) solves; 0 (default) keeps
                               the coarse solve FP64 everywhere */
+    int32_t local_form;    /* local solves inside the Krylov loop (ddh_local_form): explicit edge
+                              operators (default) or the FDM on the interior cross; the same
+                              A11^-1, so the iterates agree to rounding */
 } ddh_options;
 
 typedef struct {

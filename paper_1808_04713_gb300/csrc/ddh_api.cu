@@ -65,6 +65,9 @@ struct ddh_ctx {
     std::vector<void*> model_allocs;
     void* sinv64 = nullptr;
     void* sinv32 = nullptr;
+    void* pq64 = nullptr;                          // Y = [A11^-1 A_1T]_E per element
+    void* pq32 = nullptr;
+    bool edge_form = false;                        // Krylov-loop passes with Y (no FDM)
     double2* Kinv = nullptr;                       // dense coarse inverse (elimination order)
     float2* Kinv32 = nullptr;
     // nested-dissection factor: complex128 matrices, their complex64 copy (nd32.G/M null
@@ -135,6 +138,8 @@ static void free_model(ddh_ctx* ctx) {
     for (auto& kv : ctx->work) cudaFree(kv.second.p);
     ctx->work.clear();
     ctx->sinv64 = ctx->sinv32 = nullptr;
+    ctx->pq64 = ctx->pq32 = nullptr;
+    ctx->edge_form = false;
     ctx->Kinv = nullptr;
     ctx->Kinv32 = nullptr;
     ctx->refine_coarse = false;
@@ -346,6 +351,27 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, s32, &b))) return st;
         ctx->sinv64 = (void*)a;
         ctx->sinv32 = (void*)b;
+    }
+    // edge operators Y (FP64 and FP32 copies) for the Krylov-loop passes
+    {
+        int maxT = 0;
+        for (const auto& El : m.el) maxT = std::max(maxT, El.nT);
+        ctx->edge_form = ctx->opt.local_form == DDH_LOCAL_EDGE && maxT <= 128;
+        std::vector<int64_t> po(E);
+        for (int e = 0; e < E; ++e) po[e] = m.el[e].pq_off;
+        if ((st = upload(ctx, po, &d.pq_off))) return st;
+        std::vector<double2> y64(m.pq.size());
+        std::vector<float2> y32(m.pq.size());
+        for (size_t i = 0; i < m.pq.size(); ++i) {
+            y64[i] = make_double2(m.pq[i].real(), m.pq[i].imag());
+            y32[i] = make_float2((float)m.pq[i].real(), (float)m.pq[i].imag());
+        }
+        const double2* a;
+        const float2* b;
+        if ((st = upload(ctx, y64, &a))) return st;
+        if ((st = upload(ctx, y32, &b))) return st;
+        ctx->pq64 = (void*)a;
+        ctx->pq32 = (void*)b;
     }
     // coarse factor
     auto conv = [](const std::vector<cd>& v) {
@@ -605,11 +631,14 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     const DevModel& d = ctx->dm;
     cudaStream_t s = ctx->stream;
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
-    launch_pass1<T>(d, sinv, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
+    const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
+    if (ctx->edge_form && !(bt && has_bI)) launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s);
+    else launch_pass1<T>(d, sinv, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
     coarse_solve(ctx, w.t, w.x2, w.ctmp, R, done);
-    launch_pass2<T>(d, sinv, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
+    if (ctx->edge_form && !phi_out) launch_pass2_edge<T>(d, Y, w.x2, w.xE, w.xE2, R, done, s);
+    else launch_pass2<T>(d, sinv, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
     ctx->launches++;
     if (out_dual && d.n_dual > 0) {
         launch_jump_gather<T>(d, w.xE2, w.x2, out_dual, R, done, s);
@@ -1093,6 +1122,7 @@ void ddh_default_options(ddh_options* o) {
     o->check_every = 4;
     o->use_graph = 1;
     o->coarse_fp32 = 0;
+    o->local_form = DDH_LOCAL_EDGE;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1144,6 +1174,8 @@ ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (!ctx->have_mesh || !ctx->have_coef) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh and coefficients first");
     if (opt) ctx->opt = *opt;
     if (ctx->opt.restart < 2 || ctx->opt.restart > 200) return fail(ctx, DDH_ERR_INVALID_ARG, "restart must lie in [2, 200]");
+    if (ctx->opt.local_form != DDH_LOCAL_EDGE && ctx->opt.local_form != DDH_LOCAL_FDM)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "local_form must be DDH_LOCAL_EDGE or DDH_LOCAL_FDM");
     if (ctx->opt.check_every < 1) ctx->opt.check_every = 1;
     const auto t0 = std::chrono::steady_clock::now();
     cudaSetDevice(ctx->device);
@@ -1383,18 +1415,32 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
         return ms / reps;
     };
     const void* sinv = fp64 ? ctx->sinv64 : ctx->sinv32;
+    const void* Y = fp64 ? ctx->pq64 : ctx->pq32;
+    const bool ef = ctx->edge_form;
     cudaStream_t s = ctx->stream;
     const double2* z = K.zw;
     if (fp64) {
-        ms_out[0] = timeit([&] { launch_pass1<double>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s); });
+        ms_out[0] = timeit([&] {
+            if (ef) launch_pass1_edge<double>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
+            else launch_pass1<double>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
+        });
         ms_out[1] = timeit([&] { launch_coarse_assemble<double>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
-        ms_out[3] = timeit([&] { launch_pass2<double>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s); });
+        ms_out[3] = timeit([&] {
+            if (ef) launch_pass2_edge<double>(d, Y, w.x2, w.xE, w.xE2, R, nullptr, s);
+            else launch_pass2<double>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
+        });
         ms_out[4] = timeit([&] { launch_jump_gather<double>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
         ms_out[5] = timeit([&] { launch_pre<double>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
     } else {
-        ms_out[0] = timeit([&] { launch_pass1<float>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s); });
+        ms_out[0] = timeit([&] {
+            if (ef) launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
+            else launch_pass1<float>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
+        });
         ms_out[1] = timeit([&] { launch_coarse_assemble<float>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
-        ms_out[3] = timeit([&] { launch_pass2<float>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s); });
+        ms_out[3] = timeit([&] {
+            if (ef) launch_pass2_edge<float>(d, Y, w.x2, w.xE, w.xE2, R, nullptr, s);
+            else launch_pass2<float>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
+        });
         ms_out[4] = timeit([&] { launch_jump_gather<float>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
         ms_out[5] = timeit([&] { launch_pre<float>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
     }

@@ -40,6 +40,7 @@ struct DevModel {
     const int* t_off = nullptr;
     const int* nT = nullptr;
     const int64_t* sinv_off = nullptr;
+    const int64_t* pq_off = nullptr;    // start of Y = [A11^-1 A_1T]_E (nE x nT, row-major)
     const int* ptab = nullptr;
     const double* c = nullptr;          // -k^2 eps (h/2)^2
     const double* gam = nullptr;        // [E][4] imaginary part of gamma_eff (real part 0)

@@ -237,6 +237,7 @@ static void cross_green(const PTable& T, double c, const std::vector<int>& X, st
 namespace {
 struct ElemFactor {
     std::vector<cd> Se;      // nT x nT local coarse Schur complement
+    std::vector<cd> Y;       // nE x nT edge part of A11^-1 A_1T
     double sinv_err = 0;
     double gap = 1;
     double minpiv = 1;
@@ -354,10 +355,25 @@ bool factor(Model& m, int nthreads, std::string& err) {
         }
         std::vector<cd> yE, yX;
         a11_solve(nE, nX, nT, Sinv, AEX, AXE, G, AET, AXT, yE, yX);
+        ef[e].Y = yE;
         ef[e].Se = ATT;
         gemm(nT, nE, nT, ATE.data(), yE.data(), ef[e].Se.data(), true, 1);
         gemm(nT, nX, nT, ATX.data(), yX.data(), ef[e].Se.data(), true, 1);
     });
+    // edge operators for the Krylov-loop passes, blocks even-sized (16-byte aligned copies)
+    {
+        int64_t yo = 0;
+        for (int e = 0; e < E; ++e) {
+            m.el[e].pq_off = yo;
+            const int64_t s2 = (int64_t)m.el[e].nE1 * m.el[e].nT;
+            yo += s2 + (s2 & 1);
+        }
+        m.pq.assign((size_t)yo + 2, cd(0));
+        for (int e = 0; e < E; ++e) {
+            std::copy(ef[e].Y.begin(), ef[e].Y.end(), m.pq.begin() + m.el[e].pq_off);
+            std::vector<cd>().swap(ef[e].Y);
+        }
+    }
     m.min_gap = 1e300;
     if (m.check_factor) {
         m.sinv_check = 0;

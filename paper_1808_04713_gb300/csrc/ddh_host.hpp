@@ -45,6 +45,7 @@ struct Elem {
     int32_t e1_off = 0, nE1 = 0;                   // E1 (type-1 edge) slots
     int32_t t_off = 0, nT = 0;                     // T (type-2 / slaved) slots
     int64_t sinv_off = 0;                          // start of nE1^2 complex inverse
+    int64_t pq_off = 0;                            // start of Y = [A11^-1 A_1T]_E (nE1 x nT)
     int32_t ptab = 0;                              // index into tables
 };
 
@@ -95,6 +96,7 @@ struct Model {
     std::vector<double> cf_w;
     // factor
     std::vector<cd> sinv;                         // per element nE1^2, column-major
+    std::vector<cd> pq;                           // per element Y = [A11^-1 A_1T]_E, row-major
     double min_gap = 1e300;
     // coarse factorisation: nested dissection over base-grid lines, multifrontal elimination
     struct CNode {

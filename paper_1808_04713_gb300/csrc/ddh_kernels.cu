@@ -180,6 +180,108 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
     }
 }
 
+// ------------------------------------------------------------------ passes with explicit edge operators
+// Inside the Krylov loop the element solves only ever map type-1 edge values to type-1 edge
+// values and type-2 values (the jump operator touches nothing else), so with
+//   Y = [A11^-1 A_1T]_E = S_E^-1 (A_ET - A_EX G A_XT)      (nE x nT, complex symmetric A)
+// pass 1 is  x_E = S_E^-1 r_E,  t_T = Y^T r_E   (t_T = A_T1 A11^-1 [r_E; 0])
+// pass 2 is  x1_E = x_E - Y u_T                 (x1 = y1 - A11^-1 A12 x2, edge part)
+// -- two small dense products per element and right-hand side block instead of the FDM
+// chain.  Y is formed at factor time.  The interior never enters the iteration; it is
+// rebuilt by the FDM kernels in the recovery.
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pass1_edge(DevModel dm, const cpx<T>* __restrict__ sinv,
+                                                    const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
+                                                    double zsign, const double2* __restrict__ bt, int R,
+                                                    cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
+                                                    const int* __restrict__ done, int ntask, int stage_off, int vs) {
+    if (done && *done) return;
+    extern __shared__ __align__(128) char smem[];
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
+    const cpx<T>* S = sinv + dm.sinv_off[e];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_off);
+    cpx<T>* S_s = reinterpret_cast<cpx<T>*>(smem + stage_off + 128);
+    if (stage_off > 0 && nE > 0 && threadIdx.x == 0)
+        bulk_load_start(bar, S_s, S, (uint32_t)(((size_t)nE * nE * sizeof(cpx<T>) + 15) & ~(size_t)15));
+    cpx<T>* rE = reinterpret_cast<cpx<T>*>(smem);     // [RB][vs]
+    cpx<T>* xE = rE + RB * vs;                         // [RB][vs]
+    const int64_t off = dm.off[e];
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE, r = r0 + q;
+        cpx<T> v = mk<T>(0, 0);
+        const int row = dm.e1_row[e1o + i];
+        if (z && row >= 0) v = (T)(zsign * dm.e1_sign[e1o + i]) * ld<T>(z, (int64_t)r * dm.n_dual + row);
+        if (bt) v += ld<T>(bt, (int64_t)r * dm.n_local + off + dm.e1_slot[e1o + i]);
+        rE[q * vs + i] = v;
+    }
+    g.sync();
+    // t_T = Y^T r_E (threads over (rhs, T slot)); issued before the wait for S_E^-1
+    const cpx<T>* Ye = Y + dm.pq_off[e];
+    for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
+        const int q = idx / nT, t = idx % nT;
+        cpx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+        int i = 0;
+        for (; i + 1 < nE; i += 2) {
+            fma_c(a0, Ye[(int64_t)i * nT + t], rE[q * vs + i]);
+            fma_c(a1, Ye[(int64_t)(i + 1) * nT + t], rE[q * vs + i + 1]);
+        }
+        if (i < nE) fma_c(a0, Ye[(int64_t)i * nT + t], rE[q * vs + i]);
+        tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + t] = a0 + a1;
+    }
+    if (stage_off > 0 && nE > 0) {
+        if (!bulk_wait_all(bar, dm.err)) return;
+        S = S_s;
+    }
+    sinv_apply_batched<T, RB>(g, S, nE, cnt, rE, vs, xE);
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE;
+        xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = xE[q * vs + i];
+    }
+}
+
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pass2_edge(DevModel dm, const cpx<T>* __restrict__ Y,
+                                                    const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
+                                                    cpx<T>* __restrict__ xE_out, int R, const int* __restrict__ done,
+                                                    int ntask) {
+    if (done && *done) return;
+    __shared__ cpx<T> uT[RB][128];
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
+    for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
+        const int q = idx / nT, i = idx % nT, r = r0 + q;
+        cpx<T> u = mk<T>(0, 0);
+        for (int a = dm.t_ptr[to + i]; a < dm.t_ptr[to + i + 1]; ++a) {
+            const double2 xv = x2[(int64_t)r * dm.n_coarse + dm.t_col[a]];
+            const T w = (T)dm.t_w[a];
+            u.x += w * (T)xv.x;
+            u.y += w * (T)xv.y;
+        }
+        uT[q][i] = u;
+    }
+    g.sync();
+    const cpx<T>* Ye = Y + dm.pq_off[e];
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE;
+        const cpx<T>* yr = Ye + (int64_t)i * nT;
+        cpx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+        int t = 0;
+        for (; t + 1 < nT; t += 2) { fma_c(a0, yr[t], uT[q][t]); fma_c(a1, yr[t + 1], uT[q][t + 1]); }
+        if (t < nT) fma_c(a0, yr[t], uT[q][t]);
+        const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
+        xE_out[gi] = xE_in[gi] - (a0 + a1);
+    }
+}
+
 // ------------------------------------------------------------------ coarse assembly
 // t[g] = bsign * (Z2^T b_T)[g] + zsign * (C2^T z)[g] - (Z2^T tT)[g]   (FP64 output)
 template <class T>
@@ -1374,6 +1476,60 @@ void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double
         default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
     }
 }
+// shared memory of the edge-operator pass 1: r_E and x_E blocks, then (when it fits) the
+// staged S_E^-1 behind an mbarrier
+template <class T>
+static size_t edge_vec_bytes(int rb, int maxE1) {
+    return ((size_t)2 * rb * std::max(1, maxE1) * sizeof(cpx<T>) + 127) & ~(size_t)127;
+}
+template <class T>
+static int edge_stage_off(int rb, int maxE1) {
+    const size_t base = edge_vec_bytes<T>(rb, maxE1);
+    const size_t st = 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+    return (maxE1 > 0 && base + st <= 200 * 1024) ? (int)base : 0;
+}
+template <class T>
+static size_t edge_smem_total(int rb, int maxE1) {
+    const int off = edge_stage_off<T>(rb, maxE1);
+    if (!off) return edge_vec_bytes<T>(rb, maxE1);
+    return (size_t)off + 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+}
+template <class T>
+void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
+                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const int so = edge_stage_off<T>(rb, dm.maxE1);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const size_t sm = edge_smem_total<T>(rb, dm.maxE1);
+    const int vs = std::max(1, dm.maxE1);
+    const cpx<T>* S = (const cpx<T>*)sinv;
+    const cpx<T>* Yp = (const cpx<T>*)Y;
+    switch (rb) {
+        case 8: k_pass1_edge<T, 8><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 4: k_pass1_edge<T, 4><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 2: k_pass1_edge<T, 2><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        default: k_pass1_edge<T, 1><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
+    }
+}
+template <class T>
+void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
+                       const int* done, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const cpx<T>* Yp = (const cpx<T>*)Y;
+    const cpx<T>* xi = (const cpx<T>*)xE_in;
+    cpx<T>* xo = (cpx<T>*)xE_out;
+    switch (rb) {
+        case 8: k_pass2_edge<T, 8><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 4: k_pass2_edge<T, 4><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 2: k_pass2_edge<T, 2><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        default: k_pass2_edge<T, 1><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
+    }
+}
+template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass2_edge<double>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
+template void launch_pass2_edge<float>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
 template <class T>
 void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
                             double2* t, int R, const int* done, cudaStream_t st) {
@@ -1590,6 +1746,8 @@ size_t pass_smem(int pmax, bool fp64) {
 }
 template <class T, int RB>
 static void set_pass_limits(int pmax, int maxE1) {
+    cudaFuncSetAttribute(k_pass1_edge<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem_total<T>(RB, maxE1));
     const int b = (int)pass_smem_total<T>(pmax, RB, maxE1);
     cudaFuncSetAttribute(k_pass1<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     cudaFuncSetAttribute(k_pass2<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);

@@ -21,6 +21,14 @@ struct KrylovDev {
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+// Krylov-loop passes with the explicit edge operators Y = [A11^-1 A_1T]_E (no FDM; pass 1
+// requires a load without interior components, pass 2 no recovery)
+template <class T>
+void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
+                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+template <class T>
+void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
+                       const int* done, cudaStream_t st);
 template <class T>
 void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
                             double2* t, int R, const int* done, cudaStream_t st);

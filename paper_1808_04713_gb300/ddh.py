@@ -18,6 +18,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_READY, ERR_NO_CONVERGENCE, ERR_S
     WARN_NEAR_RESONANT, ERR_DEVICE_FLAG = range(9)
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
+LOCAL_EDGE, LOCAL_FDM = 0, 1
 
 
 class DDHError(RuntimeError):
@@ -30,7 +31,7 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
-                ("coarse_fp32", C.c_int32)]
+                ("coarse_fp32", C.c_int32), ("local_form", C.c_int32)]
 
 
 class Info(C.Structure):

@@ -172,3 +172,26 @@ def test_plain_path_meets_primal_yardstick_lens():
     u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
     assert st[0].primal_residual <= 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("name", ["uniform4_mixed_p", "hanging_corner", "multilevel"])
+@pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
+def test_local_forms_agree(name, prec):
+    """Explicit edge operators and the interior-cross FDM apply the same A11^-1 in the Krylov
+    loop: the solutions agree to rounding and so do the iteration counts; both meet the oracle."""
+    w = SMALL[name]()
+    out = {}
+    for form in (ddh.LOCAL_EDGE, ddh.LOCAL_FDM):
+        s = _solver(w, tol=1e-12, precision=prec, local_form=form)
+        u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-12)
+        out[form] = (u.cpu().numpy(), [x.iterations for x in st], [x.primal_residual for x in st])
+        s.close()
+    ue, ie, pe = out[ddh.LOCAL_EDGE]
+    uf, iff, pf = out[ddh.LOCAL_FDM]
+    tol = 1e-11 if prec == ddh.PREC_FP64 else 1e-8
+    assert np.linalg.norm(ue - uf) <= tol * np.linalg.norm(uf)
+    if prec == ddh.PREC_FP64:
+        assert all(abs(a - b) <= 1 for a, b in zip(ie, iff))
+    assert max(pe) <= 1e-11
+    ref = dd.Conforming(dd.problem_from_workload(w)).solve_direct()
+    assert np.linalg.norm(ue - ref) / np.linalg.norm(ref) <= (1e-10 if prec == ddh.PREC_FP64 else 1e-8)
