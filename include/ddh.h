@@ -81,9 +81,10 @@ typedef struct {
                               application (default 12) */
     int32_t check_every;   /* host polls convergence every this many iterations (default 4) */
     int32_t use_graph;     /* 1: replay one FGMRES iteration as a CUDA graph (default 1) */
-    int32_t coarse_fp32;   /* mixed precision only: 1 = apply a complex64 copy of the coarse
-                              factor inside the inner (preconditioner) solves; 0 (default) keeps
-                              the coarse solve FP64 everywhere */
+    int32_t coarse_fp32;   /* mixed precision only: 1 = inside the inner (preconditioner) solves,
+                              apply a complex64 copy of the coarse factor in FP32 arithmetic,
+                              followed by one refinement step with the FP64 residual of the
+                              assembled K; 0 (default) keeps the coarse solve FP64 everywhere */
     int32_t local_form;    /* local solves inside the Krylov loop (ddh_local_form): explicit edge
                               operators (default) or the FDM on the interior cross; the same
                               A11^-1, so the iterates agree to rounding */

@@ -514,7 +514,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     }
     // assembled K for the refinement step when the factorisation's self-check is loose
     ctx->refine_coarse = !m.dense_coarse && m.coarse_refine;
-    if (ctx->refine_coarse) {
+    if (ctx->refine_coarse || want32) {
         if ((st = upload(ctx, m.kc_ptr, &ctx->kc_ptr))) return st;
         if ((st = upload(ctx, m.kc_col, &ctx->kc_col))) return st;
         if ((st = upload(ctx, conv(m.kc_val), &ctx->kc_val))) return st;
@@ -581,7 +581,10 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
 static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done);
 
 static void coarse_solve(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done) {
-    if (!(ctx->refine_active && ctx->refine_coarse && !ctx->coarse32)) { coarse_solve_once(ctx, t, x2, tmp, R, done); return; }
+    // FP64 solves refine when the factor's self-check asks for it; solves with the complex64
+    // copy always take one FP64 refinement step
+    const bool refine = ctx->coarse32 ? ctx->kc_ptr != nullptr : (ctx->refine_active && ctx->refine_coarse);
+    if (!refine) { coarse_solve_once(ctx, t, x2, tmp, R, done); return; }
     // x = K^-1 t;  r = t - K x;  x += K^-1 r
     const int nc = ctx->dm.n_coarse;
     cudaStream_t s = ctx->stream;
@@ -1444,8 +1447,11 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
         ms_out[4] = timeit([&] { launch_jump_gather<float>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
         ms_out[5] = timeit([&] { launch_pre<float>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
     }
-    // the coarse solve overwrites its input in block-tridiagonal mode: keep a copy
+    // the coarse solve as the solves run it: the complex64 copy (refined) for mixed precision
+    // with coarse_fp32, else FP64
+    ctx->coarse32 = !fp64 && ctx->opt.coarse_fp32 != 0;
     ms_out[2] = timeit([&] { coarse_solve(ctx, w.t, w.x2, w.ctmp, R, nullptr); });
+    ctx->coarse32 = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());

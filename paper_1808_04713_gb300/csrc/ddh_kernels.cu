@@ -370,11 +370,12 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
 // each row's 8 lanes split into RB right-hand sides x 8/RB column slices, so every lane of
 // the (narrow) FP64 pipe does useful work whatever the block size, and small items spread a
 // level over all SMs (GB300 completes about one warp-wide FP64 FMA per SM every 16 cycles).
-__device__ __forceinline__ double2 ld_mat(const double2* a) { return __ldg(a); }
-__device__ __forceinline__ double2 ld_mat(const float2* a) {
-    const float2 v = __ldg(a);
-    return make_double2((double)v.x, (double)v.y);
-}
+// Arithmetic follows the factor's storage type: FP64 for the complex128 factor, FP32 for its
+// complex64 copy (vectors stay complex128 in global memory and are converted at the edges).
+template <class MT> struct NDType { using T = double; };
+template <> struct NDType<float2> { using T = float; };
+__device__ __forceinline__ cpx<double> ld_mat(const double2* a) { const double2 v = __ldg(a); return mk<double>(v.x, v.y); }
+__device__ __forceinline__ cpx<float> ld_mat(const float2* a) { const float2 v = __ldg(a); return mk<float>(v.x, v.y); }
 __device__ __forceinline__ double2 nd_pull(const double2* u, int64_t base, const int64_t* src, int64_t i) {
     const int64_t a = src[2 * i], b = src[2 * i + 1];
     double2 s = make_double2(0.0, 0.0);
@@ -382,14 +383,21 @@ __device__ __forceinline__ double2 nd_pull(const double2* u, int64_t base, const
     if (b >= 0) { const double2 v = u[base + b]; s.x += v.x; s.y += v.y; }
     return s;
 }
+template <class T>
+__device__ __forceinline__ void cfma(T& ax, T& ay, cpx<T> a, cpx<T> v) {
+    ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
+    ay = fma(a.x, v.y, fma(a.y, v.x, ay));
+}
 
 // forward level: y_F = t_F - w_F, u_N = w_B + G_N y_F (w = the children's amounts)
 template <class MT, int RB>
 __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
                                                     const double2* __restrict__ t, double2* __restrict__ y,
                                                     double2* __restrict__ u, int R, const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
     if (done && *done) return;
-    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][sF]
+    extern __shared__ __align__(16) char nd_raw[];
+    cpx<T>* nd_sm = reinterpret_cast<cpx<T>*>(nd_raw);    // [RB][sF]
     const int4 it = items[blockIdx.x];
     const int node = it.x, row0 = it.y, nrows = it.z;
     const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
                 v.x -= w.x; v.y -= w.y;
                 if (row0 == 0) y[(r0 + r) * nc + pos] = v;
             }
-            nd_sm[r * sF + i] = v;
+            nd_sm[r * sF + i] = mk<T>((T)v.x, (T)v.y);
         }
     }
     __syncthreads();
@@ -418,14 +426,9 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
         for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
             const int row = base + rl;
             const bool ok = row < row0 + nrows;
-            double ax = 0.0, ay = 0.0;
+            T ax = 0, ay = 0;
             if (ok)
-                for (int j = s; j < nF; j += S) {
-                    const double2 a = ld_mat(G + (int64_t)j * nB + row);
-                    const double2 v = nd_sm[r * sF + j];
-                    ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                    ay = fma(a.x, v.y, fma(a.y, v.x, ay));
-                }
+                for (int j = s; j < nF; j += S) cfma(ax, ay, ld_mat(G + (int64_t)j * nB + row), nd_sm[r * sF + j]);
 #pragma unroll
             for (int o = RB; o < 8; o <<= 1) {
                 ax += __shfl_xor_sync(0xffffffffu, ax, o);
@@ -433,24 +436,20 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
             }
             if (ok && s == 0 && r < nr) {
                 const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + nF + row);
-                u[(r0 + r) * ul + uo + row] = make_double2(w.x + ax, w.y + ay);
+                u[(r0 + r) * ul + uo + row] = make_double2(w.x + (double)ax, w.y + (double)ay);
             }
         }
         return;
     }
     for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
-        double ax[RB], ay[RB];
+        T ax[RB], ay[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        for (int r = 0; r < RB; ++r) { ax[r] = 0; ay[r] = 0; }
         const MT* g = G + (int64_t)row * nF;
         for (int j = lane; j < nF; j += 32) {
-            const double2 a = ld_mat(g + j);
+            const cpx<T> a = ld_mat(g + j);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * sF + j];
-                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
-                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
-            }
+            for (int r = 0; r < RB; ++r) cfma(ax[r], ay[r], a, nd_sm[r * sF + j]);
         }
 #pragma unroll
         for (int r = 0; r < RB; ++r)
@@ -460,12 +459,12 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
             }
         if (lane < nr) {
             // lane r writes right-hand side r (register arrays indexed by a constant only)
-            double sx = 0.0, sy = 0.0;
+            T sx = 0, sy = 0;
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if (r == lane) { sx = ax[r]; sy = ay[r]; }
             const double2 w = nd_pull(u, (r0 + lane) * ul, d.src, so + nF + row);
-            u[(r0 + lane) * ul + uo + row] = make_double2(w.x + sx, w.y + sy);
+            u[(r0 + lane) * ul + uo + row] = make_double2(w.x + (double)sx, w.y + (double)sy);
         }
     }
 }
@@ -475,8 +474,10 @@ template <class MT, int RB>
 __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __restrict__ items,
                                                      const double2* __restrict__ y, double2* __restrict__ x, int R,
                                                      const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
     if (done && *done) return;
-    extern __shared__ __align__(16) double2 nd_sm[];      // [RB][sn]
+    extern __shared__ __align__(16) char nd_raw[];
+    cpx<T>* nd_sm = reinterpret_cast<cpx<T>*>(nd_raw);    // [RB][sn]
     const int4 it = items[blockIdx.x];
     const int node = it.x, row0 = it.y, nrows = it.z;
     const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
@@ -486,7 +487,10 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int pos = i < nF ? f0 + i : bi[i - nF];
         const double2* src = i < nF ? y : x;
-        for (int r = 0; r < RB; ++r) nd_sm[r * sn + i] = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
+        for (int r = 0; r < RB; ++r) {
+            const double2 v = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
+            nd_sm[r * sn + i] = mk<T>((T)v.x, (T)v.y);
+        }
     }
     __syncthreads();
     const MT* M = (const MT*)d.M + d.m_off[node];
@@ -498,36 +502,27 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
         for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
             const int row = base + rl;
             const bool ok = row < row0 + nrows;
-            double ax = 0.0, ay = 0.0;
+            T ax = 0, ay = 0;
             if (ok)
-                for (int j = s; j < n; j += S) {
-                    const double2 a = ld_mat(M + (int64_t)j * nF + row);
-                    const double2 v = nd_sm[r * sn + j];
-                    ax = fma(a.x, v.x, fma(-a.y, v.y, ax));
-                    ay = fma(a.x, v.y, fma(a.y, v.x, ay));
-                }
+                for (int j = s; j < n; j += S) cfma(ax, ay, ld_mat(M + (int64_t)j * nF + row), nd_sm[r * sn + j]);
 #pragma unroll
             for (int o = RB; o < 8; o <<= 1) {
                 ax += __shfl_xor_sync(0xffffffffu, ax, o);
                 ay += __shfl_xor_sync(0xffffffffu, ay, o);
             }
-            if (ok && s == 0 && r < nr) x[(r0 + r) * nc + f0 + row] = make_double2(ax, ay);
+            if (ok && s == 0 && r < nr) x[(r0 + r) * nc + f0 + row] = make_double2((double)ax, (double)ay);
         }
         return;
     }
     for (int row = row0 + warp; row < row0 + nrows; row += blockDim.x >> 5) {
-        double ax[RB], ay[RB];
+        T ax[RB], ay[RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r) { ax[r] = 0.0; ay[r] = 0.0; }
+        for (int r = 0; r < RB; ++r) { ax[r] = 0; ay[r] = 0; }
         const MT* mr = M + (int64_t)row * n;
         for (int j = lane; j < n; j += 32) {
-            const double2 a = ld_mat(mr + j);
+            const cpx<T> a = ld_mat(mr + j);
 #pragma unroll
-            for (int r = 0; r < RB; ++r) {
-                const double2 v = nd_sm[r * sn + j];
-                ax[r] = fma(a.x, v.x, fma(-a.y, v.y, ax[r]));
-                ay[r] = fma(a.x, v.y, fma(a.y, v.x, ay[r]));
-            }
+            for (int r = 0; r < RB; ++r) cfma(ax[r], ay[r], a, nd_sm[r * sn + j]);
         }
 #pragma unroll
         for (int r = 0; r < RB; ++r)
@@ -536,11 +531,11 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
                 ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
             }
         if (lane < nr) {
-            double sx = 0.0, sy = 0.0;
+            T sx = 0, sy = 0;
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if (r == lane) { sx = ax[r]; sy = ay[r]; }
-            x[(r0 + lane) * nc + f0 + row] = make_double2(sx, sy);
+            x[(r0 + lane) * nc + f0 + row] = make_double2((double)sx, (double)sy);
         }
     }
 }
@@ -1605,13 +1600,13 @@ void nd_set_smem_limits() {
 template <class MT, int RB>
 static void nd_fwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* t, double2* y,
                      double2* u, int R, const int* done, cudaStream_t st) {
-    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(double2));
+    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(MT));
     k_nd_forward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, t, y, u, R, done);
 }
 template <class MT, int RB>
 static void nd_bwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* y, double2* x,
                      int R, const int* done, cudaStream_t st) {
-    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(double2));
+    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(MT));
     k_nd_backward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, y, x, R, done);
 }
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
