@@ -688,7 +688,9 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     ks.release();
     KrylovDev& K = ks.K;
     K.nd = nd; K.m = m; K.R = R;
-    K.chunk = nd <= 16384 ? 128 : 256;   // rows per CTA in the orthogonalisation kernels
+    // rows per CTA in the orthogonalisation kernels: 128 for short vectors, else at most ~512
+    // chunks per right-hand side (the last CTA of each right-hand side sums the chunk partials)
+    K.chunk = nd <= 16384 ? 128 : std::min(4096, std::max(256, ((nd + 511) / 512 + 255) / 256 * 256));
     K.nchunk = (nd + K.chunk - 1) / K.chunk;
     auto al = [&](size_t bytes, void** p) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
@@ -933,7 +935,8 @@ static ddh_status primal_residual_dev(ddh_ctx* ctx, const double2* bt, const dou
 template <class T>
 static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit, int R, double tol, int maxit,
                                  int restart, int check_every, std::vector<int>& its, std::vector<double>& res,
-                                 double primal_tol = 0.0, std::vector<double>* primal = nullptr) {
+                                 double primal_tol = 0.0, std::vector<double>* primal = nullptr,
+                                 bool interior = true) {
     const DevModel& d = ctx->dm;
     Work w;
     ddh_status st;
@@ -944,7 +947,9 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
     if ((st = get_work(ctx, gname, sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &g))) return st;
     if ((st = get_work(ctx, nname, sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &nu))) return st;
     // g = C^ A^-1 b^
-    apply_op<T>(ctx, w, nullptr, 0.0, bt, 1, (double2*)g, nullptr, R, nullptr);
+    // (the interior FDM terms of the load are skipped when the load has no interior part)
+    const int has_bI = interior ? 1 : 0;
+    apply_op<T>(ctx, w, nullptr, 0.0, bt, has_bI, (double2*)g, nullptr, R, nullptr);
     if ((st = ensure_krylov(ctx, ctx->kin, d.n_dual, R, restart))) return st;
     KrylovOps ops = dual_ops<T>(ctx, w);
     double tol_d = tol;
@@ -961,7 +966,7 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
         for (int i = 0; i < R; ++i) its[i] += its_c[i];
         res = res_c;
         // recovery: A^ phi_p = b^ - C^T nu
-        apply_op<T>(ctx, w, (const double2*)nu, -1.0, bt, 1, nullptr, phit, R, nullptr);
+        apply_op<T>(ctx, w, (const double2*)nu, -1.0, bt, has_bI, nullptr, phit, R, nullptr);
         if (primal_tol <= 0.0 || d.n_dual == 0) break;
         std::vector<double> pr;
         if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) return st;
@@ -1032,6 +1037,16 @@ static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
     if ((st = get_work(ctx, "phit", sizeof(double2) * (size_t)R * d.n_local, &phit))) return st;
     launch_basis(d, b_dev, (double2*)bt, 0, R, ctx->stream);
     ctx->launches++;
+    // does the load reach the element interiors?  (boundary loads such as plane-wave impedance
+    // data do not, and then the RHS pass and recovery skip the interior load terms)
+    void* fl;
+    if ((st = get_work(ctx, "iflag", sizeof(int), &fl))) return st;
+    CK(cudaMemsetAsync(fl, 0, sizeof(int), ctx->stream));
+    launch_interior_nz(d, (const double2*)bt, (int*)fl, R, ctx->stream);
+    ctx->launches++;
+    int hflag = 1;
+    CK(cudaMemcpyAsync(&hflag, fl, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     std::vector<int> its;
     std::vector<double> res;
     std::vector<double> pr;
@@ -1039,7 +1054,7 @@ static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
     struct Off { ddh_ctx* c; ~Off() { c->refine_active = false; } } off_guard{ctx};
     if ((st = dd_solve_tilde<double>(ctx, (const double2*)bt, (double2*)phit, R, tol, ctx->opt.maxit,
                                      std::min(std::max(2, ctx->opt.restart), 200), ctx->opt.check_every, its, res,
-                                     tol, &pr)))
+                                     tol, &pr, hflag != 0)))
         return st;
     launch_basis(d, (const double2*)phit, u_dev, 0, R, ctx->stream);
     ctx->launches++;

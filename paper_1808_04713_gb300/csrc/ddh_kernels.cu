@@ -540,7 +540,8 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
     }
 }
 
-// r = t - K x with K in CSR (one warp per row, all right-hand sides)
+// r = t - K x with K in CSR (one warp per row, lanes across the row's entries, up to 8
+// right-hand sides per pass so each matrix entry is loaded once per 8)
 __global__ void k_csr_residual(const int* __restrict__ ptr, const int* __restrict__ col,
                                const double2* __restrict__ val, int n, const double2* __restrict__ x,
                                const double2* __restrict__ t, double2* __restrict__ r, int R,
@@ -550,18 +551,34 @@ __global__ void k_csr_residual(const int* __restrict__ ptr, const int* __restric
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
     const int a0 = ptr[row], a1 = ptr[row + 1];
-    for (int rr = 0; rr < R; ++rr) {
-        const double2* xr = x + (int64_t)rr * n;
-        double sx = 0, sy = 0;
+    for (int r0 = 0; r0 < R; r0 += 8) {
+        double sx[8], sy[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { sx[q] = 0; sy[q] = 0; }
         for (int a = a0 + lane; a < a1; a += 32) {
-            const double2 av = val[a], xv = xr[col[a]];
-            sx = fma(av.x, xv.x, fma(-av.y, xv.y, sx));
-            sy = fma(av.x, xv.y, fma(av.y, xv.x, sy));
+            const double2 av = val[a];
+            const int c = col[a];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (r0 + q < R) {
+                    const double2 xv = x[(int64_t)(r0 + q) * n + c];
+                    sx[q] = fma(av.x, xv.x, fma(-av.y, xv.y, sx[q]));
+                    sy[q] = fma(av.x, xv.y, fma(av.y, xv.x, sy[q]));
+                }
         }
-        for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
-        if (lane == 0) {
-            const double2 tv = t[(int64_t)rr * n + row];
-            r[(int64_t)rr * n + row] = make_double2(tv.x - sx, tv.y - sy);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            for (int o = 16; o > 0; o >>= 1) {
+                sx[q] += __shfl_xor_sync(0xffffffffu, sx[q], o);
+                sy[q] += __shfl_xor_sync(0xffffffffu, sy[q], o);
+            }
+        if (lane < 8 && r0 + lane < R) {
+            double ox = 0, oy = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q == lane) { ox = sx[q]; oy = sy[q]; }
+            const double2 tv = t[(int64_t)(r0 + lane) * n + row];
+            r[(int64_t)(r0 + lane) * n + row] = make_double2(tv.x - ox, tv.y - oy);
         }
     }
 }
@@ -942,7 +959,12 @@ __global__ void k_basis(DevModel dm, const double2* __restrict__ x, double2* __r
     }
 }
 
-// (A phi) per element in FP64 (interpolatory basis), out = b - A phi (b may be null)
+// (A phi) per element in FP64 (interpolatory basis), out = b - A phi (b may be null).  The
+// operator is applied one direction at a time with the sparse 1-D tables: along x2,
+//   T1 = Phi Mt^T,  T2 = Phi Kt^T   (T[c][b] = sum_d X[b][d] Phi[c][d]),
+// then along x1, (A Phi)[a][b] = sum_c Kt[a][c] T1[c][b] + Mt[a][c] (T2 + c_e T1)[c][b], plus
+// the Robin terms (T1 on the sides a = 0, 1; Mt along x1 on the sides b = 0, 1).  Every row
+// of Mt and Kt has at most six entries (cand_list), so this is O(p^2) per element.
 __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2* __restrict__ phi,
                                                      const double2* __restrict__ b, double2* __restrict__ out) {
     extern __shared__ __align__(128) char smem[];
@@ -950,6 +972,10 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
     const int p = dm.p[e], N = p + 1;
     const CtaGroup g;
     ElemSmem<double> s = carve<double>(smem, dm.pmax, 0);
+    const int NP = dm.pmax + 1;
+    cpx<double>* T1 = s.vec;                 // [N][N], index c + N b
+    cpx<double>* T2 = s.vec + NP * NP;
+    cpx<double>* S1 = s.vec + 2 * NP * NP;   // [2][N]: sum_c Mt[a][c] Phi[c][b'] for b' = 0, 1
     load_tables<double>(g, dm, e, s);
     const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) { const double2 v = phi[base + i]; s.tile[i] = mk<double>(v.x, v.y); }
@@ -958,7 +984,48 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
     elem_gam<double>(dm, e, gam);
     const double ce = dm.c[e];
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        const cpx<double> v = apply_A_entry<double>(s.tile, s.Mt, p, ce, gam, idx % N, idx / N, false);
+        const int c = idx % N, bb = idx / N;
+        int cd[6];
+        const int nd = cand_list(bb, p, cd);
+        cpx<double> t1 = mk<double>(0, 0), t2 = mk<double>(0, 0);
+        for (int q = 0; q < nd; ++q) {
+            const int d = cd[q];
+            const cpx<double> v = s.tile[c + N * d];
+            fma_r(t1, s.Mt[bb * N + d], v);
+            const double kv = kt<double>(bb, d);
+            if (kv != 0.0) fma_r(t2, kv, v);
+        }
+        T1[idx] = t1;
+        T2[idx] = t2 + ce * t1;
+    }
+    for (int idx = threadIdx.x; idx < 2 * N; idx += blockDim.x) {
+        const int a = idx % N, bp = idx / N;
+        int ca[6];
+        const int na = cand_list(a, p, ca);
+        cpx<double> v = mk<double>(0, 0);
+        for (int q = 0; q < na; ++q) fma_r(v, s.Mt[a * N + ca[q]], s.tile[ca[q] + N * bp]);
+        S1[idx] = v;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        const int a = idx % N, bb = idx / N;
+        int ca[6];
+        const int na = cand_list(a, p, ca);
+        cpx<double> v = mk<double>(0, 0);
+        for (int q = 0; q < na; ++q) {
+            const int c = ca[q];
+            fma_r(v, s.Mt[a * N + c], T2[c + N * bb]);
+            const double kv = kt<double>(a, c);
+            if (kv != 0.0) fma_r(v, kv, T1[c + N * bb]);
+        }
+        // Robin: i g (...) with g the imaginary part of gamma_eff on the side
+        cpx<double> rob = mk<double>(0, 0);
+        if (a == 1 && gam[0] != 0.0) rob += gam[0] * T1[1 + N * bb];
+        if (a == 0 && gam[1] != 0.0) rob += gam[1] * T1[0 + N * bb];
+        if (bb == 1 && gam[2] != 0.0) rob += gam[2] * S1[a + N * 1];
+        if (bb == 0 && gam[3] != 0.0) rob += gam[3] * S1[a + N * 0];
+        v.x -= rob.y;
+        v.y += rob.x;
         double2 o = make_double2(-v.x, -v.y);
         if (b) { const double2 bv = b[base + idx]; o.x += bv.x; o.y += bv.y; }
         out[base + idx] = o;
@@ -1145,7 +1212,7 @@ __global__ void k_store(KrylovDev K) {
 }
 
 // CGS2 orthogonalisation of w against V_0..V_j, normalisation of V_{j+1} and the Givens
-// update of the Hessenberg column, in three kernels.  Each CTA owns one chunk of blockDim.x
+// update of the Hessenberg column, in three kernels.  Each CTA owns one chunk of K.chunk
 // consecutive rows of one right-hand side (grid nchunk x R); the cross-chunk sums are taken
 // by the last CTA of each right-hand side to finish (a counter per right-hand side, reset by
 // that CTA), so no kernel re-reduces the chunk partials of another.
@@ -1230,10 +1297,10 @@ __global__ void __launch_bounds__(256) k_cgs_first(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
-    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
-    __shared__ double2 ws[256];
+    const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
+    extern __shared__ __align__(16) double2 ws[];          // [K.chunk]
     __shared__ int last_f;
-    if ((int)threadIdx.x < rows) ws[threadIdx.x] = K.w[(int64_t)r * K.nd + q0 + threadIdx.x];
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) ws[t] = K.w[(int64_t)r * K.nd + q0 + t];
     __syncthreads();
     cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
     if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
@@ -1243,15 +1310,16 @@ __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
-    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
-    __shared__ double2 ws[256], h[256];
+    const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
+    extern __shared__ __align__(16) double2 ws[];          // [K.chunk]
+    __shared__ double2 h[256];
     __shared__ double red[8];
     __shared__ int last_f;
     for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = K.hcol[(int64_t)r * (K.m + 1) + i];
     __syncthreads();
     double nrm = 0;
-    if ((int)threadIdx.x < rows) {
-        const int64_t q = q0 + threadIdx.x;
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int64_t q = q0 + t;
         double2 w = K.w[(int64_t)r * K.nd + q];
         for (int i = 0; i <= j; ++i) {
             const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
@@ -1260,8 +1328,8 @@ __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
             w.y -= v.x * hh.y + v.y * hh.x;
         }
         K.w[(int64_t)r * K.nd + q] = w;
-        ws[threadIdx.x] = w;
-        nrm = w.x * w.x + w.y * w.y;
+        ws[t] = w;
+        nrm += w.x * w.x + w.y * w.y;
     }
     nrm = block_sum(nrm, red);          // also orders the ws writes before the dots
     if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nrm, 0.0);
@@ -1282,7 +1350,7 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
-    const int q0 = chunk * blockDim.x, rows = min((int)blockDim.x, K.nd - q0);
+    const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
     __shared__ double2 h[256];
     __shared__ double red[8];
     __shared__ int last_f;
@@ -1293,8 +1361,8 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     const double sc = hp > 0 ? 1.0 / hp : 1.0;
     double2* vnew = K.V + ((int64_t)r * (K.m + 1) + j + 1) * K.nd;
     double nv = 0;
-    if ((int)threadIdx.x < rows) {
-        const int64_t q = q0 + threadIdx.x;
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int64_t q = q0 + t;
         double2 w = K.w[(int64_t)r * K.nd + q];
         for (int i = 0; i <= j; ++i) {
             const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
@@ -1304,7 +1372,7 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
         }
         w.x *= sc; w.y *= sc;
         vnew[q] = w;
-        nv = w.x * w.x + w.y * w.y;
+        nv += w.x * w.x + w.y * w.y;
     }
     nv = block_sum(nv, red);
     if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nv, 0.0);
@@ -1675,11 +1743,27 @@ void launch_points(const DevModel& dm, const int* pe, const double* pu, int P, i
                    int adjoint, cudaStream_t st) {
     k_points<<<(P + 7) / 8, 256, 0, st>>>(dm, pe, pu, P, R, in, out, adjoint);
 }
+// flag |= 1 when some element has a nonzero interior (a, b >= 2) load coefficient
+__global__ void k_interior_nz(DevModel dm, const double2* __restrict__ bt, int* __restrict__ flag) {
+    const int e = blockIdx.x, r = blockIdx.y;
+    const int p = dm.p[e], N = p + 1, n = p - 1;
+    const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
+    int nz = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const double2 v = bt[base + (idx % n + 2) + N * (idx / n + 2)];
+        nz |= (v.x != 0.0 || v.y != 0.0);
+    }
+    if (__syncthreads_or(nz) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+void launch_interior_nz(const DevModel& dm, const double2* bt, int* flag, int R, cudaStream_t st) {
+    k_interior_nz<<<dim3(dm.E, R), 128, 0, st>>>(dm, bt, flag);
+}
 void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st) {
     k_basis<<<dim3(dm.E, R), 128, 0, st>>>(dm, x, y, conj_in);
 }
+static size_t elem_matvec_smem(int pmax) { return elem_smem_bytes<double>(pmax, 2 * (pmax + 1) * (pmax + 1) + 2 * (pmax + 1)); }
 void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st) {
-    const size_t sm = elem_smem_bytes<double>(dm.pmax, 0);
+    const size_t sm = elem_matvec_smem(dm.pmax);
     k_elem_matvec<<<dim3(dm.E, R), 128, sm, st>>>(dm, phi, b, out);
 }
 void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st) {
@@ -1703,9 +1787,11 @@ template void launch_pre_krylov<float>(const DevModel&, const KrylovDev&, void*,
 
 void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st) {
     const dim3 gc(K.nchunk, K.R);
-    k_cgs_first<<<gc, K.chunk, 0, st>>>(K);
-    k_cgs_second<<<gc, K.chunk, 0, st>>>(K);
-    k_cgs_final<<<gc, K.chunk, 0, st>>>(K);
+    const int nt = std::min(K.chunk, 256);
+    const size_t sm = sizeof(double2) * (size_t)K.chunk;
+    k_cgs_first<<<gc, nt, sm, st>>>(K);
+    k_cgs_second<<<gc, nt, sm, st>>>(K);
+    k_cgs_final<<<gc, nt, 0, st>>>(K);
 }
 void launch_fetch(const KrylovDev& K, cudaStream_t st) {
     k_fetch<<<dim3((K.nd + 255) / 256, K.R), 256, 0, st>>>(K);
@@ -1748,11 +1834,13 @@ static void set_pass_limits(int pmax, int maxE1) {
     cudaFuncSetAttribute(k_pass2<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 void set_smem_limits(int pmax, int maxE1) {
+    cudaFuncSetAttribute(k_cgs_first, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
+    cudaFuncSetAttribute(k_cgs_second, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
     set_pass_limits<double, 1>(pmax, maxE1); set_pass_limits<double, 2>(pmax, maxE1);
     set_pass_limits<double, 4>(pmax, maxE1); set_pass_limits<double, 8>(pmax, maxE1);
     set_pass_limits<float, 1>(pmax, maxE1); set_pass_limits<float, 2>(pmax, maxE1);
     set_pass_limits<float, 4>(pmax, maxE1); set_pass_limits<float, 8>(pmax, maxE1);
-    cudaFuncSetAttribute(k_elem_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_smem_bytes<double>(pmax, 0));
+    cudaFuncSetAttribute(k_elem_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)elem_matvec_smem(pmax));
     const int pre64 = (int)(sizeof(cpx<double>) * 8 * (size_t)maxE1 + sizeof(double) * (size_t)maxE1 * maxE1 + 16);
     const int pre32 = (int)(sizeof(cpx<float>) * 8 * (size_t)maxE1 + sizeof(float) * (size_t)maxE1 * maxE1 + 16);
     cudaFuncSetAttribute(k_pre_elem<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);

@@ -29,6 +29,8 @@ void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, cons
 template <class T>
 void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
                        const int* done, cudaStream_t st);
+// *flag |= 1 when the (interpolatory-basis) load has a nonzero interior coefficient
+void launch_interior_nz(const DevModel& dm, const double2* bt, int* flag, int R, cudaStream_t st);
 template <class T>
 void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
                             double2* t, int R, const int* done, cudaStream_t st);
