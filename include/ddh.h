@@ -77,8 +77,8 @@ typedef struct {
     int32_t l_override;    /* 0: dispersion criterion; >0: primal constraints per edge */
     int32_t precision;     /* ddh_precision */
     int32_t precond;       /* ddh_precond */
-    int32_t inner_iters;   /* mixed precision: dual FGMRES iterations per preconditioner
-                              application (default 12) */
+    int32_t inner_iters;   /* mixed precision: at most this many dual FGMRES iterations per
+                              preconditioner application (default 10) */
     int32_t check_every;   /* host polls convergence every this many iterations (default 4) */
     int32_t use_graph;     /* 1: replay one FGMRES iteration as a CUDA graph (default 1) */
     int32_t coarse_fp32;   /* mixed precision only: 1 = inside the inner (preconditioner) solves,
@@ -88,6 +88,10 @@ typedef struct {
     int32_t local_form;    /* local solves inside the Krylov loop (ddh_local_form): explicit edge
                               operators (default) or the FDM on the interior cross; the same
                               A11^-1, so the iterates agree to rounding */
+    double inner_tol;      /* mixed precision: an inner solve also stops once its dual residual
+                              estimate falls below inner_tol relative to its start (default
+                              1e-5; 0 = always inner_iters iterations).  The complex64 inner
+                              solves cannot gain much more than 5-6 digits per application */
 } ddh_options;
 
 typedef struct {

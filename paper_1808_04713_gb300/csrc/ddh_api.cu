@@ -1101,8 +1101,8 @@ static ddh_status solve_mixed(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
         std::vector<int> its_in;
         std::vector<double> res_in;
         ctx->coarse32 = ctx->opt.coarse_fp32 != 0;
-        ddh_status st2 = dd_solve_tilde<float>(ctx, (const double2*)bin, (double2*)phin, R, 0.0, m_in, m_in, m_in,
-                                               its_in, res_in);
+        ddh_status st2 = dd_solve_tilde<float>(ctx, (const double2*)bin, (double2*)phin, R,
+                                               std::max(0.0, ctx->opt.inner_tol), m_in, m_in, m_in, its_in, res_in);
         ctx->coarse32 = false;
         if (st2) return st2;
         launch_readback(d, (const double2*)phin, out, R, s);
@@ -1136,11 +1136,12 @@ void ddh_default_options(ddh_options* o) {
     o->l_override = 0;
     o->precision = DDH_PREC_FP64;
     o->precond = DDH_PRECOND_DIRICHLET;
-    o->inner_iters = 12;
+    o->inner_iters = 10;
     o->check_every = 4;
     o->use_graph = 1;
     o->coarse_fp32 = 0;
     o->local_form = DDH_LOCAL_EDGE;
+    o->inner_tol = 1e-5;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {

@@ -31,7 +31,8 @@ class Options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
-                ("coarse_fp32", C.c_int32), ("local_form", C.c_int32)]
+                ("coarse_fp32", C.c_int32), ("local_form", C.c_int32),
+                ("inner_tol", C.c_double)]
 
 
 class Info(C.Structure):
