@@ -38,6 +38,7 @@ struct KState {
     std::vector<void*> allocs;
     double2* r = nullptr;
     double* nrm2 = nullptr;
+    double* npart = nullptr;   // R x 64 partial sums of the norms
     double2* ydev = nullptr;
     int* nitdev = nullptr;
     int* h_ctl = nullptr;       // pinned: ctl[0..3], rdone[R], iters[R]
@@ -721,6 +722,7 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.zw = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); ks.r = (double2*)p;
     ok &= al(sizeof(double) * (size_t)R, &p); ks.nrm2 = (double*)p;
+    ok &= al(sizeof(double) * 64 * (size_t)R, &p); ks.npart = (double*)p;
     ok &= al(sizeof(double2) * (size_t)R * m, &p); ks.ydev = (double2*)p;
     ok &= al(sizeof(int) * (size_t)R, &p); ks.nitdev = (int*)p;
     if (!ok) { ctx->err = "cudaMalloc failed (Krylov state)"; return DDH_ERR_OOM; }
@@ -824,10 +826,12 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
     double2* r = ks.r;
     std::vector<double> h_b(R), h_n(R);
     CK(cudaMemsetAsync(ks.nrm2, 0, sizeof(double) * R, ctx->stream));
-    launch_norm2(bvec, nd, ks.nrm2, R, ctx->stream);
+    launch_norm2(bvec, nd, ks.nrm2, ks.npart, R, ctx->stream);
+    ctx->launches += 2;
     if (warm) {
         ops.op(x_out, K.w, nullptr);
         launch_axpby(bvec, 1.0, K.w, -1.0, r, (int64_t)R * nd, ctx->stream);
+        ctx->launches++;
     } else {
         CK(cudaMemcpyAsync(r, bvec, sizeof(double2) * (size_t)R * nd, cudaMemcpyDeviceToDevice, ctx->stream));
     }
@@ -843,7 +847,8 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
     while (true) {
         // (re)start: V0 = r / ||r||, g = (||r||, 0, ...)
         CK(cudaMemsetAsync(ks.nrm2, 0, sizeof(double) * R, ctx->stream));
-        launch_norm2(r, nd, ks.nrm2, R, ctx->stream);
+        launch_norm2(r, nd, ks.nrm2, ks.npart, R, ctx->stream);
+        ctx->launches += 2;
         CK(cudaMemcpyAsync(h_n.data(), ks.nrm2, sizeof(double) * R, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         std::vector<double2> g0((size_t)R * (m + 1), make_double2(0, 0));
@@ -854,6 +859,7 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
             rd[i] = active[i] ? 0 : 1;
             const double sc = (active[i] && nr > 0) ? 1.0 / nr : 0.0;
             launch_axpby(r + (size_t)i * nd, sc, nullptr, 0.0, K.V + (size_t)i * (m + 1) * nd, nd, ctx->stream);
+            ctx->launches++;
         }
         CK(cudaMemcpyAsync(K.g, g0.data(), sizeof(double2) * g0.size(), cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(K.rdone, rd.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
@@ -894,11 +900,13 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
         CK(cudaMemcpyAsync(ks.ydev, y.data(), sizeof(double2) * (size_t)R * m, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(ks.nitdev, nit.data(), sizeof(int) * R, cudaMemcpyHostToDevice, ctx->stream));
         launch_update(K.Zb, ks.ydev, ks.nitdev, x_out, nd, m, R, ctx->stream);
+        ctx->launches++;
         total += j;
         if (alldone || total >= maxit) break;
         // true residual r = b - A x for the next cycle
         ops.op(x_out, K.w, nullptr);
         launch_axpby(bvec, 1.0, K.w, -1.0, r, (int64_t)R * nd, ctx->stream);
+        ctx->launches++;
     }
     CK(cudaGetLastError());
     return DDH_OK;

@@ -1484,8 +1484,9 @@ __global__ void k_axpby(const double2* x, double a, const double2* y, double b, 
     out[i] = make_double2(a * xv.x + b * yv.x, a * xv.y + b * yv.y);
 }
 
-// sum of |x|^2 per RHS (x: [R][n]) atomically into out[r]
-__global__ void k_norm2(const double2* __restrict__ x, int64_t n, double* __restrict__ out) {
+// ||x_r||^2 in two fixed-order stages (no atomics, so the result is the same on every run):
+// 64 CTAs per right-hand side write partial sums, then one warp per right-hand side adds them
+__global__ void k_norm2(const double2* __restrict__ x, int64_t n, double* __restrict__ part) {
     const int r = blockIdx.y;
     double s = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1499,8 +1500,15 @@ __global__ void k_norm2(const double2* __restrict__ x, int64_t n, double* __rest
     if (threadIdx.x == 0) {
         double t = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-        atomicAdd(&out[r], t);
+        part[(int64_t)r * gridDim.x + blockIdx.x] = t;
     }
+}
+__global__ void k_norm2_sum(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    const int r = blockIdx.x, lane = threadIdx.x;
+    double s = 0;
+    for (int i = lane; i < nb; i += 32) s += part[(int64_t)r * nb + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
 }
 
 // ------------------------------------------------------------------ launch wrappers
@@ -1805,8 +1813,9 @@ void launch_update(const double2* Zb, const double2* y, const int* nit, double2*
 void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st) {
     k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, a, y, b, out, n);
 }
-void launch_norm2(const double2* x, int64_t n, double* out, int R, cudaStream_t st) {
-    k_norm2<<<dim3(64, R), 256, 0, st>>>(x, n, out);
+void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R, cudaStream_t st) {
+    k_norm2<<<dim3(64, R), 256, 0, st>>>(x, n, part);
+    k_norm2_sum<<<R, 32, 0, st>>>(part, 64, out);
 }
 
 void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st) {

@@ -100,7 +100,8 @@ void launch_fetch(const KrylovDev& K, cudaStream_t st);
 void launch_store(const KrylovDev& K, cudaStream_t st);
 void launch_update(const double2* Zb, const double2* y, const int* nit, double2* nu, int nd, int m, int R, cudaStream_t st);
 void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st);
-void launch_norm2(const double2* x, int64_t n, double* out, int R, cudaStream_t st);
+// out[r] = ||x_r||^2 (deterministic; part: R x 64 doubles of scratch)
+void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R, cudaStream_t st);
 void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st);
 void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, double sign, int R, cudaStream_t st);
 void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st);
