@@ -245,6 +245,28 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, Vall, &d.V_all))) return st;
     if ((st = upload(ctx, muall, &d.mu_all))) return st;
     if ((st = upload(ctx, Sall, &d.slap_all))) return st;
+    // S^Lap restricted to each element's type-1 edge slots (symmetric n_E x n_E), one copy per
+    // distinct (degree, slot pattern): on conforming meshes one per degree
+    {
+        std::map<std::pair<int, std::vector<int32_t>>, int64_t> seen;
+        std::vector<double> pre;
+        std::vector<int64_t> poff(E);
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            std::vector<int32_t> pat(m.e1_eall.begin() + El.e1_off, m.e1_eall.begin() + El.e1_off + El.nE1);
+            auto key = std::make_pair(El.ptab, pat);
+            auto it = seen.find(key);
+            if (it != seen.end()) { poff[e] = it->second; continue; }
+            const PTable& T = m.tabs[El.ptab];
+            const int ne = 4 * (El.p - 1), nE = El.nE1;
+            poff[e] = (int64_t)pre.size();
+            for (int i = 0; i < nE; ++i)
+                for (int j = 0; j < nE; ++j) pre.push_back(T.Slap[(size_t)pat[i] * ne + pat[j]]);
+            seen.emplace(std::move(key), poff[e]);
+        }
+        if ((st = upload(ctx, pre, &d.pre_all))) return st;
+        if ((st = upload(ctx, poff, &d.pre_off))) return st;
+    }
     // slots
     if ((st = upload(ctx, m.e1_slot, &d.e1_slot))) return st;
     if ((st = upload(ctx, m.e1_row, &d.e1_row))) return st;
@@ -631,7 +653,7 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
 // w = F z (zsign = +1) or the RHS / recovery passes (bt != null)
 template <class T>
 static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign, const double2* bt, int has_bI,
-                     double2* out_dual, double2* phi_out, int R, const int* done) {
+                     double2* out_dual, double2* phi_out, int R, const int* done, const KrylovDev* kdots = nullptr) {
     const DevModel& d = ctx->dm;
     cudaStream_t s = ctx->stream;
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
@@ -644,7 +666,10 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     if (ctx->edge_form && !phi_out) launch_pass2_edge<T>(d, Y, w.x2, w.xE, w.xE2, R, done, s);
     else launch_pass2<T>(d, sinv, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
     ctx->launches++;
-    if (out_dual && d.n_dual > 0) {
+    if (kdots) {
+        launch_jump_gather_dots<T>(d, w.xE2, w.x2, *kdots, s);
+        ctx->launches++;
+    } else if (out_dual && d.n_dual > 0) {
         launch_jump_gather<T>(d, w.xE2, w.x2, out_dual, R, done, s);
         ctx->launches++;
     }
@@ -739,6 +764,8 @@ struct KrylovOps {
     std::function<ddh_status(const double2*, double2*, const int*)> prec;
     // optional: fetch V[j] + precondition + store Zb[j] in one go (replaces fetch/prec/store)
     std::function<void(const KrylovDev&)> prec_krylov;
+    // optional: w = op(in) into K.w together with the first CGS pass (used when K.chunk == 128)
+    std::function<void(const double2*, const KrylovDev&)> op_dots;
     bool graph = false;     // the body may be captured as a CUDA graph
     int key = 0;            // graph cache key (precision of the element kernels)
 };
@@ -755,9 +782,11 @@ static ddh_status iteration_body(ddh_ctx* ctx, KState& ks, const KrylovOps& ops)
         if (st) return st;
         launch_store(K, ctx->stream);
     }
-    ops.op(K.zw, K.w, done);
-    launch_krylov_iter_tail(K, ctx->stream);
-    ctx->launches += (ops.prec_krylov ? 0 : 2) + 3;
+    const bool fused = ops.op_dots && K.chunk == 128;
+    if (fused) ops.op_dots(K.zw, K);
+    else ops.op(K.zw, K.w, done);
+    launch_krylov_iter_tail(K, ctx->stream, fused);
+    ctx->launches += (ops.prec_krylov ? 0 : 2) + (fused ? 2 : 3);
     return DDH_OK;
 }
 
@@ -922,6 +951,10 @@ static KrylovOps dual_ops(ddh_ctx* ctx, const Work& w) {
         apply_prec<T>(ctx, w, in, out, ctx->kin.K.R, done);
         return DDH_OK;
     };
+    if (ctx->dm.n_dual > 0)
+        o.op_dots = [ctx, w](const double2* in, const KrylovDev& K) {
+            apply_op<T>(ctx, w, in, 1.0, nullptr, 0, K.w, nullptr, K.R, K.ctl + 1, &K);
+        };
     // conforming meshes with the Dirichlet preconditioner: fetch + precondition + store fused
     if (ctx->opt.precond == DDH_PRECOND_DIRICHLET && ctx->m.hblk_row0.empty()) {
         o.prec_krylov = [ctx, w](const KrylovDev& K) {

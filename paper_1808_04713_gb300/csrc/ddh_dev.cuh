@@ -57,6 +57,8 @@ struct DevModel {
     const double* V_all = nullptr;
     const double* mu_all = nullptr;
     const double* slap_all = nullptr;
+    const double* pre_all = nullptr;    // restricted S^Lap per (degree, slot pattern), n_E^2
+    const int64_t* pre_off = nullptr;   // per element: offset into pre_all
     // E1 slots
     const int* e1_slot = nullptr;
     const int* e1_row = nullptr;

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
 // chain.  Y is formed at factor time.  The interior never enters the iteration; it is
 // rebuilt by the FDM kernels in the recovery.
 template <class T, int RB>
-__global__ void __launch_bounds__(128) k_pass1_edge(DevModel dm, const cpx<T>* __restrict__ sinv,
+__global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                     const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
                                                     double zsign, const double2* __restrict__ bt, int R,
                                                     cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
@@ -209,7 +209,6 @@ __global__ void __launch_bounds__(128) k_pass1_edge(DevModel dm, const cpx<T>* _
     if (stage_off > 0 && nE > 0 && threadIdx.x == 0)
         bulk_load_start(bar, S_s, S, (uint32_t)(((size_t)nE * nE * sizeof(cpx<T>) + 15) & ~(size_t)15));
     cpx<T>* rE = reinterpret_cast<cpx<T>*>(smem);     // [RB][vs]
-    cpx<T>* xE = rE + RB * vs;                         // [RB][vs]
     const int64_t off = dm.off[e];
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
         const int q = idx / nE, i = idx % nE, r = r0 + q;
@@ -220,27 +219,52 @@ __global__ void __launch_bounds__(128) k_pass1_edge(DevModel dm, const cpx<T>* _
         rE[q * vs + i] = v;
     }
     g.sync();
-    // t_T = Y^T r_E (threads over (rhs, T slot)); issued before the wait for S_E^-1
-    const cpx<T>* Ye = Y + dm.pq_off[e];
-    for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
-        const int q = idx / nT, t = idx % nT;
-        cpx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
-        int i = 0;
-        for (; i + 1 < nE; i += 2) {
-            fma_c(a0, Ye[(int64_t)i * nT + t], rE[q * vs + i]);
-            fma_c(a1, Ye[(int64_t)(i + 1) * nT + t], rE[q * vs + i + 1]);
-        }
-        if (i < nE) fma_c(a0, Ye[(int64_t)i * nT + t], rE[q * vs + i]);
-        tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + t] = a0 + a1;
-    }
     if (stage_off > 0 && nE > 0) {
         if (!bulk_wait_all(bar, dm.err)) return;
         S = S_s;
     }
-    sinv_apply_batched<T, RB>(g, S, nE, cnt, rE, vs, xE);
-    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
-        const int q = idx / nE, i = idx % nE;
-        xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = xE[q * vs + i];
+    // [x_E; t_T] = [S_E^-1; Y^T] r_E in one pass: output row o < nE reads S_E^-1 (column-major),
+    // o >= nE reads Y (row-major nE x nT, i.e. Y^T column-major); tpr threads per output row
+    const cpx<T>* Ye = Y + dm.pq_off[e];
+    const int no = nE + nT;
+    const int tpr = no <= 64 ? 4 : (no <= 128 ? 2 : 1);       // 256 threads
+    const int chunk = (nE + tpr - 1) / tpr;
+    for (int base = 0; base < no * tpr; base += blockDim.x) {
+        const int slot = base + threadIdx.x;
+        const int o = slot / tpr, part = slot % tpr;
+        cpx<T> a0[RB], a1[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
+        if (o < no) {
+            const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
+            const int ld = o < nE ? nE : nT;
+            const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
+                const cpx<T> s0 = col0[(int64_t)j * ld], s1 = col0[(int64_t)(j + 1) * ld];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) { fma_c(a0[q], s0, rE[q * vs + j]); fma_c(a1[q], s1, rE[q * vs + j + 1]); }
+            }
+            if (j < j1) {
+                const cpx<T> s0 = col0[(int64_t)j * ld];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            cpx<T> v = a0[q] + a1[q];
+            for (int sh = 1; sh < tpr; sh <<= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, sh);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, sh);
+            }
+            if (part == 0 && o < no && q < cnt) {
+                if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
+                else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
+            }
+        }
     }
 }
 
@@ -333,7 +357,27 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
     double sx[RB], sy[RB];
 #pragma unroll
     for (int q = 0; q < RB; ++q) { sx[q] = 0; sy[q] = 0; }
-    for (int j = lane; j < n_in; j += 32) {
+    int j = lane;
+    if (RB == 1) {
+        // one right-hand side: four loads in flight per lane, two accumulator chains
+        double tx = 0, ty = 0;
+        for (; j + 96 < n_in; j += 128) {
+            const M a0 = a[j], a1 = a[j + 32], a2 = a[j + 64], a3 = a[j + 96];
+            const double2 x0 = x[r0 * xs + j], x1 = x[r0 * xs + j + 32];
+            const double2 x2 = x[r0 * xs + j + 64], x3 = x[r0 * xs + j + 96];
+            sx[0] = fma((double)a0.x, x0.x, fma(-(double)a0.y, x0.y, sx[0]));
+            sy[0] = fma((double)a0.x, x0.y, fma((double)a0.y, x0.x, sy[0]));
+            tx = fma((double)a1.x, x1.x, fma(-(double)a1.y, x1.y, tx));
+            ty = fma((double)a1.x, x1.y, fma((double)a1.y, x1.x, ty));
+            sx[0] = fma((double)a2.x, x2.x, fma(-(double)a2.y, x2.y, sx[0]));
+            sy[0] = fma((double)a2.x, x2.y, fma((double)a2.y, x2.x, sy[0]));
+            tx = fma((double)a3.x, x3.x, fma(-(double)a3.y, x3.y, tx));
+            ty = fma((double)a3.x, x3.y, fma((double)a3.y, x3.x, ty));
+        }
+        sx[0] += tx;
+        sy[0] += ty;
+    }
+    for (; j < n_in; j += 32) {
         const M av = a[j];
         const double ax = (double)av.x, ay = (double)av.y;
 #pragma unroll
@@ -358,6 +402,50 @@ __global__ void k_gemv(const M* __restrict__ A, int n_out, int n_in, const doubl
         if (mode == 0) yr[warp] = make_double2(vx, vy);
         else if (mode == 1) { yr[warp].x -= vx; yr[warp].y -= vy; }
         else { const double2 cv = c[(r0 + lane) * ys + warp]; yr[warp] = make_double2(cv.x - vx, cv.y - vy); }
+    }
+}
+
+// y = A x for one right-hand side: two warps per row (interleaved 32-column blocks), so that
+// twice as many warps per SM keep loads in flight for the FP64 pipe; 4 rows per 256 threads
+template <class M>
+__global__ void __launch_bounds__(256) k_gemv1(const M* __restrict__ A, int n_out, int n_in,
+                                               const double2* __restrict__ x, double2* __restrict__ y,
+                                               const double2* __restrict__ c, int mode, const int* __restrict__ done) {
+    if (done && *done) return;
+    __shared__ double2 red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * 4 + (warp >> 1), h = warp & 1;
+    double sx = 0, sy = 0, tx = 0, ty = 0;
+    if (row < n_out) {
+        const M* a = A + (int64_t)row * n_in;
+        int j = h * 32 + lane;
+        for (; j + 64 < n_in; j += 128) {
+            const M a0 = a[j], a1 = a[j + 64];
+            const double2 x0 = x[j], x1 = x[j + 64];
+            sx = fma((double)a0.x, x0.x, fma(-(double)a0.y, x0.y, sx));
+            sy = fma((double)a0.x, x0.y, fma((double)a0.y, x0.x, sy));
+            tx = fma((double)a1.x, x1.x, fma(-(double)a1.y, x1.y, tx));
+            ty = fma((double)a1.x, x1.y, fma((double)a1.y, x1.x, ty));
+        }
+        if (j < n_in) {
+            const M a0 = a[j];
+            const double2 x0 = x[j];
+            sx = fma((double)a0.x, x0.x, fma(-(double)a0.y, x0.y, sx));
+            sy = fma((double)a0.x, x0.y, fma((double)a0.y, x0.x, sy));
+        }
+    }
+    sx += tx; sy += ty;
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) red[warp] = make_double2(sx, sy);
+    __syncthreads();
+    if (h == 0 && lane == 0 && row < n_out) {
+        const double vx = red[warp].x + red[warp + 1].x, vy = red[warp].y + red[warp + 1].y;
+        if (mode == 0) y[row] = make_double2(vx, vy);
+        else if (mode == 1) { y[row].x -= vx; y[row].y -= vy; }
+        else { const double2 cv = c[row]; y[row] = make_double2(cv.x - vx, cv.y - vy); }
     }
 }
 
@@ -744,6 +832,40 @@ __global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __re
 
 // out_E = S^Lap[E1][E1] (C1^T v) per element (stiffness Schur complement, shared per degree);
 // one CTA per (element, block of RB RHS), each S^Lap entry read once per CTA.
+// out_E = S x for the restricted stiffness Schur complement S (n_E x n_E, symmetric, read from
+// global memory column by column: coalesced across output rows, shared by the elements of a
+// degree pattern and L1/L2-resident); tpr adjacent threads share an output row
+template <class T, int RB>
+__device__ __forceinline__ void pre_apply(const double* __restrict__ S, int nE, int cnt, const cpx<T>* in,
+                                          cpx<T>* __restrict__ out, int64_t ostride) {
+    const int tpr = nE <= 32 ? 4 : (nE <= 64 ? 2 : 1);
+    const int chunk = (nE + tpr - 1) / tpr;
+    for (int base = 0; base < nE * tpr; base += blockDim.x) {
+        const int slot = base + threadIdx.x;
+        const int i = slot / tpr, part = slot % tpr;
+        cpx<T> acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
+        if (i < nE) {
+            const int j1 = min(nE, (part + 1) * chunk);
+            for (int j = part * chunk; j < j1; ++j) {
+                const T sv = (T)__ldg(S + (int64_t)j * nE + i);
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            for (int o = 1; o < tpr; o <<= 1) {
+                acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+            }
+            if (part == 0 && i < nE && q < cnt) out[(int64_t)q * ostride + i] = acc[q];
+        }
+    }
+}
+
 template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __restrict__ v, cpx<T>* __restrict__ outE,
                                                   int R, const int* __restrict__ done) {
@@ -753,14 +875,6 @@ __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __
     const int cnt = min(RB, R - r0);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e];
     cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);                 // [RB][nE]
-    T* Ss = reinterpret_cast<T*>(smem + sizeof(cpx<T>) * RB * dm.maxE1);   // [nE][nE]
-    const int t = dm.ptab[e];
-    const int p = dm.p[e], ne = 4 * (p - 1);
-    const double* S = dm.slap_all + dm.tab_slap[t];
-    for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x) {
-        const int i = idx / nE, j = idx % nE;
-        Ss[idx] = (T)S[(int64_t)dm.e1_eall[e1o + i] * ne + dm.e1_eall[e1o + j]];
-    }
     for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
         const int q = idx / nE, i = idx % nE;
         const int row = dm.e1_row[e1o + i];
@@ -769,20 +883,7 @@ __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __
         in[q * nE + i] = val;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        cpx<T> acc[RB];
-#pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
-        for (int j = 0; j < nE; ++j) {
-            const T sv = Ss[i * nE + j];
-#pragma unroll
-            for (int q = 0; q < RB; ++q)
-                if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
-        }
-#pragma unroll
-        for (int q = 0; q < RB; ++q)
-            if (q < cnt) outE[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = acc[q];
-    }
+    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot);
 }
 
 // Conforming meshes (no hanging rows: D = 2 I, no C2 K C2^T term), fused with the Krylov
@@ -796,14 +897,6 @@ __global__ void __launch_bounds__(128) k_pre_elem_kry(DevModel dm, KrylovDev K, 
     const int cnt = min(RB, R - r0);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e];
     cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);
-    T* Ss = reinterpret_cast<T*>(smem + sizeof(cpx<T>) * RB * dm.maxE1);
-    const int t = dm.ptab[e];
-    const int p = dm.p[e], ne = 4 * (p - 1);
-    const double* S = dm.slap_all + dm.tab_slap[t];
-    for (int idx = threadIdx.x; idx < nE * nE; idx += blockDim.x) {
-        const int i = idx / nE, j = idx % nE;
-        Ss[idx] = (T)S[(int64_t)dm.e1_eall[e1o + i] * ne + dm.e1_eall[e1o + j]];
-    }
     for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
         const int q = idx / nE, i = idx % nE;
         const int row = dm.e1_row[e1o + i];
@@ -815,20 +908,7 @@ __global__ void __launch_bounds__(128) k_pre_elem_kry(DevModel dm, KrylovDev K, 
         in[q * nE + i] = val;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nE; i += blockDim.x) {
-        cpx<T> acc[RB];
-#pragma unroll
-        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
-        for (int j = 0; j < nE; ++j) {
-            const T sv = Ss[i * nE + j];
-#pragma unroll
-            for (int q = 0; q < RB; ++q)
-                if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
-        }
-#pragma unroll
-        for (int q = 0; q < RB; ++q)
-            if (q < cnt) outE[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = acc[q];
-    }
+    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot);
 }
 
 // z = D^-1 (outE[c] - outE[f]) with D = 2 I, written to zw and to the Krylov store Zb[r][j]
@@ -1306,6 +1386,44 @@ __global__ void __launch_bounds__(256) k_cgs_first(KrylovDev K) {
     if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
 }
 
+// Jump gather w = C^ x fused with the first CGS pass: the CTA that forms rows
+// [q0, q0 + 128) of w also takes their partial dots with V_0..V_j (chunk = 128 rows).
+template <class T>
+__global__ void __launch_bounds__(128) k_jump_gather_dots(DevModel dm, const cpx<T>* __restrict__ xE,
+                                                          const double2* __restrict__ x2, KrylovDev K) {
+    if (K.ctl[1]) return;
+    const int j = K.ctl[0];
+    const int chunk = blockIdx.x, r = blockIdx.y;
+    const int q0 = chunk * 128, rows = min(128, K.nd - q0);
+    __shared__ double2 ws[128];
+    __shared__ int last_f;
+    if ((int)threadIdx.x < rows) {
+        const int row = q0 + threadIdx.x;
+        double sx = 0, sy = 0;
+        const int c = dm.row_c[row], f = dm.row_f[row];
+        if (c >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + c]; sx += (double)v.x; sy += (double)v.y; }
+        { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
+        for (int a = dm.c2_ptr[row]; a < dm.c2_ptr[row + 1]; ++a) {
+            const double2 v = x2[(int64_t)r * dm.n_coarse + dm.c2_col[a]];
+            sx += dm.c2_w[a] * v.x;
+            sy += dm.c2_w[a] * v.y;
+        }
+        const double2 wv = make_double2(sx, sy);
+        K.w[(int64_t)r * K.nd + row] = wv;
+        ws[threadIdx.x] = wv;
+    }
+    __syncthreads();
+    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
+}
+template <class T>
+void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
+                             cudaStream_t st) {
+    k_jump_gather_dots<T><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
+}
+template void launch_jump_gather_dots<double>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
+template void launch_jump_gather_dots<float>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
+
 __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
@@ -1576,10 +1694,10 @@ void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, cons
     const cpx<T>* S = (const cpx<T>*)sinv;
     const cpx<T>* Yp = (const cpx<T>*)Y;
     switch (rb) {
-        case 8: k_pass1_edge<T, 8><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 4: k_pass1_edge<T, 4><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 2: k_pass1_edge<T, 2><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        default: k_pass1_edge<T, 1><<<ntask, 128, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
+        case 8: k_pass1_edge<T, 8><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 4: k_pass1_edge<T, 4><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 2: k_pass1_edge<T, 2><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        default: k_pass1_edge<T, 1><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
     }
 }
 template <class T>
@@ -1636,7 +1754,7 @@ void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, d
     k_dinv<<<gr, 128, 0, st>>>(dm, v, vd, lumped, done);
     const int rb = rhs_block(R);
     const dim3 g(dm.E, (R + rb - 1) / rb);
-    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + sizeof(T) * (size_t)dm.maxE1 * dm.maxE1 + 16;
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + 16;
     switch (rb) {
         case 8: k_pre_elem<T, 8><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
         case 4: k_pre_elem<T, 4><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
@@ -1724,6 +1842,12 @@ void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const 
 }
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st) {
+    if (R == 1) {
+        const dim3 g1((n_out + 3) / 4);
+        if (f32) k_gemv1<float2><<<g1, 256, 0, st>>>((const float2*)A, n_out, n_in, x, y, c, mode, done);
+        else k_gemv1<double2><<<g1, 256, 0, st>>>((const double2*)A, n_out, n_in, x, y, c, mode, done);
+        return;
+    }
     const int warps_per_block = 4;
     const dim3 g((n_out + warps_per_block - 1) / warps_per_block);
     const int tb = 32 * warps_per_block;
@@ -1781,7 +1905,7 @@ template <class T>
 void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R, cudaStream_t st) {
     const int rb = rhs_block(R);
     const dim3 g(dm.E, (R + rb - 1) / rb);
-    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + sizeof(T) * (size_t)dm.maxE1 * dm.maxE1 + 16;
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + 16;
     switch (rb) {
         case 8: k_pre_elem_kry<T, 8><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
         case 4: k_pre_elem_kry<T, 4><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
@@ -1793,11 +1917,11 @@ void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R
 template void launch_pre_krylov<double>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
 template void launch_pre_krylov<float>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
 
-void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st) {
+void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first) {
     const dim3 gc(K.nchunk, K.R);
     const int nt = std::min(K.chunk, 256);
     const size_t sm = sizeof(double2) * (size_t)K.chunk;
-    k_cgs_first<<<gc, nt, sm, st>>>(K);
+    if (!skip_first) k_cgs_first<<<gc, nt, sm, st>>>(K);
     k_cgs_second<<<gc, nt, sm, st>>>(K);
     k_cgs_final<<<gc, nt, 0, st>>>(K);
 }

@@ -93,7 +93,13 @@ void launch_points(const DevModel& dm, const int* pe, const double* pu, int P, i
 void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st);
 void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st);
 void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int R, cudaStream_t st);
-void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st);
+// CGS2 + normalisation + Givens of one FGMRES iteration; skip_first when the operator already
+// left the first projection's coefficients (launch_jump_gather_dots)
+void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first = false);
+// w = C^ x (into K.w) fused with the first CGS pass; requires K.chunk == 128
+template <class T>
+void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
+                             cudaStream_t st);
 template <class T>
 void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R, cudaStream_t st);
 void launch_fetch(const KrylovDev& K, cudaStream_t st);
