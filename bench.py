@@ -98,15 +98,15 @@ class ClockSampler:
 
 
 def algorithmic_work(info, R: int, p: int, nE: float, nT: float, fp64: bool):
-    """FLOPs and HBM bytes per launch of the operator components:
-    index 0 pass 1, 2 coarse solve, 3 pass 2 (per element: n = p - 1)."""
+    """FLOPs and HBM bytes per launch of the operator components, Krylov-loop
+    form with explicit edge operators: index 0 pass 1 ([S_E^-1; Y^T] r_E), 2 coarse solve
+    (dense K^-1), 3 pass 2 (x_E - Y u_T); n_E type-1 edge and n_T type-2 slots per element."""
     E = info.n_elem
-    n = p - 1
     cb = 16 if fp64 else 8
-    flops_pass1 = E * R * (8 * nE * nE + 40 * n * n + 100 * nT)
-    bytes_pass1 = E * (cb * nE * nE + R * cb * (3 * nE + nT))
-    flops_pass2 = E * R * (8 * nE * nE + 40 * n * n + 100 * (nT + nE))
-    bytes_pass2 = E * (cb * nE * nE + R * cb * (3 * nE + 2 * nT))
+    flops_pass1 = E * R * 8 * (nE * nE + nE * nT)
+    bytes_pass1 = E * cb * (nE * nE + nE * nT) + E * R * cb * (2 * nE + nT)
+    flops_pass2 = E * R * 8 * nE * nT
+    bytes_pass2 = E * cb * nE * nT + E * R * cb * (2 * nE + nT)
     nc = info.n_coarse
     flops_coarse = 8.0 * nc * nc * R
     bytes_coarse = 16.0 * nc * nc + 32.0 * nc * R
@@ -232,15 +232,15 @@ def run_ours(args):
     nE = (4 * (w.p[0] - info.l))
     nT = 4 + 4 * (info.l - 1)
     work = algorithmic_work(info, R, int(w.p[0]), nE, nT, True)
-    names = {0: "pass1 (local solve: S_E^-1 + FDM cross)", 2: "coarse solve (dense K^-1, FP64)",
-             3: "pass2 (local solve: FDM cross + S_E^-1)"}
+    names = {0: "pass1 (edge operators: [S_E^-1; Y^T] r_E)", 2: "coarse solve (dense K^-1 GEMV, FP64)",
+             3: "pass2 (edge operators: x_E - Y u_T)"}
     dom = max(work, key=lambda i: comp[i])
     fl, by = work[dom]
     fp64_peak = 1250.0         # GFLOP/s... expressed in TFLOP/s below
     achieved_tf = fl / (comp[dom] * 1e-3) / 1e12
-    # dram__bytes_read + dram__bytes_write of one k_gemv launch (dense K^-1, plane_16x16) from the
+    # dram__bytes_read + dram__bytes_write of one k_gemv1 launch (dense K^-1, plane_16x16) from the
     # ncu capture summarised in profiles/launches_plane16x16_fp64.md; unknown for other kernels
-    traffic = 59087360 + 512 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
+    traffic = 59086336 + 2816 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
     roof = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved_tf, 4),
             "peak": 1.25, "unit": "TFLOP/s", "frac": round(achieved_tf / 1.25, 4), "traffic": traffic,
             "algorithmic_bytes": int(by),
