@@ -71,6 +71,7 @@ struct ddh_ctx {
     bool edge_form = false;                        // Krylov-loop passes with Y (no FDM)
     double2* Kinv = nullptr;                       // dense coarse inverse (elimination order)
     float2* Kinv32 = nullptr;
+    int gemv_form = 1;                             // single-RHS GEMV kernel (timed at upload)
     // nested-dissection factor: complex128 matrices, their complex64 copy (nd32.G/M null
     // unless mixed precision with coarse_fp32), and per tree level the work items
     NDDev nd64, nd32;
@@ -416,6 +417,34 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         const float2* a32;
         if ((st = upload(ctx, conv32(Kn), &a32))) return st;
         ctx->Kinv32 = (float2*)a32;
+        // autotune: time the single-RHS GEMV forms on this K^-1 and keep the fastest
+        {
+            double2 *xs = nullptr, *ys = nullptr;
+            if (cudaMalloc(&xs, sizeof(double2) * nc) == cudaSuccess && cudaMalloc(&ys, sizeof(double2) * nc) == cudaSuccess) {
+                cudaMemsetAsync(xs, 0, sizeof(double2) * nc, ctx->stream);
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                float best = 1e30f;
+                for (int f = 0; f < 3; ++f) {
+                    launch_gemv(ctx->Kinv, false, nc, nc, xs, ys, nullptr, 0, nc, nc, 1, nullptr, ctx->stream, f);
+                    cudaEventRecord(e0, ctx->stream);
+                    for (int rep = 0; rep < 5; ++rep)
+                        launch_gemv(ctx->Kinv, false, nc, nc, xs, ys, nullptr, 0, nc, nc, 1, nullptr, ctx->stream, f);
+                    cudaEventRecord(e1, ctx->stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) { best = ms; ctx->gemv_form = f; }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            }
+            cudaStreamSynchronize(ctx->stream);
+            if (xs) cudaFree(xs);
+            if (ys) cudaFree(ys);
+            cudaGetLastError();
+        }
     } else {
         const int nn = (int)m.cnode.size();
         std::vector<int> f0(nn), nF(nn), nB(nn), bidx;
@@ -626,7 +655,7 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
     const bool f32 = ctx->coarse32;
     if (ctx->Kinv) {
         launch_gemv(f32 ? (const void*)ctx->Kinv32 : (const void*)ctx->Kinv, f32, nc, nc, t, x2, nullptr, 0, nc, nc, R,
-                    done, s);
+                    done, s, ctx->gemv_form);
         ctx->launches++;
         return;
     }

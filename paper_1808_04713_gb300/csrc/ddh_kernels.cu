@@ -449,6 +449,43 @@ __global__ void __launch_bounds__(256) k_gemv1(const M* __restrict__ A, int n_ou
     }
 }
 
+// y = A x for one right-hand side, two rows per warp: each x entry loaded feeds both rows
+// (8 FP64 FMAs per three 16-byte loads instead of four per two)
+template <class M>
+__global__ void __launch_bounds__(128) k_gemv2r(const M* __restrict__ A, int n_out, int n_in,
+                                                const double2* __restrict__ x, double2* __restrict__ y,
+                                                const double2* __restrict__ c, int mode, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int row = 2 * warp;
+    if (row >= n_out) return;
+    const bool two = row + 1 < n_out;
+    const M* a0 = A + (int64_t)row * n_in;
+    const M* a1 = two ? a0 + n_in : a0;
+    double s0x = 0, s0y = 0, s1x = 0, s1y = 0;
+    for (int j = lane; j < n_in; j += 32) {
+        const double2 xv = x[j];
+        const M u = a0[j], v = a1[j];
+        s0x = fma((double)u.x, xv.x, fma(-(double)u.y, xv.y, s0x));
+        s0y = fma((double)u.x, xv.y, fma((double)u.y, xv.x, s0y));
+        s1x = fma((double)v.x, xv.x, fma(-(double)v.y, xv.y, s1x));
+        s1y = fma((double)v.x, xv.y, fma((double)v.y, xv.x, s1y));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0x += __shfl_xor_sync(0xffffffffu, s0x, o);
+        s0y += __shfl_xor_sync(0xffffffffu, s0y, o);
+        s1x += __shfl_xor_sync(0xffffffffu, s1x, o);
+        s1y += __shfl_xor_sync(0xffffffffu, s1y, o);
+    }
+    if (lane < (two ? 2 : 1)) {
+        const int rr = row + lane;
+        const double vx = lane ? s1x : s0x, vy = lane ? s1y : s0y;
+        if (mode == 0) y[rr] = make_double2(vx, vy);
+        else if (mode == 1) { y[rr].x -= vx; y[rr].y -= vy; }
+        else { const double2 cv = c[rr]; y[rr] = make_double2(cv.x - vx, cv.y - vy); }
+    }
+}
+
 // ------------------------------------------------------------------ coarse solve
 // Nested-dissection solve of K x = t, one launch per tree level (see NDDev).  A CTA of 128
 // threads takes rows of one node's matrix for a block of RB right-hand sides after staging
@@ -1841,11 +1878,17 @@ void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const 
     k_dinv<<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, x, y, 1, done);
 }
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
-                 int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st) {
-    if (R == 1) {
+                 int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st, int form) {
+    if (R == 1 && form == 1) {
         const dim3 g1((n_out + 3) / 4);
         if (f32) k_gemv1<float2><<<g1, 256, 0, st>>>((const float2*)A, n_out, n_in, x, y, c, mode, done);
         else k_gemv1<double2><<<g1, 256, 0, st>>>((const double2*)A, n_out, n_in, x, y, c, mode, done);
+        return;
+    }
+    if (R == 1 && form == 2) {
+        const dim3 g2((n_out + 7) / 8);
+        if (f32) k_gemv2r<float2><<<g2, 128, 0, st>>>((const float2*)A, n_out, n_in, x, y, c, mode, done);
+        else k_gemv2r<double2><<<g2, 128, 0, st>>>((const double2*)A, n_out, n_in, x, y, c, mode, done);
         return;
     }
     const int warps_per_block = 4;

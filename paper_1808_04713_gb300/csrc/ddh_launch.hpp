@@ -82,8 +82,11 @@ void nd_set_smem_limits();   // once per device before the first (captured) laun
 void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
                          const double2* t, double2* r, int R, const int* done, cudaStream_t st);
 void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st);
+// y = A x (mode 0), y -= A x (1), y = c - A x (2).  For one right-hand side `form` picks the
+// kernel: 0 one warp per row, 1 two warps per row, 2 two rows per warp (chosen by timing at
+// factor time)
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
-                 int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st);
+                 int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st, int form = 1);
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
                           int nq, double2* bt, int R, cudaStream_t st, int dk = 0);
 void launch_grad_elem(const DevModel& dm, const double2* ut, const double2* lt, int R, double k, int mode, double* out,
