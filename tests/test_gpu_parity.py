@@ -195,3 +195,17 @@ def test_local_forms_agree(name, prec):
     assert max(pe) <= 1e-11
     ref = dd.Conforming(dd.problem_from_workload(w)).solve_direct()
     assert np.linalg.norm(ue - ref) / np.linalg.norm(ref) <= (1e-10 if prec == ddh.PREC_FP64 else 1e-8)
+
+
+@pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
+def test_repeated_solves_are_bit_identical(prec):
+    """No floating-point atomics on the solve path: the same solve twice gives the same bits
+    (the mixed form's FP32 inner solves would otherwise amplify reduction-order noise)."""
+    w = SMALL["hanging_corner"]()
+    s = _solver(w, tol=1e-10, precision=prec)
+    b = s.rhs_planewave(w.thetas)
+    u1, st1 = s.solve(b, tol=1e-10)
+    u2, st2 = s.solve(b, tol=1e-10)
+    assert torch.equal(u1, u2)
+    assert [x.iterations for x in st1] == [x.iterations for x in st2]
+    s.close()
