@@ -77,6 +77,10 @@ struct ddh_ctx {
     NDDev nd64, nd32;
     const int4* nd_items = nullptr;
     void* nd_u = nullptr;                          // forward updates [R][u_len] (work buffer)
+    int nd_cut = 1 << 30;                          // levels >= nd_cut run as per-CTA subtrees
+    int nd_nsub = 0, nd_sub_fwd_rows = 0, nd_sub_bwd_rows = 0;
+    const int* nd_sub_ptr = nullptr;
+    const int* nd_sub_nodes = nullptr;
     std::vector<int> nd_fwd_off, nd_fwd_n, nd_fwd_rows;   // per level: first item, items, staged rows
     std::vector<int> nd_bwd_off, nd_bwd_n, nd_bwd_rows;
     bool coarse32 = false;                         // current inner solves use the complex64 copy
@@ -149,6 +153,9 @@ static void free_model(ddh_ctx* ctx) {
     ctx->nd32 = NDDev();
     ctx->nd_items = nullptr;
     ctx->nd_u = nullptr;
+    ctx->nd_cut = 1 << 30;
+    ctx->nd_nsub = ctx->nd_sub_fwd_rows = ctx->nd_sub_bwd_rows = 0;
+    ctx->nd_sub_ptr = ctx->nd_sub_nodes = nullptr;
     ctx->nd_fwd_off.clear(); ctx->nd_fwd_n.clear(); ctx->nd_fwd_rows.clear();
     ctx->nd_bwd_off.clear(); ctx->nd_bwd_n.clear(); ctx->nd_bwd_rows.clear();
     ctx->kc_ptr = ctx->kc_col = nullptr;
@@ -531,6 +538,44 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         }
         for (int lv = 0; lv < L; ++lv)
             if (ctx->nd_bwd_rows[lv] > 12800) return fail(ctx, DDH_ERR_INVALID_ARG, "coarse front too large for shared memory");
+        // subtrees: the first level with at least 300 nodes and everything below it run as one
+        // launch per direction, a CTA per subtree (fewer, longer-lived CTAs for the many small fronts)
+        {
+            std::vector<int> count(L, 0);
+            for (const auto& N : m.cnode) count[N.depth]++;
+            int cut = L;
+            for (int lv = 1; lv < L; ++lv)
+                if (count[lv] >= 300) { cut = lv; break; }
+            ctx->nd_cut = cut;
+            ctx->nd_nsub = 0;
+            if (cut < L) {
+                std::vector<std::vector<int>> kids(nn);
+                for (int id = 0; id < nn; ++id)
+                    if (m.cnode[id].parent >= 0) kids[m.cnode[id].parent].push_back(id);
+                std::vector<int> sp(1, 0), sn;
+                for (int id = 0; id < nn; ++id) {
+                    if (m.cnode[id].depth != cut) continue;
+                    // postorder of the subtree below id (node ids are already postorder)
+                    std::vector<int> st{id}, sub;
+                    while (!st.empty()) {
+                        const int v = st.back();
+                        st.pop_back();
+                        sub.push_back(v);
+                        for (int c : kids[v]) st.push_back(c);
+                    }
+                    std::sort(sub.begin(), sub.end());
+                    sn.insert(sn.end(), sub.begin(), sub.end());
+                    sp.push_back((int)sn.size());
+                }
+                ctx->nd_nsub = (int)sp.size() - 1;
+                for (int lv = cut; lv < L; ++lv) {
+                    ctx->nd_sub_fwd_rows = std::max(ctx->nd_sub_fwd_rows, ctx->nd_fwd_rows[lv]);
+                    ctx->nd_sub_bwd_rows = std::max(ctx->nd_sub_bwd_rows, ctx->nd_bwd_rows[lv]);
+                }
+                if ((st = upload(ctx, sp, &ctx->nd_sub_ptr))) return st;
+                if ((st = upload(ctx, sn, &ctx->nd_sub_nodes))) return st;
+            }
+        }
         NDDev& D = ctx->nd64;
         D.nc = nc;
         D.u_len = std::max<int64_t>(1, ul);
@@ -665,16 +710,30 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
     double2* y = tmp;
     double2* u = (double2*)ctx->nd_u;
     const int L = (int)ctx->nd_fwd_rows.size();
-    for (int lv = L - 1; lv >= 0; --lv) {
+    // subtree launches pay off when the launches are latency-bound (few right-hand sides); with
+    // more right-hand sides the serial node chain inside a subtree costs more than it saves
+    const bool subs = ctx->nd_nsub > 0 && R < 4;
+    const int cut = subs ? std::min(L, ctx->nd_cut) : L;
+    if (subs) {
+        launch_nd_subtrees(true, D, f32nd, ctx->nd_sub_ptr, ctx->nd_sub_nodes, ctx->nd_nsub, ctx->nd_sub_fwd_rows, t, y,
+                           u, R, done, s);
+        ctx->launches++;
+    }
+    for (int lv = cut - 1; lv >= 0; --lv) {
         if (!ctx->nd_fwd_n[lv]) continue;
         launch_nd_forward(D, f32nd, ctx->nd_items + ctx->nd_fwd_off[lv], ctx->nd_fwd_n[lv], ctx->nd_fwd_rows[lv], t, y, u,
                           R, done, s);
         ctx->launches++;
     }
-    for (int lv = 0; lv < L; ++lv) {
+    for (int lv = 0; lv < cut; ++lv) {
         if (!ctx->nd_bwd_n[lv]) continue;
         launch_nd_backward(D, f32nd, ctx->nd_items + ctx->nd_bwd_off[lv], ctx->nd_bwd_n[lv], ctx->nd_bwd_rows[lv], y, x2,
                            R, done, s);
+        ctx->launches++;
+    }
+    if (subs) {
+        launch_nd_subtrees(false, D, f32nd, ctx->nd_sub_ptr, ctx->nd_sub_nodes, ctx->nd_nsub, ctx->nd_sub_bwd_rows, y, x2,
+                           nullptr, R, done, s);
         ctx->launches++;
     }
 }

@@ -514,18 +514,15 @@ __device__ __forceinline__ void cfma(T& ax, T& ay, cpx<T> a, cpx<T> v) {
     ay = fma(a.x, v.y, fma(a.y, v.x, ay));
 }
 
-// forward level: y_F = t_F - w_F, u_N = w_B + G_N y_F (w = the children's amounts)
+// One node's share of a forward level: stage y_F = t_F - w_F (w = the children's amounts),
+// write y_F when asked, then u_N[row] = w_B[row] + (G_N y_F)[row] for rows [row0, row0+nrows).
+// Called by every thread of the CTA; ends without a trailing barrier.
 template <class MT, int RB>
-__global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
-                                                    const double2* __restrict__ t, double2* __restrict__ y,
-                                                    double2* __restrict__ u, int R, const int* __restrict__ done) {
+__device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int row0, int nrows, bool shortm,
+                                                bool write_y, const double2* __restrict__ t, double2* __restrict__ y,
+                                                double2* __restrict__ u, int r0, int nr,
+                                                cpx<typename NDType<MT>::T>* nd_sm) {
     using T = typename NDType<MT>::T;
-    if (done && *done) return;
-    extern __shared__ __align__(16) char nd_raw[];
-    cpx<T>* nd_sm = reinterpret_cast<cpx<T>*>(nd_raw);    // [RB][sF]
-    const int4 it = items[blockIdx.x];
-    const int node = it.x, row0 = it.y, nrows = it.z;
-    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
     const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], sF = nF | 1;
     const int64_t nc = d.nc, ul = d.u_len, so = d.s_off[node], uo = d.u_off[node];
     for (int i = threadIdx.x; i < nF; i += blockDim.x) {
@@ -536,7 +533,7 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
                 const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + i);
                 v = t[(r0 + r) * nc + pos];
                 v.x -= w.x; v.y -= w.y;
-                if (row0 == 0) y[(r0 + r) * nc + pos] = v;
+                if (write_y) y[(r0 + r) * nc + pos] = v;
             }
             nd_sm[r * sF + i] = mk<T>((T)v.x, (T)v.y);
         }
@@ -544,7 +541,7 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
     __syncthreads();
     const MT* G = (const MT*)d.G + d.g_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (it.w) {
+    if (shortm) {
         // lane = (row of 4, column slice of S, right-hand side of RB), S * RB = 8
         constexpr int S = 8 / RB;
         const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
@@ -594,18 +591,12 @@ __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restr
     }
 }
 
-// backward level: x_F = W y_F - H x_B = [W | -H] [y_F; x_B]
+// One node's share of a backward level: x_F[rows] = ([W | -H] [y_F; x_B])[rows]
 template <class MT, int RB>
-__global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __restrict__ items,
-                                                     const double2* __restrict__ y, double2* __restrict__ x, int R,
-                                                     const int* __restrict__ done) {
+__device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int row0, int nrows, bool shortm,
+                                                 const double2* __restrict__ y, double2* __restrict__ x, int r0,
+                                                 int nr, cpx<typename NDType<MT>::T>* nd_sm) {
     using T = typename NDType<MT>::T;
-    if (done && *done) return;
-    extern __shared__ __align__(16) char nd_raw[];
-    cpx<T>* nd_sm = reinterpret_cast<cpx<T>*>(nd_raw);    // [RB][sn]
-    const int4 it = items[blockIdx.x];
-    const int node = it.x, row0 = it.y, nrows = it.z;
-    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
     const int f0 = d.f0[node], nF = d.nF[node], nB = d.nB[node], n = nF + nB, sn = n | 1;
     const int64_t nc = d.nc;
     const int* bi = d.bidx + d.b_off[node];
@@ -620,8 +611,7 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
     __syncthreads();
     const MT* M = (const MT*)d.M + d.m_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (it.w) {
-        // lane = (row of 4, column slice of S, right-hand side of RB), S * RB = 8
+    if (shortm) {
         constexpr int S = 8 / RB;
         const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
         for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
@@ -662,6 +652,70 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
                 if (r == lane) { sx = ax[r]; sy = ay[r]; }
             x[(r0 + lane) * nc + f0 + row] = make_double2((double)sx, (double)sy);
         }
+    }
+}
+
+// forward level: one item per CTA
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
+                                                    const double2* __restrict__ t, double2* __restrict__ y,
+                                                    double2* __restrict__ u, int R, const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
+    if (done && *done) return;
+    extern __shared__ __align__(16) char nd_raw[];
+    const int4 it = items[blockIdx.x];
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    nd_forward_node<MT, RB>(d, it.x, it.y, it.z, it.w != 0, it.y == 0, t, y, u, r0, nr,
+                            reinterpret_cast<cpx<T>*>(nd_raw));
+}
+
+// backward level: one item per CTA
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __restrict__ items,
+                                                     const double2* __restrict__ y, double2* __restrict__ x, int R,
+                                                     const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
+    if (done && *done) return;
+    extern __shared__ __align__(16) char nd_raw[];
+    const int4 it = items[blockIdx.x];
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    nd_backward_node<MT, RB>(d, it.x, it.y, it.z, it.w != 0, y, x, r0, nr, reinterpret_cast<cpx<T>*>(nd_raw));
+}
+
+// The bottom of the tree in one launch per direction: CTA b owns the subtree below node
+// sub_root[b] and walks its nodes (postorder list sub_nodes[sub_ptr[b] .. sub_ptr[b+1]))
+// children first (forward) or parents first (backward), one barrier between nodes.
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_forward_sub(NDDev d, const int* __restrict__ sub_ptr,
+                                                        const int* __restrict__ sub_nodes,
+                                                        const double2* __restrict__ t, double2* __restrict__ y,
+                                                        double2* __restrict__ u, int R, const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
+    if (done && *done) return;
+    extern __shared__ __align__(16) char nd_raw[];
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    for (int k = sub_ptr[blockIdx.x]; k < sub_ptr[blockIdx.x + 1]; ++k) {
+        const int node = sub_nodes[k];
+        nd_forward_node<MT, RB>(d, node, 0, d.nB[node], d.nF[node] <= kNDShortRow, true, t, y, u, r0, nr,
+                                reinterpret_cast<cpx<T>*>(nd_raw));
+        __syncthreads();
+    }
+}
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_backward_sub(NDDev d, const int* __restrict__ sub_ptr,
+                                                         const int* __restrict__ sub_nodes,
+                                                         const double2* __restrict__ y, double2* __restrict__ x, int R,
+                                                         const int* __restrict__ done) {
+    using T = typename NDType<MT>::T;
+    if (done && *done) return;
+    extern __shared__ __align__(16) char nd_raw[];
+    const int r0 = blockIdx.y * RB, nr = min(RB, R - r0);
+    for (int k = sub_ptr[blockIdx.x + 1] - 1; k >= sub_ptr[blockIdx.x]; --k) {
+        const int node = sub_nodes[k];
+        if (d.nF[node] > 0)
+            nd_backward_node<MT, RB>(d, node, 0, d.nF[node], d.nF[node] + d.nB[node] <= kNDShortRow, y, x, r0, nr,
+                                     reinterpret_cast<cpx<T>*>(nd_raw));
+        __syncthreads();
     }
 }
 
@@ -1823,6 +1877,8 @@ template <class MT, int RB>
 static void nd_attr() {
     cudaFuncSetAttribute(k_nd_forward<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
     cudaFuncSetAttribute(k_nd_backward<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
+    cudaFuncSetAttribute(k_nd_forward_sub<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
+    cudaFuncSetAttribute(k_nd_backward_sub<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
 }
 void nd_set_smem_limits() {
     nd_attr<double2, 1>(); nd_attr<double2, 2>(); nd_attr<double2, 4>(); nd_attr<double2, 8>();
@@ -1869,6 +1925,30 @@ void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems,
         default: ND_B(1)
     }
 #undef ND_B
+}
+template <class MT, int RB>
+static void nd_sub_t(bool fwd, const NDDev& d, const int* sp, const int* sn, int nsub, int smem_rows,
+                     const double2* a, double2* b, double2* u, int R, const int* done, cudaStream_t st) {
+    const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(MT));
+    const dim3 g(nsub, (R + RB - 1) / RB);
+    if (fwd) k_nd_forward_sub<MT, RB><<<g, 128, sm, st>>>(d, sp, sn, a, b, u, R, done);
+    else k_nd_backward_sub<MT, RB><<<g, 128, sm, st>>>(d, sp, sn, a, b, R, done);
+}
+void launch_nd_subtrees(bool forward, const NDDev& d, bool f32, const int* sub_ptr, const int* sub_nodes, int nsub,
+                        int smem_rows, const double2* in, double2* out, double2* u, int R, const int* done,
+                        cudaStream_t st) {
+    if (nsub <= 0) return;
+    const int rb = nd_rhs_block(smem_rows, R);
+#define ND_S(RBV)                                                                                                  \
+    if (f32) nd_sub_t<float2, RBV>(forward, d, sub_ptr, sub_nodes, nsub, smem_rows, in, out, u, R, done, st);      \
+    else nd_sub_t<double2, RBV>(forward, d, sub_ptr, sub_nodes, nsub, smem_rows, in, out, u, R, done, st);
+    switch (rb) {
+        case 8: ND_S(8) break;
+        case 4: ND_S(4) break;
+        case 2: ND_S(2) break;
+        default: ND_S(1)
+    }
+#undef ND_S
 }
 void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
                          const double2* t, double2* r, int R, const int* done, cudaStream_t st) {

@@ -77,6 +77,12 @@ void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, 
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
                         double2* x, int R, const int* done, cudaStream_t st);
 int nd_rhs_block(int smem_rows, int R);
+// the levels below a cut in one launch: CTA b walks the subtree nodes
+// sub_nodes[sub_ptr[b] .. sub_ptr[b+1]) (postorder), forward (in = t, out = y, u) or backward
+// (in = y, out = x)
+void launch_nd_subtrees(bool forward, const NDDev& d, bool f32, const int* sub_ptr, const int* sub_nodes, int nsub,
+                        int smem_rows, const double2* in, double2* out, double2* u, int R, const int* done,
+                        cudaStream_t st);
 void nd_set_smem_limits();   // once per device before the first (captured) launch
 // r = t - K x, K in CSR (R right-hand sides, [R][n])
 void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
