@@ -39,6 +39,22 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value: float, device: str) -> float:
+    """The largest of `value` over the ranks of the process group (the job's time is its
+    slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, steps: int, rhs: int, slowest_total_s: float) -> float:
+    """Whole-job solves/s of N independent replicas: every rank solves `steps` batches of
+    `rhs` right-hand sides; the job takes as long as its slowest rank."""
+    return world * steps * rhs / slowest_total_s
+
+
 def _oracle_timing(name: str, n: int, budget: float, threads: int = 1) -> dict:
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
                MKL_NUM_THREADS=str(threads), CUDA_VISIBLE_DEVICES="")
@@ -204,10 +220,8 @@ def run_ours(args):
     launches = s.kernel_launches() - launches0
     total = sum(times)
     if ws > 1:
-        t = torch.tensor([total], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = ws * args.steps * R / total
+        total = _max_over_ranks(total, f"cuda:{local}")
+    value = aggregate_rate(ws, args.steps, R, total)
     # end-to-end through the public API with pinned host buffers
     bh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
     uh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
@@ -220,10 +234,8 @@ def run_ours(args):
         assert st_ == 0, s.lib.ddh_last_error(s.h)
     e2e_total = sum(e2e_t)
     if ws > 1:
-        t = torch.tensor([e2e_total], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * len(e2e_t) * R / e2e_total
+        e2e_total = _max_over_ranks(e2e_total, f"cuda:{local}")
+    e2e_value = aggregate_rate(ws, len(e2e_t), R, e2e_total)
     # correctness of the timed result
     pr = s.primal_residual(b, u)
     # live per-component timing of the operator (CUDA events on the library stream)
