@@ -64,20 +64,23 @@ def _oracle_timing(name: str, n: int, budget: float, threads: int = 1) -> dict:
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples of SM clock and throttle reasons (every 10 ms).  Started before the
+    warm-up so that it is running when the timed region begins; `mark(t0, t1)` keeps the
+    samples taken inside the timed region (wall clock), else the one nearest to it."""
 
     def __init__(self, index: int):
         self.index = index
         self.rows = []
         self.proc = None
+        self.window = None
 
     def __enter__(self):
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -86,8 +89,17 @@ class ClockSampler:
         return self
 
     def _read(self):
+        import datetime
         for line in self.proc.stdout:
-            self.rows.append([c.strip() for c in line.split(",")])
+            cols = [c.strip() for c in line.split(",")]
+            try:
+                t = datetime.datetime.strptime(cols[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except (ValueError, IndexError):
+                t = time.time()
+            self.rows.append((t, cols[1:]))
+
+    def mark(self, t0: float, t1: float):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc:
@@ -98,9 +110,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self) -> dict:
+        rows = self.rows
+        inside = rows
+        if self.window and rows:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 - 0.01 <= r[0] <= t1 + 0.01]
+            if not inside:
+                mid = 0.5 * (t0 + t1)
+                inside = [min(rows, key=lambda r: abs(r[0] - mid))]
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for _, r in inside:
             try:
                 sm.append(float(r[0]))
                 mx = float(r[1])
@@ -195,6 +215,7 @@ def run_ours(args):
         b = s.rhs_planewave(w.thetas)
         u = torch.empty_like(b)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    clk = ClockSampler(local).__enter__()        # running before the timed region starts
     for _ in range(args.warmup):
         _, st = s.solve(b, tol=1e-10, out=u)
     torch.cuda.synchronize()
@@ -203,20 +224,22 @@ def run_ours(args):
     times = []
     launches0 = s.kernel_launches()
     iters = []
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()                  # evict L2 (256 MB > 129 MB) between steps
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            _, st = s.solve(b, tol=1e-10, out=u)
-            with torch.cuda.stream(stream):
-                e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / 1e3)
-            iters.append(st[0].iterations)
+    t_start = time.time()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()                  # evict L2 (256 MB > 129 MB) between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        _, st = s.solve(b, tol=1e-10, out=u)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(st[0].iterations)
     torch.cuda.synchronize()
+    clk.mark(t_start, time.time())
+    clk.__exit__(None, None, None)
     launches = s.kernel_launches() - launches0
     total = sum(times)
     if ws > 1:
@@ -250,9 +273,10 @@ def run_ours(args):
     fl, by = work[dom]
     fp64_peak = 1250.0         # GFLOP/s... expressed in TFLOP/s below
     achieved_tf = fl / (comp[dom] * 1e-3) / 1e12
-    # dram__bytes_read + dram__bytes_write of one k_gemv1 launch (dense K^-1, plane_16x16) from the
-    # ncu capture summarised in profiles/launches_plane16x16_fp64.md; unknown for other kernels
-    traffic = 59086336 + 2816 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
+    # dram__bytes_read + dram__bytes_write of one dense-K^-1 GEMV launch (plane_16x16; k_gemv, and
+    # k_gemv1 reads the same 59.09 MB) from the ncu captures summarised in
+    # profiles/launches_plane16x16_fp64.md; unknown for other kernels
+    traffic = 59092224 + 2816 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
     roof = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved_tf, 4),
             "peak": 1.25, "unit": "TFLOP/s", "frac": round(achieved_tf / 1.25, 4), "traffic": traffic,
             "algorithmic_bytes": int(by),
