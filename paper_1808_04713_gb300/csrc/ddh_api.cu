@@ -747,12 +747,12 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
     const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
     if (ctx->edge_form && !(bt && has_bI)) launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s);
-    else launch_pass1<T>(d, sinv, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
+    else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
     coarse_solve(ctx, w.t, w.x2, w.ctmp, R, done);
     if (ctx->edge_form && !phi_out) launch_pass2_edge<T>(d, Y, w.x2, w.xE, w.xE2, R, done, s);
-    else launch_pass2<T>(d, sinv, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
+    else launch_pass2<T>(d, sinv, ctx->edge_form ? Y : nullptr, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
     ctx->launches++;
     if (kdots) {
         launch_jump_gather_dots<T>(d, w.xE2, w.x2, *kdots, s);
@@ -1570,24 +1570,24 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
     if (fp64) {
         ms_out[0] = timeit([&] {
             if (ef) launch_pass1_edge<double>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
-            else launch_pass1<double>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
+            else launch_pass1<double>(d, sinv, nullptr, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
         });
         ms_out[1] = timeit([&] { launch_coarse_assemble<double>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
         ms_out[3] = timeit([&] {
             if (ef) launch_pass2_edge<double>(d, Y, w.x2, w.xE, w.xE2, R, nullptr, s);
-            else launch_pass2<double>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
+            else launch_pass2<double>(d, sinv, nullptr, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
         });
         ms_out[4] = timeit([&] { launch_jump_gather<double>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
         ms_out[5] = timeit([&] { launch_pre<double>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
     } else {
         ms_out[0] = timeit([&] {
             if (ef) launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
-            else launch_pass1<float>(d, sinv, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
+            else launch_pass1<float>(d, sinv, nullptr, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
         });
         ms_out[1] = timeit([&] { launch_coarse_assemble<float>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
         ms_out[3] = timeit([&] {
             if (ef) launch_pass2_edge<float>(d, Y, w.x2, w.xE, w.xE2, R, nullptr, s);
-            else launch_pass2<float>(d, sinv, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
+            else launch_pass2<float>(d, sinv, nullptr, w.x2, w.xE, w.xE2, 0, nullptr, 0, nullptr, R, nullptr, s);
         });
         ms_out[4] = timeit([&] { launch_jump_gather<float>(d, w.xE2, w.x2, K.w, R, nullptr, s); });
         ms_out[5] = timeit([&] { launch_pre<float>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });

@@ -90,6 +90,7 @@ __device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, con
 // One CTA per (element, block of RB right-hand sides).
 template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __restrict__ sinv,
+                                               const cpx<T>* __restrict__ Y,
                                                const double2* __restrict__ z, double zsign,
                                                const double2* __restrict__ bt, int has_bI, int R,
                                                cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
     const int stride = 4 * N;
     cpx<T>* rE = s.vec;                     // [RB][4N]
     cpx<T>* xE = s.vec + RB * stride;       // [RB][4N]
+    cpx<T>* cT = s.vec + 2 * RB * stride;   // [RB][4N]: A_TI A_II^-1 b_I (with Y)
     load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const int64_t off = dm.off[e];
@@ -138,6 +140,11 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
                 const int slot = dm.e1_slot[e1o + i];
                 rE[q * stride + i] -= apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
             }
+            if (Y)
+                for (int i = g.t(); i < nT; i += g.n()) {
+                    const int slot = dm.t_slot[to + i];
+                    cT[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+                }
             g.sync();
         }
     }
@@ -149,6 +156,18 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
         const int q = idx / nE, i = idx % nE;
         xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + i] = xE[q * stride + i];
+    }
+    if (Y) {
+        // t_T = A_TE x_E + A_TI y_I = Y^T r'_E + A_TI A_II^-1 b_I, with r'_E = r_E - A_EI A_II^-1 b_I
+        const cpx<T>* Ye = Y + dm.pq_off[e];
+        const bool withI = bt && has_bI;
+        for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
+            const int q = idx / nT, t = idx % nT;
+            cpx<T> a = withI ? cT[q * stride + t] : mk<T>(0, 0);
+            for (int i = 0; i < nE; ++i) fma_c(a, Ye[(int64_t)i * nT + t], rE[q * stride + i]);
+            tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + t] = a;
+        }
+        return;
     }
     for (int q = 0; q < cnt; ++q) {
         const int r = r0 + q;
@@ -768,6 +787,7 @@ __global__ void k_csr_residual(const int* __restrict__ ptr, const int* __restric
 // A_IE x1_E - A_IT u_T), into phi_out.  One CTA per (element, block of RB RHS).
 template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __restrict__ sinv,
+                                               const cpx<T>* __restrict__ Y,
                                                const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
                                                cpx<T>* __restrict__ xE_out, int recover,
                                                const double2* __restrict__ bt, int has_bI, int R,
@@ -809,6 +829,20 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
         uT[q * stride + i] = u;
     }
     g.sync();
+    if (Y) {
+        // x1_E = x_E - Y u_T (the edge part of A11^-1 A12 x2, formed at factor time)
+        const cpx<T>* Ye = Y + dm.pq_off[e];
+        if (stage_off > 0 && nE > 0 && !bulk_wait_all(bar, dm.err)) return;   // the unused copy still lands
+        for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+            const int q = idx / nE, i = idx % nE;
+            cpx<T> a = mk<T>(0, 0);
+            for (int t = 0; t < nT; ++t) fma_c(a, Ye[(int64_t)i * nT + t], uT[q * stride + t]);
+            const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
+            const cpx<T> v = xE_in[gi] - a;
+            sE[q * stride + i] = v;
+            if (xE_out) xE_out[gi] = v;
+        }
+    } else {
     for (int q = 0; q < cnt; ++q) {
         for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
         g.sync();
@@ -837,6 +871,7 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
         const cpx<T> v = xE_in[gi] - sE[q * stride + i];
         sE[q * stride + i] = v;
         if (xE_out) xE_out[gi] = v;
+    }
     }
     g.sync();
     if (!recover) return;
@@ -1741,7 +1776,7 @@ static size_t pass_smem_total(int pmax, int rb, int maxE1) {
 // warps (elements) per CTA: up to 4 while the per-warp shared memory fits in 200 KB
 
 template <class T>
-void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
+void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
     const int rb = rhs_block(R);
     const int so = pass_stage_off<T>(dm.pmax, rb, dm.maxE1);
@@ -1750,10 +1785,10 @@ void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double
     const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     switch (rb) {
-        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
+        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
     }
 }
 // shared memory of the edge-operator pass 1: r_E and x_E blocks, then (when it fits) the
@@ -1816,10 +1851,10 @@ void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* b
     k_coarse_assemble<T><<<dim3((dm.n_coarse + 127) / 128, R), 128, 0, st>>>(dm, (const cpx<T>*)tT, bt, z, zsign, t, R, done);
 }
 template <class T>
-void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const void* xE_in, void* xE_out,
+void launch_pass2(const DevModel& dm, const void* sinv, const void* Y, const double2* x2, const void* xE_in, void* xE_out,
                   int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st) {
     const int rb = rhs_block(R);
-    const int so = pass_stage_off<T>(dm.pmax, rb, dm.maxE1);
+    const int so = Y ? 0 : pass_stage_off<T>(dm.pmax, rb, dm.maxE1);     // with Y, S_E^-1 is not read
     const int ntask = dm.E * ((R + rb - 1) / rb);
     const dim3 g(ntask);
     const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
@@ -1827,10 +1862,10 @@ void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const
     const cpx<T>* xi = (const cpx<T>*)xE_in;
     cpx<T>* xo = (cpx<T>*)xE_out;
     switch (rb) {
-        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
+        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
     }
 }
 template <class T>
@@ -1856,12 +1891,12 @@ void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, d
     k_dinv<<<gr, 128, 0, st>>>(dm, m, z, lumped, done);
 }
 
-template void launch_pass1<double>(const DevModel&, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t);
-template void launch_pass1<float>(const DevModel&, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t);
 template void launch_coarse_assemble<double>(const DevModel&, const void*, const double2*, const double2*, double, double2*, int, const int*, cudaStream_t);
 template void launch_coarse_assemble<float>(const DevModel&, const void*, const double2*, const double2*, double, double2*, int, const int*, cudaStream_t);
-template void launch_pass2<double>(const DevModel&, const void*, const double2*, const void*, void*, int, const double2*, int, double2*, int, const int*, cudaStream_t);
-template void launch_pass2<float>(const DevModel&, const void*, const double2*, const void*, void*, int, const double2*, int, double2*, int, const int*, cudaStream_t);
+template void launch_pass2<double>(const DevModel&, const void*, const void*, const double2*, const void*, void*, int, const double2*, int, double2*, int, const int*, cudaStream_t);
+template void launch_pass2<float>(const DevModel&, const void*, const void*, const double2*, const void*, void*, int, const double2*, int, double2*, int, const int*, cudaStream_t);
 template void launch_jump_gather<double>(const DevModel&, const void*, const double2*, double2*, int, const int*, cudaStream_t);
 template void launch_jump_gather<float>(const DevModel&, const void*, const double2*, double2*, int, const int*, cudaStream_t);
 template void launch_pre<double>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);

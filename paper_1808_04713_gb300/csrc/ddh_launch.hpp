@@ -18,8 +18,10 @@ struct KrylovDev {
     int nd, m, R, nchunk, chunk; double tol;
 };
 
+// FDM-form passes; Y (edge operators, or null) replaces the cross pipelines that only feed
+// type-1 edge and type-2 values, leaving one full FDM per RHS for the interior terms
 template <class T>
-void launch_pass1(const DevModel& dm, const void* sinv, const double2* z, double zsign, const double2* bt,
+void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st);
 // Krylov-loop passes with the explicit edge operators Y = [A11^-1 A_1T]_E (no FDM; pass 1
 // requires a load without interior components, pass 2 no recovery)
@@ -35,7 +37,7 @@ template <class T>
 void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
                             double2* t, int R, const int* done, cudaStream_t st);
 template <class T>
-void launch_pass2(const DevModel& dm, const void* sinv, const double2* x2, const void* xE_in, void* xE_out,
+void launch_pass2(const DevModel& dm, const void* sinv, const void* Y, const double2* x2, const void* xE_in, void* xE_out,
                   int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st);
 template <class T>
 void launch_jump_gather(const DevModel& dm, const void* xE, const double2* x2, double2* w, int R, const int* done,
