@@ -804,7 +804,7 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     K.nd = nd; K.m = m; K.R = R;
     // rows per CTA in the orthogonalisation kernels: 128 for short vectors, else at most ~512
     // chunks per right-hand side (the last CTA of each right-hand side sums the chunk partials)
-    K.chunk = nd <= 16384 ? 128 : std::min(4096, std::max(256, ((nd + 511) / 512 + 255) / 256 * 256));
+    K.chunk = nd <= 16384 ? kCgsShortRows : std::min(4096, std::max(256, ((nd + 511) / 512 + 255) / 256 * 256));
     K.nchunk = (nd + K.chunk - 1) / K.chunk;
     auto al = [&](size_t bytes, void** p) -> bool {
         if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) return false;
@@ -852,7 +852,7 @@ struct KrylovOps {
     std::function<ddh_status(const double2*, double2*, const int*)> prec;
     // optional: fetch V[j] + precondition + store Zb[j] in one go (replaces fetch/prec/store)
     std::function<void(const KrylovDev&)> prec_krylov;
-    // optional: w = op(in) into K.w together with the first CGS pass (used when K.chunk == 128)
+    // optional: w = op(in) into K.w together with the first CGS pass (short vectors only)
     std::function<void(const double2*, const KrylovDev&)> op_dots;
     bool graph = false;     // the body may be captured as a CUDA graph
     int key = 0;            // graph cache key (precision of the element kernels)
@@ -870,7 +870,7 @@ static ddh_status iteration_body(ddh_ctx* ctx, KState& ks, const KrylovOps& ops)
         if (st) return st;
         launch_store(K, ctx->stream);
     }
-    const bool fused = ops.op_dots && K.chunk == 128;
+    const bool fused = ops.op_dots && K.chunk == kCgsShortRows;
     if (fused) ops.op_dots(K.zw, K);
     else ops.op(K.zw, K.w, done);
     launch_krylov_iter_tail(K, ctx->stream, fused);

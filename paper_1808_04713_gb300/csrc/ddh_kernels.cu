@@ -1455,32 +1455,31 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return t;
 }
 
-// true in every thread of the CTA that finishes last among the nchunk CTAs of right-hand side r
-__device__ __forceinline__ bool cgs_last_chunk(const KrylovDev& K, int r, int* flag) {
-    __threadfence();
+// true in every thread of the CTA that finishes last among the nchunk CTAs of right-hand side r.
+// The barrier orders the CTA's partial writes before thread 0's GPU-scope fence (fences are
+// cumulative), which precedes its counter increment; the winner fences again before the
+// barrier that releases its other threads to read the partials of every CTA.  One fence per
+// CTA, not per thread.
+__device__ __forceinline__ bool cgs_last_of(int* counter, int n, int* flag) {
     __syncthreads();
-    if (threadIdx.x == 0) *flag = (atomicAdd(K.cnt + r, 1) == K.nchunk - 1);
-    __syncthreads();
-    const bool last = *flag;
-    if (last) {
+    if (threadIdx.x == 0) {
         __threadfence();
-        if (threadIdx.x == 0) K.cnt[r] = 0;
+        const bool last = atomicAdd(counter, 1) == n - 1;
+        if (last) {
+            __threadfence();
+            *counter = 0;
+        }
+        *flag = last;
     }
-    return last;
+    __syncthreads();
+    return *flag;
 }
-
+__device__ __forceinline__ bool cgs_last_chunk(const KrylovDev& K, int r, int* flag) {
+    return cgs_last_of(K.cnt + r, K.nchunk, flag);
+}
 // true in every thread of the CTA that finishes last among the R per-right-hand-side winners
 __device__ __forceinline__ bool cgs_last_chunk_all(const KrylovDev& K, int* flag) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) *flag = (atomicAdd(K.cnt + K.R, 1) == K.R - 1);
-    __syncthreads();
-    const bool last = *flag;
-    if (last) {
-        __threadfence();
-        if (threadIdx.x == 0) K.cnt[K.R] = 0;
-    }
-    return last;
+    return cgs_last_of(K.cnt + K.R, K.R, flag);
 }
 
 // out[i] = sum over chunks of partial[r][c][i], i <= j (and slot m when with_m), one warp per i
@@ -1542,14 +1541,6 @@ __global__ void __launch_bounds__(128) k_jump_gather_dots(DevModel dm, const cpx
     cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
     if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
 }
-template <class T>
-void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
-                             cudaStream_t st) {
-    k_jump_gather_dots<T><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
-}
-template void launch_jump_gather_dots<double>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
-template void launch_jump_gather_dots<float>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
-
 __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
@@ -1582,10 +1573,16 @@ __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
         double2* h2 = K.h2 + (int64_t)r * (K.m + 1);
         cgs_reduce(K, j, r, h2, true);           // h2[0..j]; h2[j+1] = (||w1||^2, 0)
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = h2[j + 1].x;
-            for (int i = 0; i <= j; ++i) s -= h2[i].x * h2[i].x + h2[i].y * h2[i].y;
-            K.hn[r] = s > 0 ? sqrt(s) : 0.0;
+        if (threadIdx.x < 32) {
+            // ||w1||^2 - ||h2||^2: lanes take strided entries, then a fixed butterfly
+            double s = 0;
+            for (int i = threadIdx.x; i <= j; i += 32) {
+                const double2 v = __ldcg(h2 + i);
+                s += v.x * v.x + v.y * v.y;
+            }
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            s = __ldcg(h2 + j + 1).x - s;
+            if (threadIdx.x == 0) K.hn[r] = s > 0 ? sqrt(s) : 0.0;
         }
     }
 }
@@ -1645,19 +1642,25 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     }
     const double2* h1 = K.hcol + (int64_t)r * (K.m + 1);
     const double2* h2 = K.h2 + (int64_t)r * (K.m + 1);
+    // the earlier rotations go to shared memory first (all threads), so the serial
+    // Givens sweep below reads no global memory
+    __shared__ double cs_s[256];
+    __shared__ double2 sn_s[256];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 a = __ldcg(h1 + i), b = __ldcg(h2 + i);
         Hc[i] = make_double2(a.x + b.x, a.y + b.y);
+        if (i < j) {
+            cs_s[i] = __ldcg(K.cs + (int64_t)r * K.m + i);
+            sn_s[i] = __ldcg(K.sn + (int64_t)r * K.m + i);
+        }
     }
     if (threadIdx.x == 0) { Hc[j + 1] = make_double2(hn, 0.0); hn_s = hn; }
     __syncthreads();
     if (threadIdx.x == 0 && !K.rdone[r]) {
-        const double* cs = K.cs + (int64_t)r * K.m;
-        const double2* sn = K.sn + (int64_t)r * K.m;
         for (int i = 0; i < j; ++i) {
             const double2 a = Hc[i], b = Hc[i + 1];
-            const double c = cs[i];
-            const double2 s = sn[i];
+            const double c = cs_s[i];
+            const double2 s = sn_s[i];
             // t0 = c a + s b ; t1 = -conj(s) a + c b
             const double2 t0 = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
             const double2 t1 = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
@@ -1695,14 +1698,24 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) Hcol[i] = Hc[i];
 
     // the last right-hand side to finish advances the column counter; it stops the
-    // iteration once every right-hand side has converged or at the restart boundary
-    if (cgs_last_chunk_all(K, &last_f) && threadIdx.x == 0) {
+    // iteration once every right-hand side has converged or at the restart boundary (with
+    // one right-hand side this CTA is already the last of the launch)
+    const bool last_all = K.R == 1 ? true : cgs_last_chunk_all(K, &last_f);
+    if (last_all && threadIdx.x == 0) {
         int all = 1;
         for (int rr = 0; rr < K.R; ++rr) all &= __ldcg(K.rdone + rr);
         if (all || j + 1 >= K.m) K.ctl[1] = 1;
         K.ctl[0] = j + 1;
     }
 }
+
+template <class T>
+void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
+                             cudaStream_t st) {
+    k_jump_gather_dots<T><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
+}
+template void launch_jump_gather_dots<double>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
+template void launch_jump_gather_dots<float>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
 
 // nu[r] += sum_i y[r][i] Zb[r][i] (i < iters_r)
 __global__ void k_update(const double2* __restrict__ Zb, const double2* __restrict__ y, const int* __restrict__ nit,

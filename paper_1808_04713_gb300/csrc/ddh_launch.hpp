@@ -10,6 +10,9 @@ namespace ddh {
 // Flexible-GMRES state on the device (FP64).  Per RHS r: V[r][j][nd] (j <= m),
 // Zb[r][j][nd] (j < m), H[r][j][m+1] (column j), cs[r][m], sn[r][m], g[r][m+1].
 // ctl[0] = current column j, ctl[1] = stop flag (all converged or restart boundary).
+// rows per CTA of the orthogonalisation kernels for short vectors (n_d <= 16384)
+constexpr int kCgsShortRows = 128;
+
 struct KrylovDev {
     double2* V; double2* Zb; double2* H; double* cs; double2* sn; double2* g; double* bnorm;
     double* resid; int* ctl; int* rdone; int* iters; double2* partial; double2* hcol; double2* w;
@@ -107,7 +110,7 @@ void launch_conf_gather(const DevModel& dm, const double2* x, double* norm2, int
 // CGS2 + normalisation + Givens of one FGMRES iteration; skip_first when the operator already
 // left the first projection's coefficients (launch_jump_gather_dots)
 void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first = false);
-// w = C^ x (into K.w) fused with the first CGS pass; requires K.chunk == 128
+// w = C^ x (into K.w) fused with the first CGS pass; requires K.chunk == kCgsShortRows
 template <class T>
 void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
                              cudaStream_t st);
