@@ -526,6 +526,11 @@ static ddh_status upload_model(ddh_ctx* ctx) {
                 ctx->nd_fwd_rows[lv] = std::max(ctx->nd_fwd_rows[lv], N.nF);
             }
             ctx->nd_fwd_n[lv] = (int)items.size() - ctx->nd_fwd_off[lv];
+            // heaviest items first: CTAs are dispatched in index order, so the level's tail is
+            // made of the light items (each item writes its own rows: the result is unchanged)
+            std::stable_sort(items.begin() + ctx->nd_fwd_off[lv], items.end(), [&](const int4& a, const int4& b) {
+                return (int64_t)m.cnode[a.x].nF * (a.z + 1) > (int64_t)m.cnode[b.x].nF * (b.z + 1);
+            });
             ctx->nd_bwd_off[lv] = (int)items.size();
             for (int id = 0; id < nn; ++id) {
                 const auto& N = m.cnode[id];
@@ -535,6 +540,11 @@ static ddh_status upload_model(ddh_ctx* ctx) {
                 ctx->nd_bwd_rows[lv] = std::max(ctx->nd_bwd_rows[lv], N.nF + (int)N.B.size());
             }
             ctx->nd_bwd_n[lv] = (int)items.size() - ctx->nd_bwd_off[lv];
+            std::stable_sort(items.begin() + ctx->nd_bwd_off[lv], items.end(), [&](const int4& a, const int4& b) {
+                const auto& A = m.cnode[a.x];
+                const auto& B = m.cnode[b.x];
+                return (int64_t)(A.nF + (int)A.B.size()) * (a.z + 1) > (int64_t)(B.nF + (int)B.B.size()) * (b.z + 1);
+            });
         }
         for (int lv = 0; lv < L; ++lv)
             if (ctx->nd_bwd_rows[lv] > 12800) return fail(ctx, DDH_ERR_INVALID_ARG, "coarse front too large for shared memory");
