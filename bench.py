@@ -134,7 +134,7 @@ class ClockSampler:
 
 
 def algorithmic_work(info, R: int, p: int, nE: float, nT: float, fp64: bool):
-    """FLOPs and HBM bytes per launch of the operator components, Krylov-loop
+    """Algorithmic FLOPs and HBM bytes per launch of the operator components, Krylov-loop
     form with explicit edge operators: index 0 pass 1 ([S_E^-1; Y^T] r_E), 2 coarse solve
     (dense K^-1), 3 pass 2 (x_E - Y u_T); n_E type-1 edge and n_T type-2 slots per element."""
     E = info.n_elem

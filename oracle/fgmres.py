@@ -1,13 +1,15 @@
 """Flexible GMRES (right preconditioned, restarted, classical Gram-Schmidt applied twice).
 
-The paper uses left-preconditioned PGMRES (Sec. 2.3.4); this build uses the flexible,
-right-preconditioned variant so that the stopping test measures the true residual
+The paper uses left-preconditioned PGMRES (Sec. 2.3.4); this implementation uses the
+flexible, right-preconditioned variant so that the stopping test measures the true residual
 ||b - A x|| / ||b|| (zero initial guess, as in Sec. 3).  Complex Givens rotations
 G = [[c, s], [-conj(s), c]] with real c.
 
-Pin (tests/test_oracle_fgmres.py): on random well-conditioned complex systems the
-iterate matches numpy.linalg.solve, the residual estimate equals the true residual, and
-with the identity preconditioner the residual history is monotone.
+Pins (tests/test_oracle_dd.py): on random well-conditioned complex systems the iterate
+matches numpy.linalg.solve, the residual estimate after every iteration equals the true
+residual of the iterate formed there, a preconditioner that changes from one application to
+the next still converges to the same solution, and with the identity preconditioner the
+residual history is monotone.
 """
 from __future__ import annotations
 

@@ -114,3 +114,40 @@ def test_fgmres_against_dense_solve():
     assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-12
     assert np.allclose(x, np.linalg.solve(A, b), atol=1e-11)
     assert all(a >= b - 1e-15 for a, b in zip(hist[:15], hist[1:16]))
+
+
+def test_fgmres_residual_estimate_is_the_true_residual():
+    # stopping after k iterations (no restart) forms x_k from the same least-squares problem
+    # whose residual |g_{k+1}| the estimate reports, so the two agree to rounding
+    rng = np.random.default_rng(5)
+    n = 40
+    A = np.eye(n) * 3 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    D = np.diag(1.0 / np.diag(A))
+    for k in (1, 3, 7, 12):
+        x, it, hist = fgmres(lambda v: A @ v, lambda v: D @ v, b, tol=0.0, restart=50, maxit=k)
+        assert it == k
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert abs(hist[-1] - true) <= 1e-12 * max(1.0, true)
+
+
+def test_fgmres_flexible_preconditioner():
+    # a preconditioner that differs on every application (a few Jacobi sweeps, one more each
+    # call): flexible GMRES keeps Z_j and still reaches the dense solution
+    rng = np.random.default_rng(6)
+    n = 50
+    A = np.eye(n) * 5 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    d = np.diag(A)
+    calls = [0]
+
+    def prec(v):
+        calls[0] += 1
+        z = v / d
+        for _ in range(calls[0] % 4):
+            z = z + (v - A @ z) / d
+        return z
+
+    x, it, hist = fgmres(lambda v: A @ v, prec, b, tol=1e-12, restart=30, maxit=200)
+    assert np.allclose(x, np.linalg.solve(A, b), atol=1e-10)
+    assert np.linalg.norm(b - A @ x) / np.linalg.norm(b) <= 1e-11
