@@ -79,7 +79,11 @@ typedef struct {
     int32_t precond;       /* ddh_precond */
     int32_t inner_iters;   /* mixed precision: at most this many dual FGMRES iterations per
                               preconditioner application (default 10) */
-    int32_t check_every;   /* host polls convergence every this many iterations (default 4) */
+    int32_t check_every;   /* host polls convergence every this many iterations (default 4);
+                              the first cycle of a solve first runs up to one short of the
+                              previous solve's count on this context, then polls after each of
+                              the next two iterations (iterations past convergence do nothing,
+                              so results do not depend on the polling) */
     int32_t use_graph;     /* 1: replay one FGMRES iteration as a CUDA graph (default 1) */
     int32_t coarse_fp32;   /* mixed precision only: 1 = inside the inner (preconditioner) solves,
                               apply a complex64 copy of the coarse factor in FP32 arithmetic,
