@@ -55,6 +55,14 @@ def aggregate_rate(world: int, steps: int, rhs: int, slowest_total_s: float) -> 
     return world * steps * rhs / slowest_total_s
 
 
+def workload_config(R: int, l: int, n_dual: int, n_coarse: int, l2: str, parallelism: str) -> dict:
+    """The `config` object of both arms: the timed workload (16 x 16 squares of degree 16,
+    k = 100, one plane wave) and the sizes the method derives from it."""
+    return {"workload": WORKLOAD, "mesh": "16x16 squares", "p": 16, "k": 100.0, "rhs": R,
+            "l": int(l), "n_dual": int(n_dual), "n_coarse": int(n_coarse),
+            "dof": int((16 * 16 + 1) ** 2), "precision": "fp64", "l2": l2, "parallelism": parallelism}
+
+
 def _oracle_timing(name: str, n: int, budget: float, threads: int = 1) -> dict:
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
                MKL_NUM_THREADS=str(threads), CUDA_VISIBLE_DEVICES="")
@@ -305,10 +313,8 @@ def run_ours(args):
                "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 4),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
                "data": "synthetic plane-wave impedance data (closed form)",
-               "config": {"workload": WORKLOAD, "mesh": "16x16 squares", "p": 16, "k": 100.0, "rhs": R,
-                          "l": info.l, "n_dual": info.n_dual, "n_coarse": info.n_coarse,
-                          "dof": int((16 * 16 + 1) ** 2), "precision": "fp64",
-                          "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{ws}"},
+               "config": workload_config(R, info.l, info.n_dual, info.n_coarse,
+                                         "flushed (256 MB write) between timed steps", f"replicas x{ws}"),
                "iterations": iters[-1] if iters else None, "primal_residual": float(pr[0]),
                "dof_per_s": round(value * (16 * 16 + 1) ** 2, 1),
                "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
@@ -336,7 +342,8 @@ def run_reference(args):
            "steps": len(ts), "warmup": args.warmup, "ms_per_step": round(1e3 * per, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
            "data": "synthetic plane-wave impedance data (closed form)",
-           "config": {"workload": WORKLOAD, "mesh": "16x16 squares", "p": 16, "k": 100.0, "rhs": 1},
+           "config": workload_config(1, o["l"], o["n_dual"], o["n_coarse"], "host CPU run (no device L2)",
+                                     "oracle on rank 0"),
            "cpu_baseline": {"value": round(val, 5), "unit": UNIT, "cores": o["threads"], "kind": "oracle",
                             "sample": f"oracle DD solve of {WORKLOAD}, {len(ts)} timed solves, single BLAS thread"},
            "e2e": {"value": round(val, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
