@@ -1,0 +1,58 @@
+"""Host-only setup and factorisation of the native library (no GPU) against the oracle.
+
+The library classifies slots, builds the dual rows and the coarse matrix K, and factors K
+by nested dissection in its own C++ code. The oracle builds the same objects from
+eq. final_constraint and Algorithm 1 with dense and sparse linear algebra. They share no
+code, so equal sizes and the same l (eq. dispersion_criterion) check the host logic. The
+library's self-checks are also bounded: one coarse solve K x = t with a seeded random t,
+and S_E S_E^-1 = I for every element."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dd
+
+
+@pytest.fixture(scope="module")
+def ddh():
+    from paper_1808_04713_gb300 import build as b
+    b.build()
+    from paper_1808_04713_gb300 import ddh as m
+    return m
+
+
+CASES = {
+    "plane_2x2": W.plane_2x2,
+    "uniform3_eps": lambda: W.small_uniform(3, 8, 6.0, seed=1, eps_range=(1.0, 2.0)),
+    "uniform4_mixed_p": lambda: W.small_uniform(4, 8, 5.0, seed=2, p_range=(5, 9)),
+    "hanging4": lambda: W.small_hanging(4, refine=((1, 1),), levels=2, p=8, k=6.0),
+    "hanging_mixed_p": lambda: W.small_hanging(3, refine=((0, 0), (2, 1)), levels=1, p=7, k=5.0,
+                                               seed=3, p_range=(5, 9)),
+    "multilevel": W.multilevel_hanging,
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_host_factor_matches_oracle(ddh, name):
+    w = CASES[name]()
+    sizes, secs, l = ddh.host_factor(w.base_n, w.leaves, w.p, w.k, w.eps)
+    S = dd.DDSolver(dd.problem_from_workload(w))
+    assert l == S.l
+    assert sizes["n_local"] == int(np.sum((np.asarray(w.p) + 1) ** 2))
+    assert sizes["n_dual"] == S.nd
+    assert sizes["n_coarse"] == S.n2
+    assert sizes["n_e1"] + sizes["n_t"] > 0
+    assert 0 < sizes["max_block"] <= sizes["n_coarse"]
+    assert secs[2] <= 1e-12, secs          # ||K x - t|| / ||t|| of one coarse solve
+    assert secs[3] <= 1e-10, secs          # max_e ||S_E S_E^-1 - I||_max
+    assert secs[4] > 0                     # no interior block at resonance
+
+
+@pytest.mark.parametrize("l", [2, 3, 5])
+def test_host_factor_l_override(ddh, l):
+    w = W.small_hanging(4, refine=((1, 1),), levels=1, p=8, k=6.0)
+    sizes, secs, l_used = ddh.host_factor(w.base_n, w.leaves, w.p, w.k, w.eps, l_override=l)
+    S = dd.DDSolver(dd.problem_from_workload(w), l=l)
+    assert l_used == l
+    assert (sizes["n_dual"], sizes["n_coarse"]) == (S.nd, S.n2)
+    assert secs[2] <= 1e-12
