@@ -74,7 +74,7 @@ def vec_to_tilde(p: int, v: np.ndarray) -> np.ndarray:
 def robin_load_N(p: int, side: int, q_of_t, half_h: float, nq: int = 0) -> np.ndarray:
     """r_i = S q_i (x) (e1 +- e2)/sqrt(2) (or the mirrored Kronecker order for i = 3,4),
     with q_i = int q_eff(t) p(t) dt the Legendre coefficients of q_eff = q h/2 along the side,
-    computed by Gauss-Legendre quadrature (the paper's 'direct evaluation' option)."""
+    computed by Gauss-Legendre quadrature (evaluating the integrals directly, one of the paper's options)."""
     nq = nq or (p + 40)
     t, w = lg.gauss_legendre(nq)
     qi = (lg.legendre_p(p, t) * w) @ (np.asarray(q_of_t(t), dtype=complex) * half_h)
