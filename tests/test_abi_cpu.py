@@ -50,3 +50,20 @@ def test_gauss_rule(lib):
     x, w = ddh.table_gauss(40)
     xo, wo = np.polynomial.legendre.leggauss(40)
     assert np.abs(x - xo).max() < 1e-14 and np.abs(w - wo).max() < 1e-14
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the product path has no fallback: without the built library every entry point raises
+    from paper_1808_04713_gb300 import ddh
+    with pytest.raises(ImportError, match="not built"):
+        ddh.load_library(str(tmp_path / "libddh.so"))
+
+
+def test_context_without_gpu_reports_an_error(lib):
+    # with no CUDA device visible, creating a solver context fails with a status, not a crash
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is visible")
+    from paper_1808_04713_gb300 import ddh
+    with pytest.raises(ddh.DDHError, match="create failed"):
+        ddh.DDH(0)
