@@ -70,6 +70,11 @@ typedef enum { DDH_PRECOND_DIRICHLET = 0, DDH_PRECOND_LUMPED = 1, DDH_PRECOND_NO
  * The RHS pass and the recovery of the interior always use the FDM. */
 typedef enum { DDH_LOCAL_EDGE = 0, DDH_LOCAL_FDM = 1 } ddh_local_form;
 
+/* How the coarse system K x2 = t of eq. block_matrix_inversion (Sec. 2.3.3) is solved on the
+ * device: a dense K^-1 (one GEMV per application) or the nested-dissection multifrontal factor
+ * (one launch per tree level).  Both come from the same factorisation. */
+typedef enum { DDH_COARSE_AUTO = 0, DDH_COARSE_DENSE = 1, DDH_COARSE_ND = 2 } ddh_coarse_form;
+
 typedef struct {
     double tol;            /* relative residual target (default 1e-10) */
     int32_t maxit;         /* total Krylov iterations per RHS (default 300) */
@@ -96,6 +101,11 @@ typedef struct {
                               estimate falls below inner_tol relative to its start (default
                               1e-5; 0 = always inner_iters iterations).  The complex64 inner
                               solves cannot gain much more than 5-6 digits per application */
+    int32_t coarse_form;   /* coarse solve K x2 = t (ddh_coarse_form): DDH_COARSE_AUTO (default) applies
+                              a dense K^-1 built from the factor when n_coarse <= 6144 and the
+                              nested-dissection solve otherwise; DDH_COARSE_DENSE forces the dense
+                              K^-1 (n_coarse <= 16384, else DDH_ERR_INVALID_ARG); DDH_COARSE_ND forces
+                              the nested-dissection solve at any size */
 } ddh_options;
 
 typedef struct {
@@ -109,6 +119,10 @@ typedef struct {
     int32_t max_block;     /* largest front (fully summed + boundary unknowns); n_coarse when dense */
     double min_resonance_gap; /* min over elements of min |D_ab| / max |D_ab| of the FDM */
     double factor_seconds; /* wall time of the last ddh_factor */
+    double coarse_nd_flops;/* algorithmic real FLOPs per right-hand side of one nested-dissection
+                              coarse solve, 8 sum_fronts nF (nF + 2 nB): forward G y_F and backward
+                              [W | -H] [y_F; x_B] (reported also when the dense K^-1 is in use) */
+    int32_t coarse_form;   /* form in use: DDH_COARSE_DENSE or DDH_COARSE_ND */
 } ddh_info;
 
 typedef struct {
@@ -200,16 +214,19 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
 
 /* Allocation-free variant of ddh_primal_residual (the paper has no counterpart: this is a
  * service of the library).  Some callers cannot allocate device memory where they need the
- * residual -- code running while its stream is captured into a CUDA graph, where cudaMalloc is
- * not allowed, and applications that fix their device-memory budget at start-up.  This call
- * allocates nothing: it works in one file-scope device scratch array of 32 MiB that every GPU
- * loading the library holds until the process exits.  It needs 16 R (4 n_local + n_conforming)
- * bytes plus 2 x 256-byte-aligned norm slots; larger problems (and R > 512) are rejected with
- * DDH_ERR_INVALID_ARG and a message naming the limit.  The first call on a device looks up the
- * scratch address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the one array (it keeps the last call's
- * contents; the accumulators are cleared on entry), so calls that overlap on the GPU -- from
- * several streams or threads -- race.  Same arguments and result as ddh_primal_residual. */
+ * residual: applications that reserve their whole device-memory budget at start-up and forbid
+ * later cudaMalloc calls, and callers in latency-critical loops that avoid cudaMalloc/cudaFree
+ * because those can synchronise the whole device.  This call allocates nothing: it works in
+ * one file-scope device scratch array of 32 MiB that every GPU loading the library holds until
+ * the process exits.  It needs 16 R (4 n_local + n_conforming) bytes plus 2 x 256-byte-aligned
+ * norm slots; larger problems (and R > 512) are rejected with DDH_ERR_INVALID_ARG and a message
+ * naming the limit.  Before factor it returns DDH_ERR_NOT_READY.  The first call on a device
+ * looks up the scratch address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The call synchronises the context stream to copy the
+ * norms to out_host, and leaves the caller's current device as it found it.  Every call on a
+ * device shares the one array (it keeps the last call's contents; the accumulators are cleared
+ * on entry), so calls that overlap on the GPU -- from several streams or threads -- race.
+ * Same arguments and result as ddh_primal_residual. */
 ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
                                        double* out_host);
 
@@ -232,7 +249,7 @@ void ddh_destroy(ddh_ctx* ctx);
  * Sylvester row recurrence of Sec. 2.1.6; out: (n+1)^2 doubles, row-major Lt[k][m]. */
 ddh_status ddh_table_affine(int32_t n, double a, double b, double* out);
 /* Bubble-mass fast-diagonalisation table for degree p: V (n x n, row-major, n = p-1) and
- * mu (n) with M_b = V diag(mu) V^T (even/odd blocks, own implicit-QL eigensolver). */
+ * mu (n) with M_b = V diag(mu) V^T (even/odd blocks, own cyclic Jacobi eigensolver). */
 ddh_status ddh_table_fdm(int32_t p, double* V_out, double* mu_out);
 /* Gauss-Legendre nodes/weights by the Golub-Welsch method (own eigensolver). */
 ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);

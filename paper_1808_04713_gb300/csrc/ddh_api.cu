@@ -1170,12 +1170,20 @@ static ddh_status primal_residual_dev(ddh_ctx* ctx, const double2* bt, const dou
     return DDH_OK;
 }
 
+// Fills stats; `known` is the primal residual of this very iterate when the solve already
+// computed it (the plain method's stopping test), so it is not recomputed.
 static ddh_status finish_stats(ddh_ctx* ctx, const double2* bt, const double2* phit, int R, const std::vector<int>& its,
-                               const std::vector<int>& inner, const std::vector<double>& res, ddh_rhs_stats* stats) {
+                               const std::vector<int>& inner, const std::vector<double>& res, ddh_rhs_stats* stats,
+                               const std::vector<double>* known = nullptr) {
     if (!stats) { CK(cudaStreamSynchronize(ctx->stream)); return DDH_OK; }
     std::vector<double> pr;
     ddh_status st;
-    if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) return st;
+    if (known && (int)known->size() == R) {
+        pr = *known;
+        CK(cudaStreamSynchronize(ctx->stream));
+    } else if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) {
+        return st;
+    }
     for (int i = 0; i < R; ++i) {
         stats[i].iterations = its[i];
         stats[i].inner_iterations = inner.empty() ? 0 : inner[i];
@@ -1218,7 +1226,7 @@ static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
     CK(cudaGetLastError());
     bool conv = true;
     for (int i = 0; i < R; ++i) conv &= (d.n_dual == 0) || (i < (int)pr.size() ? pr[i] <= tol : res[i] <= tol);
-    if ((st = finish_stats(ctx, (const double2*)bt, (const double2*)phit, R, its, {}, res, stats))) return st;
+    if ((st = finish_stats(ctx, (const double2*)bt, (const double2*)phit, R, its, {}, res, stats, &pr))) return st;
     return conv ? DDH_OK : fail(ctx, DDH_ERR_NO_CONVERGENCE, "tolerance not reached within maxit");
 }
 
@@ -1299,6 +1307,7 @@ void ddh_default_options(ddh_options* o) {
     o->coarse_fp32 = 0;
     o->local_form = DDH_LOCAL_EDGE;
     o->inner_tol = 1e-5;
+    o->coarse_form = DDH_COARSE_AUTO;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1353,11 +1362,16 @@ ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (ctx->opt.local_form != DDH_LOCAL_EDGE && ctx->opt.local_form != DDH_LOCAL_FDM)
         return fail(ctx, DDH_ERR_INVALID_ARG, "local_form must be DDH_LOCAL_EDGE or DDH_LOCAL_FDM");
     if (ctx->opt.check_every < 1) ctx->opt.check_every = 1;
+    if (ctx->opt.coarse_form < DDH_COARSE_AUTO || ctx->opt.coarse_form > DDH_COARSE_ND)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form must be DDH_COARSE_AUTO, DDH_COARSE_DENSE or DDH_COARSE_ND");
     const auto t0 = std::chrono::steady_clock::now();
     cudaSetDevice(ctx->device);
     std::string err;
     const int l = ctx->opt.l_override > 0 ? ctx->opt.l_override : dispersion_l(ctx->m);
     if (!classify(ctx->m, l, err)) return fail(ctx, DDH_ERR_INVALID_ARG, err);
+    if (ctx->opt.coarse_form == DDH_COARSE_DENSE && ctx->m.n_coarse > 16384)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form DDH_COARSE_DENSE needs n_coarse <= 16384");
+    ctx->m.coarse_form = ctx->opt.coarse_form;
     const int nth = std::max(1u, std::thread::hardware_concurrency());
     if (!factor(ctx->m, nth, err)) return fail(ctx, DDH_ERR_SINGULAR, err);
     ddh_status st = upload_model(ctx);
@@ -1387,6 +1401,10 @@ ddh_status ddh_get_info(const ddh_ctx* ctx, ddh_info* out) {
     out->max_block = m.dense_coarse ? m.n_coarse : mx;
     out->min_resonance_gap = m.min_gap;
     out->factor_seconds = ctx->factor_seconds;
+    double fl = 0;
+    for (const auto& N : m.cnode) fl += 8.0 * N.nF * ((double)N.nF + 2.0 * (double)N.B.size());
+    out->coarse_nd_flops = fl;
+    out->coarse_form = m.dense_coarse ? DDH_COARSE_DENSE : DDH_COARSE_ND;
     return DDH_OK;
 }
 

@@ -110,6 +110,7 @@ struct Model {
     int c_depth = 0;                              // deepest level
     std::vector<int32_t> kc_ptr, kc_col;          // K in CSR over elimination positions
     std::vector<cd> kc_val;
+    int coarse_form = 0;                          // requested: 0 auto, 1 dense K^-1, 2 nested dissection
     bool dense_coarse = false;                    // use a dense K^-1 instead (elimination order)
     std::vector<cd> Kinv;                         // n_coarse^2 row-major when dense_coarse
     // diagnostics: relative residual ||K x - t|| / ||t|| of one coarse solve with a seeded

@@ -1,0 +1,457 @@
+// Krylov-loop element passes with the explicit edge operators, the coarse assembly, the
+// jump gather C^ x and the Dirichlet preconditioner (Sec. 2.3.3, eqs. complicated_schur_system,
+// general_preconditioner, weight_matrix).
+#include "ddh_kcommon.cuh"
+
+namespace ddh {
+
+// ------------------------------------------------------------------ passes with explicit edge operators
+// Inside the Krylov loop the element solves only ever map type-1 edge values to type-1 edge
+// values and type-2 values (the jump operator touches nothing else), so with
+//   Y = [A11^-1 A_1T]_E = S_E^-1 (A_ET - A_EX G A_XT)      (nE x nT, complex symmetric A)
+// pass 1 is  x_E = S_E^-1 r_E,  t_T = Y^T r_E   (t_T = A_T1 A11^-1 [r_E; 0])
+// pass 2 is  x1_E = x_E - Y u_T                 (x1 = y1 - A11^-1 A12 x2, edge part)
+// -- two small dense products per element and right-hand side block instead of the FDM
+// chain.  Y is formed at factor time.  The interior never enters the iteration; it is
+// rebuilt by the FDM kernels in the recovery.
+template <class T, int RB>
+__global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* __restrict__ sinv,
+                                                    const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
+                                                    double zsign, const double2* __restrict__ bt, int R,
+                                                    cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
+                                                    const int* __restrict__ done, int ntask, int stage_off, int vs) {
+    if (done && *done) return;
+    extern __shared__ __align__(128) char smem[];
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
+    const cpx<T>* S = sinv + dm.sinv_off[e];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_off);
+    cpx<T>* S_s = reinterpret_cast<cpx<T>*>(smem + stage_off + 128);
+    if (stage_off > 0 && nE > 0 && threadIdx.x == 0)
+        bulk_load_start(bar, S_s, S, (uint32_t)(((size_t)nE * nE * sizeof(cpx<T>) + 15) & ~(size_t)15));
+    cpx<T>* rE = reinterpret_cast<cpx<T>*>(smem);     // [RB][vs]
+    const int64_t off = dm.off[e];
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE, r = r0 + q;
+        cpx<T> v = mk<T>(0, 0);
+        const int row = dm.e1_row[e1o + i];
+        if (z && row >= 0) v = (T)(zsign * dm.e1_sign[e1o + i]) * ld<T>(z, (int64_t)r * dm.n_dual + row);
+        if (bt) v += ld<T>(bt, (int64_t)r * dm.n_local + off + dm.e1_slot[e1o + i]);
+        rE[q * vs + i] = v;
+    }
+    g.sync();
+    if (stage_off > 0 && nE > 0) {
+        if (!bulk_wait_all(bar, dm.err)) return;
+        S = S_s;
+    }
+    // [x_E; t_T] = [S_E^-1; Y^T] r_E in one pass: output row o < nE reads S_E^-1 (column-major),
+    // o >= nE reads Y (row-major nE x nT, i.e. Y^T column-major); tpr threads per output row
+    const cpx<T>* Ye = Y + dm.pq_off[e];
+    const int no = nE + nT;
+    const int tpr = no <= 64 ? 4 : (no <= 128 ? 2 : 1);       // 256 threads
+    const int chunk = (nE + tpr - 1) / tpr;
+    for (int base = 0; base < no * tpr; base += blockDim.x) {
+        const int slot = base + threadIdx.x;
+        const int o = slot / tpr, part = slot % tpr;
+        cpx<T> a0[RB], a1[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
+        if (o < no) {
+            const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
+            const int ld = o < nE ? nE : nT;
+            const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
+                const cpx<T> s0 = col0[(int64_t)j * ld], s1 = col0[(int64_t)(j + 1) * ld];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) { fma_c(a0[q], s0, rE[q * vs + j]); fma_c(a1[q], s1, rE[q * vs + j + 1]); }
+            }
+            if (j < j1) {
+                const cpx<T> s0 = col0[(int64_t)j * ld];
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            cpx<T> v = a0[q] + a1[q];
+            for (int sh = 1; sh < tpr; sh <<= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, sh);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, sh);
+            }
+            if (part == 0 && o < no && q < cnt) {
+                if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
+                else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
+            }
+        }
+    }
+}
+
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pass2_edge(DevModel dm, const cpx<T>* __restrict__ Y,
+                                                    const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
+                                                    cpx<T>* __restrict__ xE_out, int R, const int* __restrict__ done,
+                                                    int ntask) {
+    if (done && *done) return;
+    __shared__ cpx<T> uT[RB][128];
+    const CtaGroup g;
+    const int task = blockIdx.x;
+    if (task >= ntask) return;
+    const int e = task % dm.E, r0 = (task / dm.E) * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
+    for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
+        const int q = idx / nT, i = idx % nT, r = r0 + q;
+        cpx<T> u = mk<T>(0, 0);
+        for (int a = dm.t_ptr[to + i]; a < dm.t_ptr[to + i + 1]; ++a) {
+            const double2 xv = x2[(int64_t)r * dm.n_coarse + dm.t_col[a]];
+            const T w = (T)dm.t_w[a];
+            u.x += w * (T)xv.x;
+            u.y += w * (T)xv.y;
+        }
+        uT[q][i] = u;
+    }
+    g.sync();
+    const cpx<T>* Ye = Y + dm.pq_off[e];
+    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
+        const int q = idx / nE, i = idx % nE;
+        const cpx<T>* yr = Ye + (int64_t)i * nT;
+        cpx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+        int t = 0;
+        for (; t + 1 < nT; t += 2) { fma_c(a0, yr[t], uT[q][t]); fma_c(a1, yr[t + 1], uT[q][t + 1]); }
+        if (t < nT) fma_c(a0, yr[t], uT[q][t]);
+        const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
+        xE_out[gi] = xE_in[gi] - (a0 + a1);
+    }
+}
+
+// ------------------------------------------------------------------ coarse assembly
+// t[g] = bsign * (Z2^T b_T)[g] + zsign * (C2^T z)[g] - (Z2^T tT)[g]   (FP64 output)
+template <class T>
+__global__ void k_coarse_assemble(DevModel dm, const cpx<T>* __restrict__ tT, const double2* __restrict__ bt,
+                                  const double2* __restrict__ z, double zsign, double2* __restrict__ tout,
+                                  int R, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (g >= dm.n_coarse) return;
+    double2 acc = make_double2(0, 0);
+    for (int a = dm.g_ptr[g]; a < dm.g_ptr[g + 1]; ++a) {
+        const int ts = dm.g_tslot[a];
+        const double w = dm.g_w[a];
+        const cpx<T> v = tT[(int64_t)r * dm.nT_tot + ts];
+        acc.x -= w * (double)v.x;
+        acc.y -= w * (double)v.y;
+        if (bt) {
+            const int e = dm.t_elem[ts];
+            const double2 b = bt[(int64_t)r * dm.n_local + dm.off[e] + dm.t_slot[ts]];
+            acc.x += w * b.x;
+            acc.y += w * b.y;
+        }
+    }
+    if (z)
+        for (int a = dm.c2t_ptr[g]; a < dm.c2t_ptr[g + 1]; ++a) {
+            const double w = zsign * dm.c2t_w[a];
+            const double2 v = z[(int64_t)r * dm.n_dual + dm.c2t_row[a]];
+            acc.x += w * v.x;
+            acc.y += w * v.y;
+        }
+    tout[(int64_t)r * dm.n_coarse + g] = acc;
+}
+
+// ------------------------------------------------------------------ jump gather (C^ x)
+// w[row] = x1_E[c] - x1_E[f] + sum_k C2[row][k] x2[k]
+template <class T>
+__global__ void k_jump_gather(DevModel dm, const cpx<T>* __restrict__ xE, const double2* __restrict__ x2,
+                              double2* __restrict__ w, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (row >= dm.n_dual) return;
+    double sx = 0, sy = 0;
+    const int c = dm.row_c[row], f = dm.row_f[row];
+    if (c >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + c]; sx += (double)v.x; sy += (double)v.y; }
+    { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
+    for (int a = dm.c2_ptr[row]; a < dm.c2_ptr[row + 1]; ++a) {
+        const double2 v = x2[(int64_t)r * dm.n_coarse + dm.c2_col[a]];
+        sx += dm.c2_w[a] * v.x;
+        sy += dm.c2_w[a] * v.y;
+    }
+    w[(int64_t)r * dm.n_dual + row] = make_double2(sx, sy);
+}
+
+// ------------------------------------------------------------------ preconditioner
+// y = D^-1 x, D = C1_E C1_E^T + C2 C2^T: 1/2 on conforming rows, dense blocks on hanging edges
+__global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __restrict__ y, int lumped,
+                       const int* __restrict__ done) {
+    if (done && *done) return;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (row >= dm.n_dual) return;
+    const int64_t ro = (int64_t)r * dm.n_dual;
+    const int hb = dm.row_hb[row];
+    if (hb < 0) {
+        const double2 v = x[ro + row];
+        y[ro + row] = make_double2(0.5 * v.x, 0.5 * v.y);
+        return;
+    }
+    const int r0 = dm.hb_row0[hb], nr = dm.hb_n[hb];
+    const double* Di = dm.hb_Dinv + dm.hb_off[hb] + (int64_t)(row - r0) * nr;
+    double sx = 0, sy = 0;
+    for (int j = 0; j < nr; ++j) {
+        const double2 v = x[ro + r0 + j];
+        sx += Di[j] * v.x;
+        sy += Di[j] * v.y;
+    }
+    y[ro + row] = make_double2(sx, sy);
+    (void)lumped;
+}
+
+// out_E = S^Lap[E1][E1] (C1^T v) per element (stiffness Schur complement, shared per degree);
+// one CTA per (element, block of RB RHS), each S^Lap entry read once per CTA.
+// out_E = S x for the restricted stiffness Schur complement S (n_E x n_E, symmetric, read from
+// global memory column by column: coalesced across output rows, shared by the elements of a
+// degree pattern and L1/L2-resident); tpr adjacent threads share an output row
+template <class T, int RB>
+__device__ __forceinline__ void pre_apply(const double* __restrict__ S, int nE, int cnt, const cpx<T>* in,
+                                          cpx<T>* __restrict__ out, int64_t ostride) {
+    const int tpr = nE <= 32 ? 4 : (nE <= 64 ? 2 : 1);
+    const int chunk = (nE + tpr - 1) / tpr;
+    for (int base = 0; base < nE * tpr; base += blockDim.x) {
+        const int slot = base + threadIdx.x;
+        const int i = slot / tpr, part = slot % tpr;
+        cpx<T> acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) acc[q] = mk<T>(0, 0);
+        if (i < nE) {
+            const int j1 = min(nE, (part + 1) * chunk);
+            for (int j = part * chunk; j < j1; ++j) {
+                const T sv = (T)__ldg(S + (int64_t)j * nE + i);
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    if (q < cnt) fma_r(acc[q], sv, in[q * nE + j]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            for (int o = 1; o < tpr; o <<= 1) {
+                acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
+                acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
+            }
+            if (part == 0 && i < nE && q < cnt) out[(int64_t)q * ostride + i] = acc[q];
+        }
+    }
+}
+
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __restrict__ v, cpx<T>* __restrict__ outE,
+                                                  int R, const int* __restrict__ done) {
+    if (done && *done) return;
+    extern __shared__ __align__(128) char smem[];
+    const int e = blockIdx.x, r0 = blockIdx.y * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e];
+    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);                 // [RB][nE]
+    for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
+        const int q = idx / nE, i = idx % nE;
+        const int row = dm.e1_row[e1o + i];
+        cpx<T> val = mk<T>(0, 0);
+        if (row >= 0) val = (T)dm.e1_sign[e1o + i] * ld<T>(v, (int64_t)(r0 + q) * dm.n_dual + row);
+        in[q * nE + i] = val;
+    }
+    __syncthreads();
+    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot);
+}
+
+// Conforming meshes (no hanging rows: D = 2 I, no C2 K C2^T term), fused with the Krylov
+// fetch: v = V[r][j] read directly (j = ctl[0]), D^-1 = 1/2 applied in the gather.
+template <class T, int RB>
+__global__ void __launch_bounds__(128) k_pre_elem_kry(DevModel dm, KrylovDev K, cpx<T>* __restrict__ outE, int R) {
+    if (K.ctl[1]) return;
+    const int jj = K.ctl[0];
+    extern __shared__ __align__(128) char smem[];
+    const int e = blockIdx.x, r0 = blockIdx.y * RB;
+    const int cnt = min(RB, R - r0);
+    const int nE = dm.nE1[e], e1o = dm.e1_off[e];
+    cpx<T>* in = reinterpret_cast<cpx<T>*>(smem);
+    for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
+        const int q = idx / nE, i = idx % nE;
+        const int row = dm.e1_row[e1o + i];
+        cpx<T> val = mk<T>(0, 0);
+        if (row >= 0) {
+            const double2* v = K.V + ((int64_t)(r0 + q) * (K.m + 1) + jj) * K.nd;
+            val = (T)(0.5 * dm.e1_sign[e1o + i]) * ld<T>(v, row);
+        }
+        in[q * nE + i] = val;
+    }
+    __syncthreads();
+    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot);
+}
+
+// z = D^-1 (outE[c] - outE[f]) with D = 2 I, written to zw and to the Krylov store Zb[r][j]
+template <class T>
+__global__ void k_pre_rows_kry(DevModel dm, KrylovDev K, const cpx<T>* __restrict__ outE) {
+    if (K.ctl[1]) return;
+    const int jj = K.ctl[0];
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (row >= dm.n_dual) return;
+    double sx = 0, sy = 0;
+    const int c = dm.row_c[row], f = dm.row_f[row];
+    if (c >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + c]; sx += (double)a.x; sy += (double)a.y; }
+    { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
+    const double2 z = make_double2(0.5 * sx, 0.5 * sy);
+    K.zw[(int64_t)r * K.nd + row] = z;
+    K.Zb[((int64_t)r * K.m + jj) * K.nd + row] = z;
+}
+
+// m[row] = outE[c] - outE[f] + (C2 K^Lap C2^T v)[row]
+template <class T>
+__global__ void k_pre_rows(DevModel dm, const cpx<T>* __restrict__ outE, const double2* __restrict__ v,
+                           double2* __restrict__ m, int lumped, const int* __restrict__ done) {
+    if (done && *done) return;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (row >= dm.n_dual) return;
+    double sx = 0, sy = 0;
+    const int c = dm.row_c[row], f = dm.row_f[row];
+    if (c >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + c]; sx += (double)a.x; sy += (double)a.y; }
+    { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
+    if (!lumped)
+        for (int a = dm.mh_ptr[row]; a < dm.mh_ptr[row + 1]; ++a) {
+            const double2 vv = v[(int64_t)r * dm.n_dual + dm.mh_col[a]];
+            sx += dm.mh_val[a] * vv.x;
+            sy += dm.mh_val[a] * vv.y;
+        }
+    m[(int64_t)r * dm.n_dual + row] = make_double2(sx, sy);
+}
+
+// ------------------------------------------------------------------ launch wrappers
+template <class T>
+void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
+                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const int so = edge_stage_off<T>(rb, dm.maxE1);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const size_t sm = edge_smem_total<T>(rb, dm.maxE1);
+    const int vs = std::max(1, dm.maxE1);
+    const cpx<T>* S = (const cpx<T>*)sinv;
+    const cpx<T>* Yp = (const cpx<T>*)Y;
+    switch (rb) {
+        case 8: k_pass1_edge<T, 8><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 4: k_pass1_edge<T, 4><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 2: k_pass1_edge<T, 2><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        default: k_pass1_edge<T, 1><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
+    }
+}
+template <class T>
+void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
+                       const int* done, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const int ntask = dm.E * ((R + rb - 1) / rb);
+    const cpx<T>* Yp = (const cpx<T>*)Y;
+    const cpx<T>* xi = (const cpx<T>*)xE_in;
+    cpx<T>* xo = (cpx<T>*)xE_out;
+    switch (rb) {
+        case 8: k_pass2_edge<T, 8><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 4: k_pass2_edge<T, 4><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 2: k_pass2_edge<T, 2><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        default: k_pass2_edge<T, 1><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
+    }
+}
+template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass2_edge<double>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
+template void launch_pass2_edge<float>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
+template <class T>
+void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* bt, const double2* z, double zsign,
+                            double2* t, int R, const int* done, cudaStream_t st) {
+    k_coarse_assemble<T><<<dim3((dm.n_coarse + 127) / 128, R), 128, 0, st>>>(dm, (const cpx<T>*)tT, bt, z, zsign, t, R, done);
+}
+template <class T>
+void launch_jump_gather(const DevModel& dm, const void* xE, const double2* x2, double2* w, int R, const int* done,
+                        cudaStream_t st) {
+    k_jump_gather<T><<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, w, done);
+}
+template <class T>
+void launch_pre(const DevModel& dm, const double2* v, double2* vd, void* outE, double2* m, double2* z, int lumped,
+                int R, const int* done, cudaStream_t st) {
+    const dim3 gr((dm.n_dual + 127) / 128, R);
+    k_dinv<<<gr, 128, 0, st>>>(dm, v, vd, lumped, done);
+    const int rb = rhs_block(R);
+    const dim3 g(dm.E, (R + rb - 1) / rb);
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + 16;
+    switch (rb) {
+        case 8: k_pre_elem<T, 8><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        case 4: k_pre_elem<T, 4><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        case 2: k_pre_elem<T, 2><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done); break;
+        default: k_pre_elem<T, 1><<<g, 128, sm, st>>>(dm, vd, (cpx<T>*)outE, R, done);
+    }
+    k_pre_rows<T><<<gr, 128, 0, st>>>(dm, (const cpx<T>*)outE, vd, m, lumped, done);
+    k_dinv<<<gr, 128, 0, st>>>(dm, m, z, lumped, done);
+}
+
+template void launch_coarse_assemble<double>(const DevModel&, const void*, const double2*, const double2*, double, double2*, int, const int*, cudaStream_t);
+template void launch_coarse_assemble<float>(const DevModel&, const void*, const double2*, const double2*, double, double2*, int, const int*, cudaStream_t);
+template void launch_jump_gather<double>(const DevModel&, const void*, const double2*, double2*, int, const int*, cudaStream_t);
+template void launch_jump_gather<float>(const DevModel&, const void*, const double2*, double2*, int, const int*, cudaStream_t);
+template void launch_pre<double>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
+template void launch_pre<float>(const DevModel&, const double2*, double2*, void*, double2*, double2*, int, int, const int*, cudaStream_t);
+void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const int* done, cudaStream_t st) {
+    k_dinv<<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, x, y, 1, done);
+}
+template <class T>
+void launch_pre_krylov(const DevModel& dm, const KrylovDev& K, void* outE, int R, cudaStream_t st) {
+    const int rb = rhs_block(R);
+    const dim3 g(dm.E, (R + rb - 1) / rb);
+    const size_t sm = sizeof(cpx<T>) * (size_t)rb * dm.maxE1 + 16;
+    switch (rb) {
+        case 8: k_pre_elem_kry<T, 8><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        case 4: k_pre_elem_kry<T, 4><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        case 2: k_pre_elem_kry<T, 2><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R); break;
+        default: k_pre_elem_kry<T, 1><<<g, 128, sm, st>>>(dm, K, (cpx<T>*)outE, R);
+    }
+    k_pre_rows_kry<T><<<dim3((dm.n_dual + 127) / 128, R), 128, 0, st>>>(dm, K, (const cpx<T>*)outE);
+}
+template void launch_pre_krylov<double>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
+template void launch_pre_krylov<float>(const DevModel&, const KrylovDev&, void*, int, cudaStream_t);
+
+
+template <class T, int RB>
+static void set_edge_pass_limits(int maxE1) {
+    cudaFuncSetAttribute(k_pass1_edge<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem_total<T>(RB, maxE1));
+}
+void set_edge_limits(int pmax, int maxE1) {
+    (void)pmax;
+    set_edge_pass_limits<double, 1>(maxE1); set_edge_pass_limits<double, 2>(maxE1);
+    set_edge_pass_limits<double, 4>(maxE1); set_edge_pass_limits<double, 8>(maxE1);
+    set_edge_pass_limits<float, 1>(maxE1); set_edge_pass_limits<float, 2>(maxE1);
+    set_edge_pass_limits<float, 4>(maxE1); set_edge_pass_limits<float, 8>(maxE1);
+    const int pre64 = (int)(sizeof(cpx<double>) * 8 * (size_t)maxE1 + sizeof(double) * (size_t)maxE1 * maxE1 + 16);
+    const int pre32 = (int)(sizeof(cpx<float>) * 8 * (size_t)maxE1 + sizeof(float) * (size_t)maxE1 * maxE1 + 16);
+    cudaFuncSetAttribute(k_pre_elem<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre64);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+    cudaFuncSetAttribute(k_pre_elem_kry<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, pre32);
+}
+
+}  // namespace ddh

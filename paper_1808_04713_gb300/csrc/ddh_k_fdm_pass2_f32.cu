@@ -1,0 +1,9 @@
+// FDM recovery / FDM-form pass 2, complex64 element arithmetic.
+#include "ddh_k_fdm.cuh"
+
+namespace ddh {
+
+template void launch_pass2<float>(const DevModel&, const void*, const void*, const double2*, const void*, void*, int, const double2*, int, double2*, int, const int*, cudaStream_t);
+template void set_pass2_limits<float>(int, int);
+
+}  // namespace ddh

@@ -1,4 +1,4 @@
-// Host-callable launch wrappers of the CUDA kernels (one translation unit owns the kernels).
+// Host-callable launch wrappers of the CUDA kernels (defined in the ddh_k_*.cu units).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>

@@ -1,12 +1,15 @@
 // Allocation-free variant of the FP64 primal-residual yardstick (ddh_primal_residual).
 //
-// Some callers cannot allocate device memory at the point where they need this number:
-// code that runs while its stream is being captured into a CUDA graph (cudaMalloc is not a
-// capturable operation), and applications that fix their device-memory budget at start-up
-// and forbid allocations afterwards.  This entry point works in one file-scope scratch array
-// in device memory instead of the context's on-demand work buffers.  The array is a symbol
-// of this library: every GPU that loads the library holds kScratchBytes of it until the
-// process exits.
+// Some callers cannot allocate device memory at the point where they need this number.
+// An application that reserves its whole device-memory budget at start-up (its own pool
+// allocator, or a hard cap shared with other solvers on the same GPU) forbids any later
+// cudaMalloc: the allocation would fail or break its accounting.  A caller inside a
+// latency-critical loop avoids cudaMalloc and cudaFree because they can synchronise the
+// whole device and stall the work of other streams.  This entry point works in one
+// file-scope scratch array in device memory instead of the context's on-demand work
+// buffers, so it allocates nothing.  The array is a symbol of this library: every GPU
+// that loads the library holds kScratchBytes of it until the process exits.  The call
+// still synchronises the context stream to return the norms to the host.
 #include <mutex>
 
 #include "../../include/ddh.h"
@@ -38,6 +41,20 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Makes `dev` current for the lifetime of the guard and gives the caller's current device
+// back on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
@@ -60,7 +77,8 @@ extern "C" ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_de
                            "scratch (4 R n_local + R n_conforming complex128); use ddh_primal_residual");
         return DDH_ERR_INVALID_ARG;
     }
-    if (cudaSetDevice(dev) != cudaSuccess) { ctx_set_error(ctx, "cudaSetDevice failed"); return DDH_ERR_CUDA; }
+    const DeviceGuard guard(dev);
+    if (!guard.ok) { ctx_set_error(ctx, "cudaSetDevice failed"); return DDH_ERR_CUDA; }
     unsigned char* base;
     {
         // once per device, with that device current: the device address of the scratch symbol

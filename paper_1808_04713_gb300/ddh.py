@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_READY, ERR_NO_CONVERGENCE, ERR_S
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
 LOCAL_EDGE, LOCAL_FDM = 0, 1
+COARSE_AUTO, COARSE_DENSE, COARSE_ND = 0, 1, 2
 
 
 class DDHError(RuntimeError):
@@ -32,14 +33,15 @@ class Options(C.Structure):
                 ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
                 ("coarse_fp32", C.c_int32), ("local_form", C.c_int32),
-                ("inner_tol", C.c_double)]
+                ("inner_tol", C.c_double), ("coarse_form", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("n_elem", C.c_int32), ("l", C.c_int32), ("n_local", C.c_int64),
                 ("n_dual", C.c_int64), ("n_coarse", C.c_int64), ("n_conforming", C.c_int64),
                 ("n_coarse_blocks", C.c_int32), ("max_block", C.c_int32),
-                ("min_resonance_gap", C.c_double), ("factor_seconds", C.c_double)]
+                ("min_resonance_gap", C.c_double), ("factor_seconds", C.c_double),
+                ("coarse_nd_flops", C.c_double), ("coarse_form", C.c_int32)]
 
 
 class RhsStats(C.Structure):

@@ -133,6 +133,20 @@ def lens_48() -> Workload:
                     np.array([0.0]), points=pts, fd_index=fd)
 
 
+def corner_block(w: Workload, n: int, n_rhs: int = 1) -> Workload:
+    """The n x n block of elements in the lower-left corner of a uniform workload, as a problem
+    of its own on [0, n/base_n]^2 rescaled to the unit square by keeping the element size: the
+    same degree, wavenumber and permittivity draws of those elements, and the first n_rhs angles.
+    (A bounded sample of a large uniform workload for the CPU oracle.)"""
+    assert int(w.leaves[:, 0].max()) == 0, "uniform workloads only"
+    sel = (w.leaves[:, 1] < n) & (w.leaves[:, 2] < n)
+    lv = w.leaves[sel]
+    # same element size h = 1/base_n on a domain of n x n elements: wavenumber scaled by n/base_n
+    scale = n / w.base_n
+    return Workload(f"{w.name}_corner{n}", n, lv.copy(), w.p[sel].copy(), w.eps[sel].copy(), w.k * scale,
+                    w.thetas[:n_rhs].copy())
+
+
 WORKLOADS = {
     "plane_2x2": plane_2x2,
     "plane_16x16": plane_16x16,
