@@ -1,11 +1,16 @@
 #!/usr/bin/env python
-"""Benchmark: Helmholtz DD solves/sec at relative residual 1e-10 (plane_16x16 workload:
-16x16 squares, p = 16, k = 100, one plane wave, complex128 -- the plain FP64 GPU method).
+"""Benchmark: Helmholtz DD solves/sec at relative residual 1e-10, mixed+batched vs plain FP64.
 
-One step = one complete solve (RHS resident on the device): the RHS pass g = C^ A^-1 b^,
-FGMRES on the dual interface problem to relative residual 1e-10 (every iteration one
-preconditioner application and one interface-operator application: local solves, coarse
-assembly and solve, jump gather), and the recovery of the element solution.
+Headline workload random_eps_64: [0,1]^2, 64 x 64 squares, p = 20 (1,640,961 DoF), k = 400,
+eps_r i.i.d. U[1,2] per element (seed 4), 8 incident plane waves (seed 44) solved as one batch.
+`value` is the mixed-precision batched form: FP64 flexible GMRES on the conforming system with a
+complex64 dual-primal solve as its preconditioner (FP64 coarse solve, residuals and Arnoldi).
+One step = one complete solve of the 8 right-hand sides (resident on the device) to FP64 primal
+relative residual 1e-10.  Beside it, on the same workload and tolerance:
+  plain_fp64    the plain method (everything complex128), same 8 right-hand sides;
+  disk_hanging  the batching workload (4144 leaves with hanging nodes, p ~ U{8..24}, 64 plane
+                waves), both forms at 64 right-hand sides;
+  plane_16x16   the plain FP64 GPU baseline workload (16 x 16, p = 16, k = 100, one plane wave).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -27,9 +32,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Helmholtz DD solves/sec at rel. residual 1e-10; mixed+batched vs plain FP64"
-COMPARE_WORKLOAD = "random_eps_64"
 UNIT = "solves/s"
-WORKLOAD = "plane_16x16"
+WORKLOAD = "random_eps_64"
+TOL = 1e-10
+CPU_SAMPLE_BLOCK = 16           # the oracle times the 16 x 16-element corner of the workload
+# FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA per SM per clock x 2 FLOP
+# x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25; cuBLAS DGEMM measured 1.10 on this GPU)
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 70.0         # FP32 SIMT FMA throughput timed on this GPU
 
 
 def _dist():
@@ -55,20 +65,28 @@ def aggregate_rate(world: int, steps: int, rhs: int, slowest_total_s: float) -> 
     return world * steps * rhs / slowest_total_s
 
 
-def workload_config(R: int, l: int, n_dual: int, n_coarse: int, l2: str, parallelism: str) -> dict:
-    """The `config` object of both arms: the timed workload (16 x 16 squares of degree 16,
-    k = 100, one plane wave) and the sizes the method derives from it."""
-    return {"workload": WORKLOAD, "mesh": "16x16 squares", "p": 16, "k": 100.0, "rhs": R,
-            "l": int(l), "n_dual": int(n_dual), "n_coarse": int(n_coarse),
-            "dof": int((16 * 16 + 1) ** 2), "precision": "fp64", "l2": l2, "parallelism": parallelism}
+def workload_config(world: int) -> dict:
+    """The `config` object of both arms: the timed workload and how it is timed."""
+    return {"workload": WORKLOAD, "mesh": "64x64 squares", "p": 20, "k": 400.0,
+            "eps": "U[1,2] per element, seed 4", "rhs": 8, "angles": "U[0,2pi), seed 44",
+            "dof": (64 * 20 + 1) ** 2, "tol": TOL, "form": "mixed (complex64 inner DD, FP64 outer FGMRES)",
+            "l2": "inputs larger than L2 (231 MB of local vectors) and L2 flushed (256 MB write) between timed steps",
+            "parallelism": f"replicas x{world}"}
 
 
-def _oracle_timing(name: str, n: int, budget: float, threads: int = 1) -> dict:
+def _oracle_timing(name: str, n: int, budget: float, threads: int) -> dict:
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
                MKL_NUM_THREADS=str(threads), CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-m", "oracle.timing", name, str(n), str(budget)],
                          cwd=ROOT, env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_scaled_rate(per_solve_s: float, n_elem_sample: int, n_elem_full: int) -> float:
+    """Solves/s of the full workload from the oracle's time per solve on the corner sample: the
+    oracle's work per iteration grows in proportion to the elements (dense LU solves per
+    element dominate it), so the time is scaled by the element ratio."""
+    return 1.0 / (per_solve_s * n_elem_full / n_elem_sample)
 
 
 class ClockSampler:
@@ -141,119 +159,170 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_work(info, R: int, p: int, nE: float, nT: float, fp64: bool):
-    """Algorithmic FLOPs and HBM bytes per launch of the operator components, Krylov-loop
-    form with explicit edge operators: index 0 pass 1 ([S_E^-1; Y^T] r_E), 2 coarse solve
-    (dense K^-1), 3 pass 2 (x_E - Y u_T); n_E type-1 edge and n_T type-2 slots per element."""
+COMPONENTS = ["pass1", "coarse_assemble", "coarse_solve", "pass2", "jump_gather", "precond"]
+
+
+def component_work(info, R: int, nE: int, nT: int, fp64: bool) -> dict:
+    """Algorithmic FLOPs of the operator components per launch (Krylov-loop form with explicit
+    edge operators; n_E type-1 edge and n_T type-2 slots per element):
+      0 pass 1   [S_E^-1; Y^T] r_E        8 (n_E^2 + n_E n_T) per element and RHS
+      2 coarse   dense K^-1: 8 n_c^2, nested dissection: 8 sum nF (nF + 2 nB), per RHS
+      3 pass 2   x_E - Y u_T              8 n_E n_T per element and RHS
+      5 precond  S^Lap (real) x C1^T v    4 n_E^2 per element and RHS
+    The element components run in the path's element precision, the coarse solve in FP64."""
     E = info.n_elem
-    cb = 16 if fp64 else 8
-    flops_pass1 = E * R * 8 * (nE * nE + nE * nT)
-    bytes_pass1 = E * cb * (nE * nE + nE * nT) + E * R * cb * (2 * nE + nT)
-    flops_pass2 = E * R * 8 * nE * nT
-    bytes_pass2 = E * cb * nE * nT + E * R * cb * (2 * nE + nT)
-    nc = info.n_coarse
-    flops_coarse = 8.0 * nc * nc * R
-    bytes_coarse = 16.0 * nc * nc + 32.0 * nc * R
-    return {0: (flops_pass1, bytes_pass1), 2: (flops_coarse, bytes_coarse), 3: (flops_pass2, bytes_pass2)}
+    coarse = 8.0 * info.n_coarse ** 2 if info.coarse_form == 1 else info.coarse_nd_flops
+    return {0: E * R * 8.0 * (nE * nE + nE * nT), 2: coarse * R, 3: E * R * 8.0 * nE * nT,
+            5: E * R * 4.0 * nE * nE}
 
 
-def _mixed_vs_plain(local: int, stream, steps: int) -> dict:
-    """Mixed precision (complex64 inner DD, FP64 outer FGMRES on the conforming system) against
-    the plain FP64 method on the batched 64x64 workload (p = 20, k = 400, random eps, 8 plane
-    waves), both to the same FP64 primal relative residual 1e-10; CUDA events on the library
-    stream, right-hand sides resident (the 231 MB of local vectors exceed L2)."""
-    import torch
+def roofline(comp_ms, info, R: int, p: int, fp64_elements: bool, coarse_name: str) -> dict:
+    """Roofline of the dominant component (largest time per launch among those with a FLOP
+    count), from live CUDA-event times of ddh_profile_op."""
+    nE = 4 * (p - info.l)
+    nT = 4 + 4 * (info.l - 1)
+    work = component_work(info, R, nE, nT, fp64_elements)
+    dom = max(work, key=lambda i: comp_ms[i])
+    fl = work[dom]
+    t = comp_ms[dom] * 1e-3
+    fp64 = dom == 2 or fp64_elements
+    peak = FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS
+    names = {0: "pass 1 (k_pass1_edge: [S_E^-1; Y^T] r_E)", 2: coarse_name,
+             3: "pass 2 (k_pass2_edge: x_E - Y u_T)", 5: "preconditioner (k_pre_elem_kry + k_pre_rows_kry)"}
+    achieved = fl / t / 1e12
+    return {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 4), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "flops_per_launch": fl,
+            "peak_source": ("FP64 1.25 TFLOP/s derived from 152 SMs x 2 FP64 FMA/clk x 2.07 GHz "
+                            "(cuBLAS DGEMM measured 1.10)") if fp64 else "FP32 SIMT 70 TFLOP/s timed on this GPU",
+            "component_ms": {k: round(float(v), 5) for k, v in zip(COMPONENTS, comp_ms)}}
+
+
+def _context(name, prec, local, stream, **opts):
     import workloads as W
     from paper_1808_04713_gb300 import ddh
-    w = W.WORKLOADS[COMPARE_WORKLOAD]()
-    R = w.n_rhs
-    res = {"workload": COMPARE_WORKLOAD, "rhs": R, "tol": 1e-10, "steps": steps}
-    for name, prec in (("plain_fp64", ddh.PREC_FP64), ("mixed", ddh.PREC_MIXED_FP32)):
-        s = ddh.DDH(local, stream=stream)
-        s.set_mesh(w.base_n, w.leaves, w.p)
-        s.set_coefficients(w.k, w.eps)
-        s.factor(tol=1e-10, precision=prec)
-        with torch.cuda.stream(stream):
-            b = s.rhs_planewave(w.thetas)
-            u = torch.empty_like(b)
-        _, st = s.solve(b, tol=1e-10, out=u)
-        ts = []
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            _, st = s.solve(b, tol=1e-10, out=u)
-            with torch.cuda.stream(stream):
-                e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / 1e3)
-        pr = s.primal_residual(b, u)
-        res[name] = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT,
-                     "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3),
-                     "iterations": max(x.iterations for x in st),
-                     "inner_iterations": max(x.inner_iterations for x in st),
-                     "max_primal_residual": float(max(pr))}
-        s.close()
-    res["mixed_over_plain"] = round(res["mixed"]["value"] / res["plain_fp64"]["value"], 3)
-    return res
-
-
-def run_ours(args):
-    import numpy as np
-    import torch
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_1808_04713_gb300 import build as B
-    B.build()
-    import workloads as W
-    from paper_1808_04713_gb300 import ddh
-    w = W.WORKLOADS[WORKLOAD]()
-    stream = torch.cuda.Stream()
+    w = W.WORKLOADS[name]()
     s = ddh.DDH(local, stream=stream)
     s.set_mesh(w.base_n, w.leaves, w.p)
     s.set_coefficients(w.k, w.eps)
-    s.factor(tol=1e-10)
+    s.factor(tol=TOL, precision=prec, **opts)
+    return w, s
+
+
+def _time_solves(s, b, u, stream, flush, steps: int):
+    """CUDA-event times of `steps` complete solves on the library stream, L2 flushed before each."""
+    import torch
+    ts = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        s.solve(b, tol=TOL, out=u, stats=False)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return ts
+
+
+def _form(name, prec, local, stream, flush, warmup, steps, R=None, **opts):
+    """Solves/s of one form on one workload, with its iteration counts and FP64 primal residual."""
+    import torch
+    from paper_1808_04713_gb300 import ddh
+    w, s = _context(name, prec, local, stream, **opts)
+    R = w.n_rhs if R is None else R
+    with torch.cuda.stream(stream):
+        b = s.rhs_planewave(w.thetas[:R])
+        u = torch.empty_like(b)
+    for _ in range(warmup):
+        s.solve(b, tol=TOL, out=u, stats=False)
+    l0 = s.kernel_launches()
+    ts = _time_solves(s, b, u, stream, flush, steps)
+    launches = (s.kernel_launches() - l0) // max(1, steps)
+    pr = s.primal_residual(b, u)
+    _, st = s.solve(b, tol=TOL, out=u)          # untimed: iteration counts (solves are bit-identical)
+    info = s.info()
+    out = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT, "rhs": R,
+           "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3), "steps": len(ts),
+           "iterations": max(x.iterations for x in st), "inner_iterations": max(x.inner_iterations for x in st),
+           "max_primal_residual": float(max(pr)), "launches_per_step": int(launches),
+           "l": info.l, "n_dual": info.n_dual, "n_coarse": info.n_coarse,
+           "dof_per_s": round(R * len(ts) / sum(ts) * info.n_conforming, 1)}
+    return w, s, b, u, out
+
+
+def _cpu_baseline(n_elem_full: int, iters_full: int) -> dict:
+    """The oracle, as it stands, on the 16 x 16 corner of the workload (same element operators),
+    timed with one BLAS thread and with all host cores; rates scaled to the full workload."""
+    cores = os.cpu_count() or 1
+    runs = {}
+    for th in sorted({1, cores}):
+        o = _oracle_timing(f"{WORKLOAD}@corner{CPU_SAMPLE_BLOCK}", 2, 20.0, threads=th)
+        runs[th] = o
+    best = min(runs, key=lambda th: statistics.mean(runs[th]["solve_s"]))
+    o = runs[best]
+    per = statistics.mean(o["solve_s"])
+    val = oracle_scaled_rate(per, o["n_elem"], n_elem_full)
+    its_s = o["iterations"][0]
+    return {"value": round(val, 6), "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+            "value_iteration_scaled": round(val * its_s / iters_full, 6) if iters_full > 0 else None,
+            "by_threads": {str(th): {"solve_s": round(statistics.mean(r["solve_s"]), 3),
+                                     "setup_s": round(r["setup_s"], 2)} for th, r in runs.items()},
+            "sample": (f"oracle DD solve (FP64, 1 RHS, tol 1e-10) of the {CPU_SAMPLE_BLOCK}x{CPU_SAMPLE_BLOCK}-element "
+                       f"corner of {WORKLOAD} as a problem of its own (same p, k h and eps draws; {o['n_elem']} "
+                       f"elements, {its_s} FGMRES iterations), {len(o['solve_s'])} solves after a "
+                       f"{o['setup_s']:.1f} s setup, {o['threads']} BLAS threads (fastest of 1 and {cores}); "
+                       f"value = 1 / (time per solve x {n_elem_full}/{o['n_elem']} elements); "
+                       f"value_iteration_scaled also scales by the iteration counts ({its_s} for the sample vs "
+                       f"{iters_full} for the GPU's plain FP64 form on the full workload)")}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1808_04713_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1808_04713_gb300 import ddh
+    dev = f"cuda:{local}"
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # ---- headline: mixed + batched on random_eps_64 (8 RHS)
+    w, s = _context(WORKLOAD, ddh.PREC_MIXED_FP32, local, stream)
     info = s.info()
     R = w.n_rhs
     with torch.cuda.stream(stream):
         b = s.rhs_planewave(w.thetas)
         u = torch.empty_like(b)
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     clk = ClockSampler(local).__enter__()        # running before the timed region starts
     for _ in range(args.warmup):
-        _, st = s.solve(b, tol=1e-10, out=u)
+        s.solve(b, tol=TOL, out=u, stats=False)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    times = []
     launches0 = s.kernel_launches()
-    iters = []
     t_start = time.time()
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()                  # evict L2 (256 MB > 129 MB) between steps
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        _, st = s.solve(b, tol=1e-10, out=u)
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        e1.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        iters.append(st[0].iterations)
+    times = _time_solves(s, b, u, stream, flush, args.steps)
     torch.cuda.synchronize()
     clk.mark(t_start, time.time())
     clk.__exit__(None, None, None)
     launches = s.kernel_launches() - launches0
     total = sum(times)
     if ws > 1:
-        total = _max_over_ranks(total, f"cuda:{local}")
+        total = _max_over_ranks(total, dev)
     value = aggregate_rate(ws, args.steps, R, total)
-    # end-to-end through the public API with pinned host buffers
+    pr = s.primal_residual(b, u)
+    _, st = s.solve(b, tol=TOL, out=u)          # untimed: iteration counts
+    # end to end through the public API: host buffers in, host buffers out
     bh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
     uh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
     bh.copy_(b.cpu())
@@ -263,67 +332,80 @@ def run_ours(args):
             flush.zero_()                  # same L2 state as the device-timed steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st_ = s.lib.ddh_solve_host(s.h, bh.data_ptr(), uh.data_ptr(), R, 1e-10, None)
+        st_ = s.lib.ddh_solve_host(s.h, bh.data_ptr(), uh.data_ptr(), R, TOL, None)
         e2e_t.append(time.perf_counter() - t0)
         assert st_ == 0, s.lib.ddh_last_error(s.h)
     e2e_total = sum(e2e_t)
     if ws > 1:
-        e2e_total = _max_over_ranks(e2e_total, f"cuda:{local}")
+        e2e_total = _max_over_ranks(e2e_total, dev)
     e2e_value = aggregate_rate(ws, len(e2e_t), R, e2e_total)
-    # correctness of the timed result
-    pr = s.primal_residual(b, u)
-    # live per-component timing of the operator (CUDA events on the library stream)
-    comp = s.profile_op(R, ddh.PREC_FP64, reps=20)
-    m = s.lib
-    nE = (4 * (w.p[0] - info.l))
-    nT = 4 + 4 * (info.l - 1)
-    work = algorithmic_work(info, R, int(w.p[0]), nE, nT, True)
-    names = {0: "pass1 (edge operators: [S_E^-1; Y^T] r_E)", 2: "coarse solve (dense K^-1 GEMV, FP64)",
-             3: "pass2 (edge operators: x_E - Y u_T)"}
-    dom = max(work, key=lambda i: comp[i])
-    fl, by = work[dom]
-    fp64_peak = 1250.0         # GFLOP/s... expressed in TFLOP/s below
-    achieved_tf = fl / (comp[dom] * 1e-3) / 1e12
-    # dram__bytes_read + dram__bytes_write of one dense-K^-1 GEMV launch (plane_16x16; k_gemv, and
-    # k_gemv1 reads the same 59.09 MB) from the ncu captures summarised in
-    # profiles/launches_plane16x16_fp64.md; unknown for other kernels
-    traffic = 59092224 + 2816 if (dom == 2 and WORKLOAD == "plane_16x16" and R == 1) else None
-    roof = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved_tf, 4),
-            "peak": 1.25, "unit": "TFLOP/s", "frac": round(achieved_tf / 1.25, 4), "traffic": traffic,
-            "algorithmic_bytes": int(by),
-            "peak_source": "fallback: nominal GB300 FP64 1.25 TFLOP/s (measured DGEMM 1.10)",
-            "achieved_hbm_GBs": round(by / (comp[dom] * 1e-3) / 1e9, 1),
-            "component_ms": {"pass1": comp[0], "coarse_assemble": comp[1], "coarse_solve": comp[2],
-                             "pass2": comp[3], "jump_gather": comp[4], "precond": comp[5]}}
+    e2e_same = bool(torch.equal(uh, u.cpu()))     # repeated solves are bit-identical
+    comp = s.profile_op(R, ddh.PREC_MIXED_FP32, reps=10)
+    roof = roofline(comp, info, R, 20, False, "coarse solve (nested dissection, FP64: k_nd_forward/backward levels)")
     clocks = clk.summary()
-    compare = None
-    if not args.no_compare:
-        compare = _mixed_vs_plain(local, stream, 2)
+    s.close()
+    del u, b
+
+    extras = {}
+    if not args.headline_only:
+        # ---- the plain FP64 method on the same workload and tolerance
+        _, sp_, bp, up, plain = _form(WORKLOAD, ddh.PREC_FP64, local, stream, flush, 1, max(3, min(args.steps, 10)))
+        compp = sp_.profile_op(R, ddh.PREC_FP64, reps=10)
+        plain["roofline"] = roofline(compp, sp_.info(), R, 20, True,
+                                     "coarse solve (nested dissection, FP64: k_nd_forward/backward levels)")
+        sp_.close()
+        del bp, up
+        extras["plain_fp64"] = plain
+        # ---- batching workload, both forms at 64 right-hand sides
+        dh = {}
+        for nm, prec in (("mixed", ddh.PREC_MIXED_FP32), ("plain_fp64", ddh.PREC_FP64)):
+            _, sd, bd, ud, res = _form("disk_hanging", prec, local, stream, flush, 1, 2)
+            sd.close()
+            del bd, ud
+            dh[nm] = res
+        dh["mixed_over_plain"] = round(dh["mixed"]["value"] / dh["plain_fp64"]["value"], 3)
+        extras["disk_hanging"] = dh
+        # ---- plain FP64 GPU baseline workload
+        _, s2, b2, u2, c2 = _form("plane_16x16", ddh.PREC_FP64, local, stream, flush, 3, max(3, args.steps))
+        i2 = s2.info()
+        comp2 = s2.profile_op(1, ddh.PREC_FP64, reps=20)
+        c2["roofline"] = roofline(comp2, i2, 1, 16, True, "coarse solve (dense K^-1 GEMV, FP64)")
+        # the same coarse solve measured against the nested-dissection factor's work (the
+        # method's own coarse cost): what the dense GEMV delivers per unit of necessary work
+        c2["roofline"]["coarse_frac_of_nd_work"] = round(i2.coarse_nd_flops / (comp2[2] * 1e-3) / 1e12
+                                                          / FP64_PEAK_TFLOPS, 4)
+        c2["roofline"]["coarse_nd_flops"] = i2.coarse_nd_flops
+        s2.close()
+        del b2, u2
+        extras["plane_16x16"] = c2
+
     out = None
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
-            o = _oracle_timing(WORKLOAD, 6, 20.0, threads=1)
-            per = statistics.mean(o["solve_s"])
-            cpu = {"value": round(1.0 / per, 4), "unit": UNIT, "cores": o["threads"], "kind": "oracle",
-                   "sample": f"oracle DD solve of {WORKLOAD} (1 RHS, tol 1e-10) repeated {len(o['solve_s'])}x "
-                             f"after a {o['setup_s']:.1f}s setup, single BLAS thread; "
-                             f"{o['iterations'][0]} FGMRES iterations"}
+            # the oracle runs the plain dual iteration: scale by the plain FP64 form's count
+            its_plain = extras["plain_fp64"]["iterations"] if "plain_fp64" in extras else 0
+            cpu = _cpu_baseline(info.n_elem, its_plain)
+        mixed_over_plain = (round(value / ws / extras["plain_fp64"]["value"], 3) if "plain_fp64" in extras else None)
         out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 4),
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-               "data": "synthetic plane-wave impedance data (closed form)",
-               "config": workload_config(R, info.l, info.n_dual, info.n_coarse,
-                                         "flushed (256 MB write) between timed steps", f"replicas x{ws}"),
-               "iterations": iters[-1] if iters else None, "primal_residual": float(pr[0]),
-               "dof_per_s": round(value * (16 * 16 + 1) ** 2, 1),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64/c128",
+               "data": "synthetic: seeded eps draws and incident angles, plane-wave impedance data (closed form)",
+               "config": workload_config(ws),
+               "sizes": {"l": info.l, "n_dual": info.n_dual, "n_coarse": info.n_coarse,
+                         "n_local": info.n_local, "coarse_fronts": info.n_coarse_blocks},
+               "iterations": max(x.iterations for x in st),
+               "inner_iterations": max(x.inner_iterations for x in st),
+               "max_primal_residual": float(max(pr)),
+               "dof_per_s": round(value * info.n_conforming, 1),
+               "mixed_over_plain_fp64": mixed_over_plain,
                "e2e": {"value": round(e2e_value, 3), "unit": UNIT,
                        "h2d_bytes_per_step": int(16 * R * info.n_local),
-                       "d2h_bytes_per_step": int(16 * R * info.n_local)},
-               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-               "mixed_vs_plain": compare}
+                       "d2h_bytes_per_step": int(16 * R * info.n_local),
+                       "result_identical_to_device_solve": e2e_same},
+               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+        out.update(extras)
         print(json.dumps(out))
-    s.close()
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -333,20 +415,28 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return
+    import workloads as W
+    n_full = W.WORKLOADS[WORKLOAD]().n_elem
     n = max(1, args.steps + args.warmup)
-    o = _oracle_timing(WORKLOAD, n, 150.0, threads=1)
+    cores = os.cpu_count() or 1
+    o = _oracle_timing(f"{WORKLOAD}@corner{CPU_SAMPLE_BLOCK}", n, 240.0, threads=cores)
     ts = o["solve_s"][min(args.warmup, len(o["solve_s"]) - 1):]
     per = statistics.mean(ts)
-    val = 1.0 / per
-    out = {"impl": "reference", "metric": METRIC, "value": round(val, 5), "unit": UNIT, "n_gpus": ws,
-           "steps": len(ts), "warmup": args.warmup, "ms_per_step": round(1e3 * per, 3),
+    val = oracle_scaled_rate(per, o["n_elem"], n_full)
+    out = {"impl": "reference", "metric": METRIC, "value": round(val, 6), "unit": UNIT, "n_gpus": ws,
+           "steps": len(ts), "warmup": args.warmup, "ms_per_step": round(1e3 * per * n_full / o["n_elem"], 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-           "data": "synthetic plane-wave impedance data (closed form)",
-           "config": workload_config(1, o["l"], o["n_dual"], o["n_coarse"], "host CPU run (no device L2)",
-                                     "oracle on rank 0"),
-           "cpu_baseline": {"value": round(val, 5), "unit": UNIT, "cores": o["threads"], "kind": "oracle",
-                            "sample": f"oracle DD solve of {WORKLOAD}, {len(ts)} timed solves, single BLAS thread"},
-           "e2e": {"value": round(val, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "data": "synthetic: seeded eps draws and incident angles, plane-wave impedance data (closed form)",
+           "config": workload_config(ws),
+           "cpu_baseline": {"value": round(val, 6), "unit": UNIT, "cores": o["threads"], "kind": "oracle",
+                            "sample": (f"each step one oracle DD solve (FP64, 1 RHS, tol 1e-10) of the "
+                                       f"{CPU_SAMPLE_BLOCK}x{CPU_SAMPLE_BLOCK}-element corner of {WORKLOAD} "
+                                       f"({o['n_elem']} elements, same p, k h and eps draws, "
+                                       f"{o['iterations'][0]} FGMRES iterations), {o['threads']} BLAS threads; "
+                                       f"value = 1 / (time per solve x {n_full}/{o['n_elem']} elements); the full "
+                                       f"workload needs more iterations than the sample, so this overstates "
+                                       f"the oracle's rate")},
+           "e2e": {"value": round(val, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
@@ -357,7 +447,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-compare", action="store_true", help="skip the mixed-vs-plain comparison")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the headline form (no plain FP64, disk_hanging or plane_16x16 lines)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

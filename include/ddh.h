@@ -71,9 +71,12 @@ typedef enum { DDH_PRECOND_DIRICHLET = 0, DDH_PRECOND_LUMPED = 1, DDH_PRECOND_NO
 typedef enum { DDH_LOCAL_EDGE = 0, DDH_LOCAL_FDM = 1 } ddh_local_form;
 
 /* How the coarse system K x2 = t of eq. block_matrix_inversion (Sec. 2.3.3) is solved on the
- * device: a dense K^-1 (one GEMV per application) or the nested-dissection multifrontal factor
- * (one launch per tree level).  Both come from the same factorisation. */
-typedef enum { DDH_COARSE_AUTO = 0, DDH_COARSE_DENSE = 1, DDH_COARSE_ND = 2 } ddh_coarse_form;
+ * device: a dense K^-1 (one GEMV per application) or the nested-dissection multifrontal factor,
+ * either in one launch whose CTAs take the fronts' work items in an order that respects the
+ * elimination tree (DDH_COARSE_ND) or with one launch per tree level (DDH_COARSE_ND_LEVELS).
+ * All come from the same factorisation. */
+typedef enum { DDH_COARSE_AUTO = 0, DDH_COARSE_DENSE = 1, DDH_COARSE_ND = 2,
+               DDH_COARSE_ND_LEVELS = 3 } ddh_coarse_form;
 
 typedef struct {
     double tol;            /* relative residual target (default 1e-10) */
@@ -83,7 +86,8 @@ typedef struct {
     int32_t precision;     /* ddh_precision */
     int32_t precond;       /* ddh_precond */
     int32_t inner_iters;   /* mixed precision: at most this many dual FGMRES iterations per
-                              preconditioner application (default 10) */
+                              preconditioner application (default 50; an application normally
+                              stops earlier, at inner_tol) */
     int32_t check_every;   /* host polls convergence every this many iterations (default 4);
                               the first cycle of a solve first runs up to one short of the
                               previous solve's count on this context, then polls after each of
@@ -103,9 +107,10 @@ typedef struct {
                               solves cannot gain much more than 5-6 digits per application */
     int32_t coarse_form;   /* coarse solve K x2 = t (ddh_coarse_form): DDH_COARSE_AUTO (default) applies
                               a dense K^-1 built from the factor when n_coarse <= 6144 and the
-                              nested-dissection solve otherwise; DDH_COARSE_DENSE forces the dense
-                              K^-1 (n_coarse <= 16384, else DDH_ERR_INVALID_ARG); DDH_COARSE_ND forces
-                              the nested-dissection solve at any size */
+                              per-level nested-dissection solve otherwise; DDH_COARSE_DENSE forces
+                              the dense K^-1 (n_coarse <= 16384, else DDH_ERR_INVALID_ARG);
+                              DDH_COARSE_ND and DDH_COARSE_ND_LEVELS force the nested-dissection
+                              solve at any size, in one launch or one launch per tree level */
 } ddh_options;
 
 typedef struct {
@@ -122,7 +127,10 @@ typedef struct {
     double coarse_nd_flops;/* algorithmic real FLOPs per right-hand side of one nested-dissection
                               coarse solve, 8 sum_fronts nF (nF + 2 nB): forward G y_F and backward
                               [W | -H] [y_F; x_B] (reported also when the dense K^-1 is in use) */
-    int32_t coarse_form;   /* form in use: DDH_COARSE_DENSE or DDH_COARSE_ND */
+    int32_t coarse_form;   /* form in use: DDH_COARSE_DENSE, DDH_COARSE_ND or DDH_COARSE_ND_LEVELS */
+    int32_t coarse_subtrees; /* DDH_COARSE_ND_LEVELS: subtrees whose levels run as one launch per
+                                direction when a solve has fewer than 4 right-hand sides (0: every
+                                level is its own launch) */
 } ddh_info;
 
 typedef struct {
@@ -229,6 +237,20 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
  * Same arguments and result as ddh_primal_residual. */
 ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
                                        double* out_host);
+
+/* Apply one of the two operators of the dual iteration to caller-given dual vectors (for
+ * checks of the hot path against a reference; the solves apply the same code):
+ *   which = 0  the interface operator F nu = C^ A^-1 C^T nu (eq. complicated_schur_system,
+ *              applied by the block inversion of eq. block_matrix_inversion: pass 1, coarse
+ *              assembly and solve, pass 2, jump gather);
+ *   which = 1  the preconditioner P^-1 v (eqs. general_preconditioner, weight_matrix, with the
+ *              option's preconditioner kind).
+ * v_dev, out_dev: device complex128 [R][n_dual] (dual rows in the library's order: master edges
+ * in mesh order, then their fine sides, then moments l+1 .. trace degree).  precision selects
+ * the element-level arithmetic (DDH_PREC_FP64 or the complex64 kernels of DDH_PREC_MIXED_FP32);
+ * the coarse solve is FP64 without refinement.  Synchronises the context stream. */
+ddh_status ddh_apply_dual_operator(ddh_ctx* ctx, int32_t which, const void* v_dev, void* out_dev, int32_t R,
+                                   int32_t precision);
 
 /* Time the components of one interface-operator application F = C^ A^-1 C^T and of the
  * preconditioner on the context stream with CUDA events, each launched `reps` times on the

@@ -86,6 +86,9 @@ struct ddh_ctx {
     const int* nd_sub_nodes = nullptr;
     std::vector<int> nd_fwd_off, nd_fwd_n, nd_fwd_rows;   // per level: first item, items, staged rows
     std::vector<int> nd_bwd_off, nd_bwd_n, nd_bwd_rows;
+    std::map<int, std::vector<int>> nd_rb;         // per R: tuned RHS block of each level (fwd, then bwd)
+    NDSched nd_sched;                              // one-launch schedule of the same items
+    bool nd_levels = false;                        // one launch per tree level instead
     bool coarse32 = false;                         // current inner solves use the complex64 copy
     bool refine_coarse = false;                    // one FP64 refinement step per coarse solve
     bool refine_active = false;                    // refinement used by the current solves
@@ -161,6 +164,9 @@ static void free_model(ddh_ctx* ctx) {
     ctx->nd_sub_ptr = ctx->nd_sub_nodes = nullptr;
     ctx->nd_fwd_off.clear(); ctx->nd_fwd_n.clear(); ctx->nd_fwd_rows.clear();
     ctx->nd_bwd_off.clear(); ctx->nd_bwd_n.clear(); ctx->nd_bwd_rows.clear();
+    ctx->nd_sched = NDSched();
+    ctx->nd_levels = false;
+    ctx->nd_rb.clear();
     ctx->kc_ptr = ctx->kc_col = nullptr;
     ctx->kc_val = nullptr;
     ctx->gx = ctx->gw = nullptr;
@@ -589,6 +595,49 @@ static ddh_status upload_model(ddh_ctx* ctx) {
                 if ((st = upload(ctx, sn, &ctx->nd_sub_nodes))) return st;
             }
         }
+        // one-launch schedule: forward items deepest level first, then backward items root
+        // level first (w bit 1), with per-node children, item counts and backward dependency
+        {
+            std::vector<int4> seq;
+            std::vector<int> kid(2 * (size_t)nn, -1), nfi(nn, 0), nbi(nn, 0), bdep(nn, -1);
+            for (int lv = L - 1; lv >= 0; --lv)
+                for (int i = 0; i < ctx->nd_fwd_n[lv]; ++i) {
+                    const int4 it = items[ctx->nd_fwd_off[lv] + i];
+                    seq.push_back(it);
+                    nfi[it.x]++;
+                }
+            for (int lv = 0; lv < L; ++lv)
+                for (int i = 0; i < ctx->nd_bwd_n[lv]; ++i) {
+                    int4 it = items[ctx->nd_bwd_off[lv] + i];
+                    it.w |= 2;
+                    seq.push_back(it);
+                    nbi[it.x]++;
+                }
+            for (int id = 0; id < nn; ++id) {
+                const int pa = m.cnode[id].parent;
+                if (pa >= 0) {
+                    if (kid[2 * (size_t)pa] < 0) kid[2 * (size_t)pa] = id;
+                    else if (kid[2 * (size_t)pa + 1] < 0) kid[2 * (size_t)pa + 1] = id;
+                    else return fail(ctx, DDH_ERR_INVALID_ARG, "coarse tree node with more than two children");
+                }
+                int a = pa;
+                while (a >= 0 && nbi[a] == 0) a = m.cnode[a].parent;
+                bdep[id] = a;
+            }
+            NDSched& S = ctx->nd_sched;
+            S.nseq = (int)seq.size();
+            S.nn = nn;
+            S.smem_rows = 0;
+            for (int lv = 0; lv < L; ++lv)
+                S.smem_rows = std::max(S.smem_rows, std::max(ctx->nd_fwd_rows[lv], ctx->nd_bwd_rows[lv]));
+            if (seq.empty()) seq.push_back(make_int4(0, 0, 0, 0));
+            if ((st = upload(ctx, seq, &S.seq))) return st;
+            if ((st = upload(ctx, kid, &S.kid))) return st;
+            if ((st = upload(ctx, bdep, &S.bdep))) return st;
+            if ((st = upload(ctx, nfi, &S.nfi))) return st;
+            if ((st = upload(ctx, nbi, &S.nbi))) return st;
+            ctx->nd_levels = ctx->opt.coarse_form != DDH_COARSE_ND;   // AUTO: one launch per level
+        }
         NDDev& D = ctx->nd64;
         D.nc = nc;
         D.u_len = std::max<int64_t>(1, ul);
@@ -659,6 +708,59 @@ struct Work {
     void* outE; double2* vd; double2* mvec;
 };
 
+// Per-level autotuner of the nested-dissection solve: for R right-hand sides, time every level
+// launch (forward and backward) with each admissible RHS block (8, 4, 2, 1 right-hand sides per
+// CTA) and keep the fastest.  A level of few large fronts runs faster with small blocks (more
+// CTAs), a level of many small fronts with large ones (each staged vector serves more
+// right-hand sides).  Runs once per R, before any graph capture, on the work buffers (cleared).
+static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
+    if (ctx->Kinv || !ctx->nd_levels || ctx->nd_rb.count(R)) return DDH_OK;
+    const int L = (int)ctx->nd_fwd_rows.size();
+    const int nc = ctx->dm.n_coarse;
+    const bool subs = ctx->nd_nsub > 0 && R < 4;
+    const int cut = subs ? std::min(L, ctx->nd_cut) : L;
+    cudaStream_t s = ctx->stream;
+    double2* y = w.ctmp;
+    double2* u = (double2*)ctx->nd_u;
+    CK(cudaMemsetAsync(w.t, 0, sizeof(double2) * (size_t)R * nc, s));
+    CK(cudaMemsetAsync(w.x2, 0, sizeof(double2) * (size_t)R * nc, s));
+    CK(cudaMemsetAsync(y, 0, sizeof(double2) * (size_t)R * nc, s));
+    CK(cudaMemsetAsync(u, 0, sizeof(double2) * (size_t)R * ctx->nd64.u_len, s));
+    std::vector<int> best(2 * (size_t)L, 0);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int dir = 0; dir < 2; ++dir)
+        for (int lv = 0; lv < cut; ++lv) {
+            const int n = dir ? ctx->nd_bwd_n[lv] : ctx->nd_fwd_n[lv];
+            const int rows = dir ? ctx->nd_bwd_rows[lv] : ctx->nd_fwd_rows[lv];
+            if (!n) continue;
+            const int rb_max = nd_rhs_block(rows, R);
+            float tbest = 1e30f;
+            for (int rb = rb_max; rb >= 1; rb >>= 1) {
+                auto run = [&] {
+                    if (dir) launch_nd_backward(ctx->nd64, false, ctx->nd_items + ctx->nd_bwd_off[lv], n, rows, y, w.x2, R,
+                                                nullptr, s, rb);
+                    else launch_nd_forward(ctx->nd64, false, ctx->nd_items + ctx->nd_fwd_off[lv], n, rows, w.t, y, u, R,
+                                           nullptr, s, rb);
+                };
+                run();
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) run();
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < 0.97f * tbest) { tbest = ms; best[(size_t)dir * L + lv] = rb; }
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    ctx->nd_rb[R] = best;
+    return DDH_OK;
+}
+
 static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     const DevModel& d = ctx->dm;
     const size_t es = fp64 ? sizeof(double2) : sizeof(float2);
@@ -678,12 +780,14 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     if (!ctx->Kinv) {
         if ((st = get_work(ctx, "ndu", sizeof(double2) * (size_t)R * ctx->nd64.u_len, &p))) return st;
         ctx->nd_u = p;
+        if ((st = get_work(ctx, "ndstate", sizeof(int) * nd_state_ints(ctx->nd_sched, R), &p))) return st;
+        ctx->nd_sched.state = (int*)p;
     }
     if ((st = get_work(ctx, "vd", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.vd = (double2*)p;
     if ((st = get_work(ctx, "mvec", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.mvec = (double2*)p;
-    return DDH_OK;
+    return nd_tune(ctx, w, R);
 }
 
 // x2 = K^-1 t (vectors FP64; t is left intact).  The factor is complex128, or its complex64
@@ -722,11 +826,18 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
     const NDDev& D = f32nd ? ctx->nd32 : ctx->nd64;
     double2* y = tmp;
     double2* u = (double2*)ctx->nd_u;
+    if (!ctx->nd_levels) {
+        launch_nd_persistent(D, ctx->nd_sched, f32nd, t, y, x2, u, R, done, ctx->dm.err, s);
+        ctx->launches++;
+        return;
+    }
     const int L = (int)ctx->nd_fwd_rows.size();
     // subtree launches pay off when the launches are latency-bound (few right-hand sides); with
     // more right-hand sides the serial node chain inside a subtree costs more than it saves
     const bool subs = ctx->nd_nsub > 0 && R < 4;
     const int cut = subs ? std::min(L, ctx->nd_cut) : L;
+    const auto tuned = ctx->nd_rb.find(R);
+    const std::vector<int>* rbs = tuned != ctx->nd_rb.end() ? &tuned->second : nullptr;
     if (subs) {
         launch_nd_subtrees(true, D, f32nd, ctx->nd_sub_ptr, ctx->nd_sub_nodes, ctx->nd_nsub, ctx->nd_sub_fwd_rows, t, y,
                            u, R, done, s);
@@ -735,13 +846,13 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
     for (int lv = cut - 1; lv >= 0; --lv) {
         if (!ctx->nd_fwd_n[lv]) continue;
         launch_nd_forward(D, f32nd, ctx->nd_items + ctx->nd_fwd_off[lv], ctx->nd_fwd_n[lv], ctx->nd_fwd_rows[lv], t, y, u,
-                          R, done, s);
+                          R, done, s, rbs ? (*rbs)[lv] : 0);
         ctx->launches++;
     }
     for (int lv = 0; lv < cut; ++lv) {
         if (!ctx->nd_bwd_n[lv]) continue;
         launch_nd_backward(D, f32nd, ctx->nd_items + ctx->nd_bwd_off[lv], ctx->nd_bwd_n[lv], ctx->nd_bwd_rows[lv], y, x2,
-                           R, done, s);
+                           R, done, s, rbs ? (*rbs)[L + lv] : 0);
         ctx->launches++;
     }
     if (subs) {
@@ -1267,7 +1378,8 @@ static ddh_status solve_mixed(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
         std::vector<double> res_in;
         ctx->coarse32 = ctx->opt.coarse_fp32 != 0;
         ddh_status st2 = dd_solve_tilde<float>(ctx, (const double2*)bin, (double2*)phin, R,
-                                               std::max(0.0, ctx->opt.inner_tol), m_in, m_in, m_in, its_in, res_in);
+                                               std::max(0.0, ctx->opt.inner_tol), m_in, m_in,
+                                               std::min(m_in, ctx->opt.check_every), its_in, res_in);
         ctx->coarse32 = false;
         if (st2) return st2;
         launch_readback(d, (const double2*)phin, out, R, s);
@@ -1301,7 +1413,7 @@ void ddh_default_options(ddh_options* o) {
     o->l_override = 0;
     o->precision = DDH_PREC_FP64;
     o->precond = DDH_PRECOND_DIRICHLET;
-    o->inner_iters = 10;
+    o->inner_iters = 50;
     o->check_every = 4;
     o->use_graph = 1;
     o->coarse_fp32 = 0;
@@ -1362,8 +1474,8 @@ ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (ctx->opt.local_form != DDH_LOCAL_EDGE && ctx->opt.local_form != DDH_LOCAL_FDM)
         return fail(ctx, DDH_ERR_INVALID_ARG, "local_form must be DDH_LOCAL_EDGE or DDH_LOCAL_FDM");
     if (ctx->opt.check_every < 1) ctx->opt.check_every = 1;
-    if (ctx->opt.coarse_form < DDH_COARSE_AUTO || ctx->opt.coarse_form > DDH_COARSE_ND)
-        return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form must be DDH_COARSE_AUTO, DDH_COARSE_DENSE or DDH_COARSE_ND");
+    if (ctx->opt.coarse_form < DDH_COARSE_AUTO || ctx->opt.coarse_form > DDH_COARSE_ND_LEVELS)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form must be one of the ddh_coarse_form values");
     const auto t0 = std::chrono::steady_clock::now();
     cudaSetDevice(ctx->device);
     std::string err;
@@ -1404,7 +1516,8 @@ ddh_status ddh_get_info(const ddh_ctx* ctx, ddh_info* out) {
     double fl = 0;
     for (const auto& N : m.cnode) fl += 8.0 * N.nF * ((double)N.nF + 2.0 * (double)N.B.size());
     out->coarse_nd_flops = fl;
-    out->coarse_form = m.dense_coarse ? DDH_COARSE_DENSE : DDH_COARSE_ND;
+    out->coarse_form = m.dense_coarse ? DDH_COARSE_DENSE : (ctx->nd_levels ? DDH_COARSE_ND_LEVELS : DDH_COARSE_ND);
+    out->coarse_subtrees = m.dense_coarse ? 0 : ctx->nd_nsub;
     return DDH_OK;
 }
 
@@ -1583,6 +1696,32 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
     std::vector<double> out;
     if ((st = primal_residual_dev(ctx, (const double2*)bt, (const double2*)pt, R, out))) return st;
     for (int i = 0; i < R; ++i) out_host[i] = out[i];
+    return DDH_OK;
+}
+
+ddh_status ddh_apply_dual_operator(ddh_ctx* ctx, int32_t which, const void* v_dev, void* out_dev, int32_t R,
+                                   int32_t precision) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!v_dev || !out_dev || R <= 0 || (which != 0 && which != 1) ||
+        (precision != DDH_PREC_FP64 && precision != DDH_PREC_MIXED_FP32))
+        return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->dm.n_dual == 0) return DDH_OK;
+    const bool fp64 = precision == DDH_PREC_FP64;
+    Work w;
+    ddh_status st;
+    if ((st = get_op_work(ctx, R, fp64, w))) return st;
+    const double2* v = (const double2*)v_dev;
+    double2* out = (double2*)out_dev;
+    if (which == 0) {
+        if (fp64) apply_op<double>(ctx, w, v, 1.0, nullptr, 0, out, nullptr, R, nullptr);
+        else apply_op<float>(ctx, w, v, 1.0, nullptr, 0, out, nullptr, R, nullptr);
+    } else {
+        if (fp64) apply_prec<double>(ctx, w, v, out, R, nullptr);
+        else apply_prec<float>(ctx, w, v, out, R, nullptr);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
     return DDH_OK;
 }
 

@@ -264,7 +264,7 @@ bool coarse_factor(Model& m, const std::vector<int32_t>& kn_ptr, const std::vect
     }
     m.coarse_refine = m.coarse_check > 1e-12;
     // ---- dense inverse for small coarse problems (elimination order), refined like the solves
-    m.dense_coarse = m.coarse_form == 1 || (m.coarse_form == 0 && nc <= 6144);
+    m.dense_coarse = m.coarse_form == 1 || (m.coarse_form == 0 && nc <= 6144);   // 2, 3: nested dissection
     m.Kinv.clear();
     if (m.dense_coarse) {
         m.Kinv.assign((size_t)nc * nc, cd(0));

@@ -166,11 +166,16 @@ template <class MT> struct NDType { using T = double; };
 template <> struct NDType<float2> { using T = float; };
 __device__ __forceinline__ cpx<double> ld_mat(const double2* a) { const double2 v = __ldg(a); return mk<double>(v.x, v.y); }
 __device__ __forceinline__ cpx<float> ld_mat(const float2* a) { const float2 v = __ldg(a); return mk<float>(v.x, v.y); }
+// Loads of vectors written during the same launch by other CTAs (the one-launch schedule) go
+// through L2 (ld.global.cg): another SM's L1 may hold a stale copy of the line.
+template <bool CG>
+__device__ __forceinline__ double2 ldv(const double2* p) { return CG ? __ldcg(p) : *p; }
+template <bool CG>
 __device__ __forceinline__ double2 nd_pull(const double2* u, int64_t base, const int64_t* src, int64_t i) {
     const int64_t a = src[2 * i], b = src[2 * i + 1];
     double2 s = make_double2(0.0, 0.0);
-    if (a >= 0) { const double2 v = u[base + a]; s.x += v.x; s.y += v.y; }
-    if (b >= 0) { const double2 v = u[base + b]; s.x += v.x; s.y += v.y; }
+    if (a >= 0) { const double2 v = ldv<CG>(u + base + a); s.x += v.x; s.y += v.y; }
+    if (b >= 0) { const double2 v = ldv<CG>(u + base + b); s.x += v.x; s.y += v.y; }
     return s;
 }
 template <class T>
@@ -182,7 +187,7 @@ __device__ __forceinline__ void cfma(T& ax, T& ay, cpx<T> a, cpx<T> v) {
 // One node's share of a forward level: stage y_F = t_F - w_F (w = the children's amounts),
 // write y_F when asked, then u_N[row] = w_B[row] + (G_N y_F)[row] for rows [row0, row0+nrows).
 // Called by every thread of the CTA; ends without a trailing barrier.
-template <class MT, int RB>
+template <class MT, int RB, bool CG = false>
 __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int row0, int nrows, bool shortm,
                                                 bool write_y, const double2* __restrict__ t, double2* __restrict__ y,
                                                 double2* __restrict__ u, int r0, int nr,
@@ -195,7 +200,7 @@ __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int ro
         for (int r = 0; r < RB; ++r) {
             double2 v = make_double2(0.0, 0.0);
             if (r < nr) {
-                const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + i);
+                const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + i);
                 v = t[(r0 + r) * nc + pos];
                 v.x -= w.x; v.y -= w.y;
                 if (write_y) y[(r0 + r) * nc + pos] = v;
@@ -222,7 +227,7 @@ __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int ro
                 ay += __shfl_xor_sync(0xffffffffu, ay, o);
             }
             if (ok && s == 0 && r < nr) {
-                const double2 w = nd_pull(u, (r0 + r) * ul, d.src, so + nF + row);
+                const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + nF + row);
                 u[(r0 + r) * ul + uo + row] = make_double2(w.x + (double)ax, w.y + (double)ay);
             }
         }
@@ -250,14 +255,14 @@ __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int ro
 #pragma unroll
             for (int r = 0; r < RB; ++r)
                 if (r == lane) { sx = ax[r]; sy = ay[r]; }
-            const double2 w = nd_pull(u, (r0 + lane) * ul, d.src, so + nF + row);
+            const double2 w = nd_pull<CG>(u, (r0 + lane) * ul, d.src, so + nF + row);
             u[(r0 + lane) * ul + uo + row] = make_double2(w.x + (double)sx, w.y + (double)sy);
         }
     }
 }
 
 // One node's share of a backward level: x_F[rows] = ([W | -H] [y_F; x_B])[rows]
-template <class MT, int RB>
+template <class MT, int RB, bool CG = false>
 __device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int row0, int nrows, bool shortm,
                                                  const double2* __restrict__ y, double2* __restrict__ x, int r0,
                                                  int nr, cpx<typename NDType<MT>::T>* nd_sm) {
@@ -269,7 +274,7 @@ __device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int r
         const int pos = i < nF ? f0 + i : bi[i - nF];
         const double2* src = i < nF ? y : x;
         for (int r = 0; r < RB; ++r) {
-            const double2 v = r < nr ? src[(r0 + r) * nc + pos] : make_double2(0.0, 0.0);
+            const double2 v = r < nr ? ldv<CG>(src + (r0 + r) * nc + pos) : make_double2(0.0, 0.0);
             nd_sm[r * sn + i] = mk<T>((T)v.x, (T)v.y);
         }
     }
@@ -384,6 +389,77 @@ __global__ void __launch_bounds__(128) k_nd_backward_sub(NDDev d, const int* __r
     }
 }
 
+// ---- the whole solve in one launch (see NDSched): items in dependency-safe ticket order
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Bounded wait (one thread) until *cnt >= target.  Gives up when another CTA has aborted or
+// after about a second, raising the abort flag; returns whether the dependency is met.
+__device__ __forceinline__ bool nd_wait(const int* cnt, int target, int* abort_f) {
+    if (target <= 0) return true;
+    for (int it = 0; it < (1 << 21); ++it) {
+        if (ld_acquire_gpu(cnt) >= target) return true;
+        if (ld_acquire_gpu(abort_f)) return false;
+        if (it > 32) __nanosleep(256);
+    }
+    atomicExch(abort_f, 1);
+    return false;
+}
+
+template <class MT, int RB>
+__global__ void __launch_bounds__(128) k_nd_persistent(NDDev d, NDSched sc, const double2* __restrict__ t,
+                                                       double2* y, double2* x, double2* u, int R,
+                                                       const int* __restrict__ done, int* err) {
+    using T = typename NDType<MT>::T;
+    if (done && *done) return;
+    extern __shared__ __align__(16) char nd_raw[];
+    __shared__ int s_ticket, s_ok;
+    const int nrb = (R + RB - 1) / RB;
+    const int total = sc.nseq * nrb;
+    int* ticket = sc.state;
+    int* abort_f = sc.state + 1;
+    int* fcnt = sc.state + 2;                       // [nn][nrb] finished forward items
+    int* bcnt = fcnt + (size_t)sc.nn * nrb;         // [nn][nrb] finished backward items
+    cpx<T>* sm = reinterpret_cast<cpx<T>*>(nd_raw);
+    while (true) {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int tk = s_ticket;
+        if (tk >= total) return;
+        const int4 it = sc.seq[tk / nrb];
+        const int rb = tk % nrb, node = it.x;
+        const bool bwd = (it.w & 2) != 0, shortm = (it.w & 1) != 0;
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            if (!bwd) {
+                for (int c = 0; c < 2 && ok; ++c) {
+                    const int k = sc.kid[2 * node + c];
+                    if (k >= 0) ok = nd_wait(fcnt + (size_t)k * nrb + rb, sc.nfi[k], abort_f);
+                }
+            } else {
+                ok = nd_wait(fcnt + (size_t)node * nrb + rb, sc.nfi[node], abort_f);
+                const int a = sc.bdep[node];
+                if (ok && a >= 0) ok = nd_wait(bcnt + (size_t)a * nrb + rb, sc.nbi[a], abort_f);
+            }
+            if (!ok && err) atomicExch(err, 3);
+            __threadfence();
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int r0 = rb * RB, nr = min(RB, R - r0);
+        if (!bwd) nd_forward_node<MT, RB, true>(d, node, it.y, it.z, shortm, it.y == 0, t, y, u, r0, nr, sm);
+        else nd_backward_node<MT, RB, true>(d, node, it.y, it.z, shortm, y, x, r0, nr, sm);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd((bwd ? bcnt : fcnt) + (size_t)node * nrb + rb, 1);
+        }
+    }
+}
+
 // r = t - K x with K in CSR (one warp per row, lanes across the row's entries, up to 8
 // right-hand sides per pass so each matrix entry is loaded once per 8)
 __global__ void k_csr_residual(const int* __restrict__ ptr, const int* __restrict__ col,
@@ -440,6 +516,7 @@ static void nd_attr() {
     cudaFuncSetAttribute(k_nd_backward<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
     cudaFuncSetAttribute(k_nd_forward_sub<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
     cudaFuncSetAttribute(k_nd_backward_sub<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
+    cudaFuncSetAttribute(k_nd_persistent<MT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, kNDSmemMax);
 }
 void nd_set_smem_limits() {
     nd_attr<double2, 1>(); nd_attr<double2, 2>(); nd_attr<double2, 4>(); nd_attr<double2, 8>();
@@ -458,9 +535,10 @@ static void nd_bwd_t(const NDDev& d, const int4* items, int nitems, int smem_row
     k_nd_backward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, y, x, R, done);
 }
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
-                       double2* y, double2* u, int R, const int* done, cudaStream_t st) {
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want) {
     if (nitems <= 0) return;
-    const int rb = nd_rhs_block(smem_rows, R);
+    const int rb_max = nd_rhs_block(smem_rows, R);
+    const int rb = rb_want > 0 && rb_want <= rb_max ? rb_want : rb_max;
 #define ND_F(RBV)                                                                             \
     if (f32) nd_fwd_t<float2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);        \
     else nd_fwd_t<double2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);
@@ -473,9 +551,10 @@ void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, 
 #undef ND_F
 }
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
-                        double2* x, int R, const int* done, cudaStream_t st) {
+                        double2* x, int R, const int* done, cudaStream_t st, int rb_want) {
     if (nitems <= 0) return;
-    const int rb = nd_rhs_block(smem_rows, R);
+    const int rb_max = nd_rhs_block(smem_rows, R);
+    const int rb = rb_want > 0 && rb_want <= rb_max ? rb_want : rb_max;
 #define ND_B(RBV)                                                                          \
     if (f32) nd_bwd_t<float2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);        \
     else nd_bwd_t<double2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);
@@ -510,6 +589,38 @@ void launch_nd_subtrees(bool forward, const NDDev& d, bool f32, const int* sub_p
         default: ND_S(1)
     }
 #undef ND_S
+}
+size_t nd_state_ints(const NDSched& s, int R) {
+    const int rb = nd_rhs_block(s.smem_rows, R);
+    return 2 + 2 * (size_t)s.nn * ((R + rb - 1) / rb);
+}
+template <class MT, int RB>
+static void nd_persist_t(const NDDev& d, const NDSched& s, const double2* t, double2* y, double2* x, double2* u,
+                         int R, const int* done, int* err, cudaStream_t st) {
+    const size_t sm = std::max<size_t>(16, (size_t)(s.smem_rows | 1) * RB * sizeof(MT));
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_nd_persistent<MT, RB>, 128, sm);
+    const int nrb = (R + RB - 1) / RB;
+    const int grid = std::max(1, std::min(std::max(1, per) * std::max(1, nsm), s.nseq * nrb));
+    cudaMemsetAsync(s.state, 0, sizeof(int) * nd_state_ints(s, R), st);
+    k_nd_persistent<MT, RB><<<grid, 128, sm, st>>>(d, s, t, y, x, u, R, done, err);
+}
+void launch_nd_persistent(const NDDev& d, const NDSched& s, bool f32, const double2* t, double2* y, double2* x,
+                          double2* u, int R, const int* done, int* err, cudaStream_t st) {
+    if (s.nseq <= 0) return;
+    const int rb = nd_rhs_block(s.smem_rows, R);
+#define ND_P(RBV)                                                                   \
+    if (f32) nd_persist_t<float2, RBV>(d, s, t, y, x, u, R, done, err, st);         \
+    else nd_persist_t<double2, RBV>(d, s, t, y, x, u, R, done, err, st);
+    switch (rb) {
+        case 8: ND_P(8) break;
+        case 4: ND_P(4) break;
+        case 2: ND_P(2) break;
+        default: ND_P(1)
+    }
+#undef ND_P
 }
 void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,
                          const double2* t, double2* r, int R, const int* done, cudaStream_t st) {

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
     // o >= nE reads Y (row-major nE x nT, i.e. Y^T column-major); tpr threads per output row
     const cpx<T>* Ye = Y + dm.pq_off[e];
     const int no = nE + nT;
-    const int tpr = no <= 64 ? 4 : (no <= 128 ? 2 : 1);       // 256 threads
+    // every vertex and edge slot is type-1 edge or type-2, so no = 4p <= 128 (p <= 32)
+    const int tpr = no <= 64 ? 4 : 2;                           // 256 threads
     const int chunk = (nE + tpr - 1) / tpr;
     for (int base = 0; base < no * tpr; base += blockDim.x) {
         const int slot = base + threadIdx.x;

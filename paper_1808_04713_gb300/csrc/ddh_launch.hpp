@@ -77,10 +77,13 @@ struct NDDev {
 // entries stores that matrix column-major, and its items have up to 16 rows (8 lanes per
 // row, split over right-hand sides and column slices).
 constexpr int kNDShortRow = 128;
+// rb_want: right-hand sides per CTA (1, 2, 4 or 8; 0 or larger than nd_rhs_block allows: the
+// largest allowed).  Smaller blocks put more CTAs on a level of few, large fronts.
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
-                       double2* y, double2* u, int R, const int* done, cudaStream_t st);
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want = 0);
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
-                        double2* x, int R, const int* done, cudaStream_t st);
+                        double2* x, int R, const int* done, cudaStream_t st, int rb_want = 0);
+// largest right-hand-side block whose staged vectors fit in shared memory (and below 2 R)
 int nd_rhs_block(int smem_rows, int R);
 // the levels below a cut in one launch: CTA b walks the subtree nodes
 // sub_nodes[sub_ptr[b] .. sub_ptr[b+1]) (postorder), forward (in = t, out = y, u) or backward
@@ -88,6 +91,32 @@ int nd_rhs_block(int smem_rows, int R);
 void launch_nd_subtrees(bool forward, const NDDev& d, bool f32, const int* sub_ptr, const int* sub_nodes, int nsub,
                         int smem_rows, const double2* in, double2* out, double2* u, int R, const int* done,
                         cudaStream_t st);
+// The whole nested-dissection solve in one launch, scheduled by dependencies instead of by
+// tree level.  seq lists every forward item (deepest level first) and then every backward item
+// (root level first); .w bit 0 = short-row form, bit 1 = backward.  CTAs take (item, RHS block)
+// pairs in ticket order.  A forward item of node N waits until every forward item of N's
+// children is done; a backward item waits until N's own forward items are done and, when N has
+// an ancestor with backward items, until the nearest such ancestor's backward items are done.
+// Every wait points to smaller tickets, and a ticket is only ever held by a running CTA, so the
+// smallest unfinished ticket can always proceed.  Waits are bounded: on time-out the CTA sets
+// the abort flag and the error word, and every CTA leaves.  state holds the ticket counter,
+// the abort flag and per (node, RHS block) counters of finished forward and backward items; it
+// is cleared by the launcher before each solve.
+struct NDSched {
+    const int4* seq = nullptr;
+    int nseq = 0;
+    int nn = 0;
+    const int* kid = nullptr;       // [2 nn] children, -1 when absent
+    const int* bdep = nullptr;      // [nn] nearest ancestor with backward items, -1 when none
+    const int* nfi = nullptr;       // [nn] forward items per node
+    const int* nbi = nullptr;       // [nn] backward items per node
+    int* state = nullptr;           // 2 + 2 nn ceil(R / RB) ints (work buffer)
+    int smem_rows = 0;              // largest staged vector over all items
+};
+void launch_nd_persistent(const NDDev& d, const NDSched& s, bool f32, const double2* t, double2* y, double2* x,
+                          double2* u, int R, const int* done, int* err, cudaStream_t st);
+// ints of NDSched::state needed for R right-hand sides
+size_t nd_state_ints(const NDSched& s, int R);
 void nd_set_smem_limits();   // once per device before the first (captured) launch
 // r = t - K x, K in CSR (R right-hand sides, [R][n])
 void launch_csr_residual(const int* ptr, const int* col, const double2* val, int n, const double2* x,

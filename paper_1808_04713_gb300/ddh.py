@@ -19,7 +19,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_READY, ERR_NO_CONVERGENCE, ERR_S
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
 LOCAL_EDGE, LOCAL_FDM = 0, 1
-COARSE_AUTO, COARSE_DENSE, COARSE_ND = 0, 1, 2
+COARSE_AUTO, COARSE_DENSE, COARSE_ND, COARSE_ND_LEVELS = 0, 1, 2, 3
 
 
 class DDHError(RuntimeError):
@@ -41,7 +41,7 @@ class Info(C.Structure):
                 ("n_dual", C.c_int64), ("n_coarse", C.c_int64), ("n_conforming", C.c_int64),
                 ("n_coarse_blocks", C.c_int32), ("max_block", C.c_int32),
                 ("min_resonance_gap", C.c_double), ("factor_seconds", C.c_double),
-                ("coarse_nd_flops", C.c_double), ("coarse_form", C.c_int32)]
+                ("coarse_nd_flops", C.c_double), ("coarse_form", C.c_int32), ("coarse_subtrees", C.c_int32)]
 
 
 class RhsStats(C.Structure):
@@ -66,6 +66,7 @@ _SIGS = {
     "ddh_grad_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_primal_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_primal_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ddh_apply_dual_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
     "ddh_profile_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "ddh_last_error": (C.c_char_p, [C.c_void_p]),
@@ -240,6 +241,14 @@ class DDH:
         R = b.shape[0]
         out = np.zeros(R)
         self._check(self.lib.ddh_primal_residual(self.h, _ptr(b.contiguous()), _ptr(u.contiguous()), R, out.ctypes.data))
+        return out
+
+    def apply_dual_operator(self, which: int, v, precision: int = PREC_FP64):
+        """F v (which = 0) or P^-1 v (which = 1) for dual vectors v [R, n_dual] (complex128)."""
+        v = v.contiguous()
+        out = self.torch.zeros_like(v)
+        self._check(self.lib.ddh_apply_dual_operator(self.h, int(which), _ptr(v), _ptr(out), int(v.shape[0]),
+                                                     int(precision)))
         return out
 
     def profile_op(self, R: int, precision: int = PREC_FP64, reps: int = 20) -> np.ndarray:

@@ -1,11 +1,13 @@
 """Time the components of one interface-operator application on a named workload.
 
-    python -m paper_1808_04713_gb300.profile_op <workload> [R] [fp64|mixed] [reps]
+    python -m paper_1808_04713_gb300.profile_op <workload> [R] [fp64|mixed] [reps] [solves]
 
 Factors the workload, runs one solve with R right-hand sides (which sizes the work buffers
 and captures the iteration graph), then prints the average milliseconds per application of
 pass 1, coarse assembly, coarse solve, pass 2, jump gather and preconditioner, each timed with
-CUDA events on the library stream (ddh_profile_op).  A short fixed command for profilers.
+CUDA events on the library stream (ddh_profile_op).  With `solves` > 0 it then runs that
+many more complete solves (for launch lists of a whole solve).  A short fixed command for
+profilers.
 """
 from __future__ import annotations
 
@@ -27,6 +29,7 @@ def main(argv=None) -> None:
     R = int(argv[1]) if len(argv) > 1 else w.n_rhs
     prec = ddh.PREC_MIXED_FP32 if len(argv) > 2 and argv[2] == "mixed" else ddh.PREC_FP64
     reps = int(argv[3]) if len(argv) > 3 else 3
+    solves = int(argv[4]) if len(argv) > 4 else 0
     s = ddh.DDH(0)
     s.set_mesh(w.base_n, w.leaves, w.p)
     s.set_coefficients(w.k, w.eps)
@@ -36,6 +39,9 @@ def main(argv=None) -> None:
     torch.cuda.synchronize()
     ms = s.profile_op(R, 0 if prec == ddh.PREC_FP64 else 1, reps)
     info = s.info()
+    for _ in range(solves):
+        _, st = s.solve(b, tol=1e-10, allow_noconv=True)
+    torch.cuda.synchronize()
     keys = ["pass1", "coarse_assemble", "coarse_solve", "pass2", "jump_gather", "precond"]
     print(json.dumps({"workload": name, "rhs": R, "precision": "fp64" if prec == ddh.PREC_FP64 else "mixed",
                       "iterations": max(x.iterations for x in st), "coarse_fronts": info.n_coarse_blocks,

@@ -14,14 +14,15 @@ import bench  # noqa: E402
 def test_reference_arm_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
-                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600, check=True)
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=900, check=True)
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
     assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
     assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-    cfg = line["config"]
-    ours = bench.workload_config(1, 4, 5760, 1921, "-", "-")
-    for k in ("workload", "mesh", "p", "k", "rhs", "l", "n_dual", "n_coarse", "dof", "precision"):
-        assert cfg[k] == ours[k], k
-    assert set(cfg) == set(ours)
+    assert line["config"] == bench.workload_config(1)
+
+
+def test_oracle_rate_scales_with_elements():
+    # 2 s per solve on a 256-element sample of a 4096-element workload: 32 s per full solve
+    assert abs(bench.oracle_scaled_rate(2.0, 256, 4096) - 1.0 / 32.0) < 1e-15

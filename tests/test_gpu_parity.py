@@ -92,22 +92,23 @@ def test_full_size_16x16_against_oracle():
     against the oracle's dual-primal solve, plus the oracle's own primal residual of the
     GPU solution."""
     w = W.plane_16x16()
-    s = _solver(w, tol=1e-10)
+    s = _solver(w, tol=1e-12)
     assert s.info().l == 4 and s.info().n_dual == 5760 and s.info().n_coarse == 1921
-    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
-    assert st[0].dual_residual <= 1e-10 and st[0].primal_residual <= 1e-10
+    # both sides solved to 1e-12 so that the stopping point does not dominate the 1e-10 bound
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-12)
+    assert st[0].dual_residual <= 1e-12 and st[0].primal_residual <= 1e-12
     prob = dd.problem_from_workload(w)
-    ref = dd.DDSolver(prob).solve(tol=1e-10)
+    ref = dd.DDSolver(prob).solve(tol=1e-12)
     got = u.cpu().numpy()
-    assert np.linalg.norm(got - ref["phi_N"]) / np.linalg.norm(ref["phi_N"]) <= 1e-9
+    assert np.linalg.norm(got - ref["phi_N"]) / np.linalg.norm(ref["phi_N"]) <= 1e-10
     assert abs(st[0].iterations - ref["iterations"][0]) <= 1
-    assert dd.Conforming(prob).residual(got)[0] <= 1e-10
+    assert dd.Conforming(prob).residual(got)[0] <= 1e-12
     # the GPU's own FP64 yardstick agrees with the oracle's
     # the GPU yardstick projects by master-slot read-back, the oracle by least squares: the two
     # agree to within a small factor on a converged solution
     rg = s.primal_residual(s.rhs_planewave(w.thetas), u)[0]
     ro = dd.Conforming(prob).residual(got)[0]
-    assert rg <= 1e-10 and ro <= 1e-10 and 0.25 <= rg / ro <= 4.0
+    assert rg <= 1e-12 and ro <= 1e-12 and 0.25 <= rg / ro <= 4.0
     s.close()
 
 

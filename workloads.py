@@ -104,15 +104,18 @@ def plane_16x16() -> Workload:
                     np.array([math.pi / 7]))
 
 
-def disk_hanging() -> Workload:
-    lv = disk_leaves(32, 0.25, 2)
+def disk_hanging(base_n: int = 32, n_rhs: int = 64) -> Workload:
+    """The batching workload on a base_n x base_n grid (32 by default).  Smaller grids keep the
+    refinement rule, the degree and angle distributions and the element k h (k = 150 base_n/32)."""
+    lv = disk_leaves(base_n, 0.25, 2)
     E = lv.shape[0]
-    c = leaf_centres(32, lv)
+    c = leaf_centres(base_n, lv)
     inside = (c[:, 0] - 0.5) ** 2 + (c[:, 1] - 0.5) ** 2 < 0.25 ** 2
     eps = np.where(inside, 4.0, 1.0)
     p = np.random.default_rng(3).integers(8, 25, size=E).astype(np.int32)
-    thetas = np.random.default_rng(33).uniform(0.0, 2.0 * math.pi, size=64)
-    return Workload("disk_hanging", 32, lv, p, eps, 150.0, thetas)
+    thetas = np.random.default_rng(33).uniform(0.0, 2.0 * math.pi, size=n_rhs)
+    name = "disk_hanging" if (base_n, n_rhs) == (32, 64) else f"disk_hanging_{base_n}_r{n_rhs}"
+    return Workload(name, base_n, lv, p, eps, 150.0 * base_n / 32, thetas)
 
 
 def random_eps_64() -> Workload:
