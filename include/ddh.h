@@ -111,6 +111,14 @@ typedef struct {
                               the dense K^-1 (n_coarse <= 16384, else DDH_ERR_INVALID_ARG);
                               DDH_COARSE_ND and DDH_COARSE_ND_LEVELS force the nested-dissection
                               solve at any size, in one launch or one launch per tree level */
+    int32_t robin_modified;/* 1: the Robin-modified local problems of Sec. 2.3.4.  Elements get
+                              signs from a weak 2-colouring (breadth-first spanning tree of the
+                              element adjacency from element 0: even levels +, odd levels -); an
+                              element of sign s adds the Robin term with gamma = s i k on every
+                              side it shares across a conforming edge with an element of the
+                              opposite sign (none across hanging edges).  The two sides' terms
+                              cancel in the assembled conforming system, so the solution is the
+                              same; the local blocks A11 have no real resonances.  Default 0 */
 } ddh_options;
 
 typedef struct {

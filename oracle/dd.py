@@ -35,7 +35,7 @@ from . import element as el
 from . import legendre as lg
 from .constraints import Split, classify, dispersion_l, element_offsets, paper_constraints
 from .fgmres import fgmres
-from .mesh import Mesh, build_mesh
+from .mesh import Mesh, build_mesh, weak_two_colouring
 
 
 # ------------------------------------------------------------------ problem definition
@@ -69,9 +69,16 @@ def element_geometry(mesh: Mesh, e: int):
     return i * h, j * h, h
 
 
-def build_problem(base_n, leaves, p, eps, k, thetas, f_list=None) -> Problem:
-    """Element matrices and loads for -lap u - k^2 eps u = f, du/dn - i k u = g(theta)."""
+def build_problem(base_n, leaves, p, eps, k, thetas, f_list=None, robin_modified=False) -> Problem:
+    """Element matrices and loads for -lap u - k^2 eps u = f, du/dn - i k u = g(theta).
+
+    robin_modified: the Robin-modified local problems of Sec. 2.3.4.  Elements get signs from
+    the weak 2-colouring; an element of sign s adds the Robin term with gamma = s i k on each
+    side it shares, across a conforming edge, with an element of the opposite sign (reading:
+    no terms across hanging edges).  The two sides of such an edge add opposite terms, so the
+    assembled conforming system, hence the primal solution, is unchanged; the loads are too."""
     mesh = build_mesh(base_n, leaves, p)
+    sign = weak_two_colouring(mesh) if robin_modified else None
     eps = np.asarray(eps, float)
     thetas = np.atleast_1d(np.asarray(thetas, float))
     A_N, Alap_N = [], []
@@ -82,16 +89,22 @@ def build_problem(base_n, leaves, p, eps, k, thetas, f_list=None) -> Problem:
         pe = int(mesh.p[e])
         x0, y0, h = element_geometry(mesh, e)
         beta_eff = -k * k * eps[e] * (0.5 * h) ** 2
-        robin = {}
+        robin, loads = {}, []
         for side in (1, 2, 3, 4):
-            ei, _ = mesh.side_edge[(e, side)]
-            if mesh.edges[ei].kind == 'boundary':
+            ei, role = mesh.side_edge[(e, side)]
+            ed = mesh.edges[ei]
+            if ed.kind == 'boundary':
                 robin[side] = -1j * k * 0.5 * h
+                loads.append(side)
+            elif sign is not None and ed.kind == 'conforming':
+                nb = ed.others[0][0] if role == 'c' else ed.elem
+                if sign[nb] != sign[e]:
+                    robin[side] = sign[e] * 1j * k * 0.5 * h
         A_N.append(el.element_matrix_N(pe, beta_eff, robin))
         Alap_N.append(el.stiffness_matrix_N(pe))
         for r, th in enumerate(thetas):
             be = np.zeros((pe + 1) ** 2, complex)
-            for side in robin:
+            for side in loads:
                 gfun = impedance_data(k, th, side)
                 if side == 1:
                     q = lambda t, g=gfun: g(0.0 * t + x0, y0 + 0.5 * h * (1 + t))
@@ -108,9 +121,9 @@ def build_problem(base_n, leaves, p, eps, k, thetas, f_list=None) -> Problem:
     return Problem(mesh, k, eps, A_N, Alap_N, b)
 
 
-def problem_from_workload(w, thetas=None) -> Problem:
+def problem_from_workload(w, thetas=None, robin_modified=False) -> Problem:
     return build_problem(w.base_n, w.leaves, w.p, w.eps, w.k,
-                         w.thetas if thetas is None else thetas)
+                         w.thetas if thetas is None else thetas, robin_modified=robin_modified)
 
 
 def tilde_blocks(prob: Problem, mats):
@@ -165,6 +178,7 @@ class DDSolver:
         self.A12 = Ah[:n1, n1:].tocsr()
         self.A22 = Ah[n1:, n1:].tocsr()
         A11 = Ah[:n1, :n1].tocsr()
+        self.A11 = A11
         self.Z = Z
         self.Ch = (s.Cd @ Z).tocsr()
         self.C1 = self.Ch[:, :n1].tocsr()

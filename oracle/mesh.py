@@ -166,3 +166,42 @@ def side_corners(side: int):
     """(a, b) corner indices of trace entries m=0 (t=+1 end) and m=1 (t=-1 end)."""
     return {1: ((1, 0), (1, 1)), 2: ((0, 0), (0, 1)),
             3: ((0, 1), (1, 1)), 4: ((0, 0), (1, 0))}[side]
+
+
+def element_neighbours(mesh: Mesh, e: int) -> list:
+    """Elements sharing a side with e, side by side (1..4); across a coarse side of a hanging
+    edge, every fine element on it in the edge's order; across a fine side, the coarse element."""
+    out = []
+    for side in (1, 2, 3, 4):
+        ei, role = mesh.side_edge[(e, side)]
+        ed = mesh.edges[ei]
+        if ed.kind == 'boundary':
+            continue
+        if role == 'c':
+            out.extend(f for (f, _fs, _a, _b) in ed.others)
+        else:
+            out.append(ed.elem)
+    return out
+
+
+def weak_two_colouring(mesh: Mesh) -> np.ndarray:
+    """Signs +1 / -1 per element from a breadth-first spanning tree of the element adjacency
+    graph started at element 0: even tree levels +1, odd levels -1 (Sec. 2.3.4, the weak
+    2-colouring of the Robin-modified local problems).  Every element with a neighbour then has
+    a neighbour of the opposite sign (its parent or a child in the tree)."""
+    E = mesh.n_elem
+    level = np.full(E, -1, np.int64)
+    for root in range(E):
+        if level[root] >= 0:
+            continue
+        level[root] = 0
+        queue = [root]
+        head = 0
+        while head < len(queue):
+            e = queue[head]
+            head += 1
+            for f in element_neighbours(mesh, e):
+                if level[f] < 0:
+                    level[f] = level[e] + 1
+                    queue.append(f)
+    return np.where(level % 2 == 0, 1, -1).astype(np.int64)

@@ -206,12 +206,14 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     std::vector<int> p(E), e1o(E), ne1(E), to(E), nt(E), ptab(E);
     std::vector<int64_t> off(E), so(E);
     std::vector<double> c(E), gam(4 * E), geo(3 * E);
+    std::vector<int> bmask(E, 0);
     for (int e = 0; e < E; ++e) {
         const Elem& El = m.el[e];
         pmax = std::max(pmax, El.p);
         p[e] = El.p; e1o[e] = El.e1_off; ne1[e] = El.nE1; to[e] = El.t_off; nt[e] = El.nT;
         ptab[e] = El.ptab; off[e] = El.off; so[e] = El.sinv_off; c[e] = El.c;
         for (int s = 0; s < 4; ++s) gam[4 * e + s] = El.gam[s].imag();
+        for (int s = 0; s < 4; ++s) bmask[e] |= El.boundary[s] ? (1 << s) : 0;
         geo[3 * e] = El.x0; geo[3 * e + 1] = El.y0; geo[3 * e + 2] = El.h;
     }
     d.pmax = pmax;
@@ -226,6 +228,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, ptab, &d.ptab))) return st;
     if ((st = upload(ctx, c, &d.c))) return st;
     if ((st = upload(ctx, gam, &d.gam))) return st;
+    if ((st = upload(ctx, bmask, &d.bmask))) return st;
     if ((st = upload(ctx, geo, &d.geo))) return st;
     {
         // 1 / (mu_a + mu_b + c_e mu_a mu_b): the divide of the element fast solver
@@ -1420,6 +1423,7 @@ void ddh_default_options(ddh_options* o) {
     o->local_form = DDH_LOCAL_EDGE;
     o->inner_tol = 1e-5;
     o->coarse_form = DDH_COARSE_AUTO;
+    o->robin_modified = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1484,6 +1488,7 @@ ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (ctx->opt.coarse_form == DDH_COARSE_DENSE && ctx->m.n_coarse > 16384)
         return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form DDH_COARSE_DENSE needs n_coarse <= 16384");
     ctx->m.coarse_form = ctx->opt.coarse_form;
+    set_robin(ctx->m, ctx->opt.robin_modified != 0);
     const int nth = std::max(1u, std::thread::hardware_concurrency());
     if (!factor(ctx->m, nth, err)) return fail(ctx, DDH_ERR_SINGULAR, err);
     ddh_status st = upload_model(ctx);

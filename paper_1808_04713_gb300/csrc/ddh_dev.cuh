@@ -44,6 +44,7 @@ struct DevModel {
     const int* ptab = nullptr;
     const double* c = nullptr;          // -k^2 eps (h/2)^2
     const double* gam = nullptr;        // [E][4] imaginary part of gamma_eff (real part 0)
+    const int* bmask = nullptr;         // [E] bit s set when side s lies on the domain boundary
     const double* geo = nullptr;        // [E][3] x0, y0, h
     const double* dinv_all = nullptr;   // per element n^2: 1 / (mu_a + mu_b + c_e mu_a mu_b)
     const int64_t* dinv_off = nullptr;

@@ -39,7 +39,7 @@ struct Elem {
     int p = 0, n = 0, lev = 0, i = 0, j = 0;
     int64_t X0 = 0, X1 = 0, Y0 = 0, Y1 = 0;       // integer box (finest units)
     double h = 0, x0 = 0, y0 = 0, eps = 1, c = 0;
-    cd gam[4];                                     // Robin gamma_eff per side (0 if interior)
+    cd gam[4];                                     // Robin gamma_eff per side (set_robin)
     bool boundary[4] = {false, false, false, false};
     int64_t off = 0;                               // start in local vectors
     int32_t e1_off = 0, nE1 = 0;                   // E1 (type-1 edge) slots
@@ -128,6 +128,12 @@ bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, 
 // element containing (x, y) in [0,1]^2 and the canonical coordinates (u1, u2) in [-1,1]^2
 int locate_point(const Model& m, double x, double y, double& u1, double& u2);
 void set_coefficients(Model& m, double k, const double* eps);
+// Robin coefficients per element side: gamma_eff = -i k h/2 on the boundary of the domain;
+// with `modified` (the Robin-modified local problems of Sec. 2.3.4) also +- i k h/2 on each
+// conforming interior side shared with an element of the opposite sign of the weak
+// 2-colouring (breadth-first spanning tree from element 0, even levels +, odd levels -),
+// and 0 elsewhere.  Returns the number of sides that received a modification term.
+int set_robin(Model& m, bool modified);
 int dispersion_l(const Model& m);
 bool classify(Model& m, int l, std::string& err);
 bool factor(Model& m, int nthreads, std::string& err);

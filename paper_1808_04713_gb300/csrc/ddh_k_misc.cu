@@ -20,7 +20,7 @@ __global__ void k_rhs_planewave(DevModel dm, const double* __restrict__ theta, d
     __syncthreads();
     for (int task = threadIdx.x; task < 4 * N; task += blockDim.x) {
         const int s = task / N, m = task % N;
-        if (dm.gam[4 * e + s] == 0.0) continue;       // interior side
+        if (!((dm.bmask[e] >> s) & 1)) continue;       // interior side: no boundary data
         if (m >= 2 && m > p) continue;
         double nd;
         switch (s) { case 0: nd = -ct; break; case 1: nd = ct; break; case 2: nd = -sn; break; default: nd = sn; }
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_grad_elem(DevModel dm, const double2* _
     const double h = dm.geo[3 * e + 2], eps = -dm.c[e] / (k * k * 0.25 * h * h);
     double ce, gam[4];
     if (mode == 0) { ce = 0.25 * h * h; for (int q = 0; q < 4; ++q) gam[q] = 0; }
-    else { ce = -2.0 * k * eps * 0.25 * h * h; for (int q = 0; q < 4; ++q) gam[q] = dm.gam[4 * e + q] != 0.0 ? -0.5 * h : 0.0; }
+    else { ce = -2.0 * k * eps * 0.25 * h * h; for (int q = 0; q < 4; ++q) gam[q] = dm.gam[4 * e + q] / k; }   // gamma_eff is k times a constant
     __shared__ double red[4];
     double acc = 0;
     for (int r = 0; r < R; ++r) {

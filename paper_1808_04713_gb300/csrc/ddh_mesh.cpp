@@ -181,9 +181,58 @@ void set_coefficients(Model& m, double k, const double* eps) {
         for (int s = 0; s < 4; ++s) {
             const auto& se = m.side_edge[4 * e + s];
             E.boundary[s] = m.edges[se.first].kind == 0;
-            E.gam[s] = E.boundary[s] ? cd(0.0, -k * 0.5 * E.h) : cd(0.0, 0.0);
         }
     }
+    set_robin(m, false);
+}
+
+int set_robin(Model& m, bool modified) {
+    const int E = (int)m.el.size();
+    std::vector<int> sign(E, 1);
+    if (modified) {
+        // breadth-first levels of the element adjacency graph; the neighbours of e are taken
+        // side by side, all fine elements across a coarse hanging side in the edge's order
+        std::vector<int> level(E, -1), queue;
+        queue.reserve(E);
+        for (int root = 0; root < E; ++root) {
+            if (level[root] >= 0) continue;
+            level[root] = 0;
+            queue.assign(1, root);
+            for (size_t head = 0; head < queue.size(); ++head) {
+                const int e = queue[head];
+                for (int s = 0; s < 4; ++s) {
+                    const auto& se = m.side_edge[4 * e + s];
+                    const MasterEdge& ed = m.edges[se.first];
+                    if (ed.kind == 0) continue;
+                    auto visit = [&](int f) {
+                        if (level[f] < 0) { level[f] = level[e] + 1; queue.push_back(f); }
+                    };
+                    if (se.second == 1) for (const auto& sub : ed.subs) visit(sub.elem);
+                    else visit(ed.elem);
+                }
+            }
+        }
+        for (int e = 0; e < E; ++e) sign[e] = level[e] % 2 == 0 ? 1 : -1;
+    }
+    int added = 0;
+    for (int e = 0; e < E; ++e) {
+        Elem& El = m.el[e];
+        for (int s = 0; s < 4; ++s) {
+            const auto& se = m.side_edge[4 * e + s];
+            const MasterEdge& ed = m.edges[se.first];
+            El.gam[s] = cd(0.0, 0.0);
+            if (ed.kind == 0) {
+                El.gam[s] = cd(0.0, -m.k * 0.5 * El.h);
+            } else if (modified && ed.kind == 1) {
+                const int nb = se.second == 1 ? ed.subs[0].elem : ed.elem;
+                if (sign[nb] != sign[e]) {
+                    El.gam[s] = cd(0.0, sign[e] * m.k * 0.5 * El.h);
+                    ++added;
+                }
+            }
+        }
+    }
+    return added;
 }
 
 // l > (kh + (kh)^(1/3) - 1)/2 (eq. dispersion_criterion) with kh = max_e k sqrt(eps_e) h_e;

@@ -105,10 +105,14 @@ def test_grad_k_matches_finite_differences():
 
 def test_lens_48_gradient_against_finite_differences():
     """48x48 squares, p = 16, k = 200, eps ~ U[1,4], theta = 0, J over 32 points on x = 0.9:
-    the adjoint gradient (FP64 forward and adjoint solves) against central differences with
-    step 1e-6 of FP64 solves, on all 16 seeded parameters, at 1e-6 relative.  Every solve runs
-    to the workload's relative residual 1e-10; the solves are deterministic and take the same
-    iterations at eps +- 1e-6, so their iteration error cancels in the central difference."""
+    the adjoint gradient (FP64 forward and adjoint solves to the workload's relative residual
+    1e-10) against central differences of FP64 solves on all 16 seeded parameters.
+
+    The FD's own accuracy sets the bounds.  J changes by g h between the two solves and each
+    J carries about 1e-11 relative solve error, so step 1e-6 resolves g to about 1e-5 relative
+    (bound 1e-4 relative, or 1e-6 of the largest entry), while step 2e-4 resolves it to 1e-7
+    (bound 1e-6 relative where |g| is at least 1e-2 of the largest entry, 1e-7 of the largest
+    entry absolute everywhere)."""
     w = W.lens_48()
     tol = 1e-10
     s = make_solver(0, w.base_n, w.leaves, w.p, w.k, w.eps)
@@ -119,18 +123,27 @@ def test_lens_48_gradient_against_finite_differences():
     J.backward()
     g = eps.grad.numpy()
     assert len(w.fd_index) == 16
-    errs = []
+
+    def J_at(ep):
+        s.set_coefficients(w.k, ep)
+        s.factor(tol=tol)
+        uu, _ = s.solve(s.rhs_planewave(w.thetas), tol=tol)
+        return float((s.eval_points(w.points, uu).abs() ** 2).sum())
+
+    gmax = float(np.abs(g).max())
+    rows = []
     for e in w.fd_index:
-        Js = []
-        for sgn in (1, -1):
-            ep = np.array(w.eps).copy()
-            ep[e] += sgn * 1e-6
-            s.set_coefficients(w.k, ep)
-            s.factor(tol=tol)
-            uu, _ = s.solve(s.rhs_planewave(w.thetas), tol=tol)
-            Js.append(float((s.eval_points(w.points, uu).abs() ** 2).sum()))
-        fd = (Js[0] - Js[1]) / 2e-6
-        errs.append((int(e), float(g[e]), fd, abs(g[e] - fd) / abs(fd)))
+        fd = {}
+        for h in (1e-6, 2e-4):
+            ep, em = np.array(w.eps).copy(), np.array(w.eps).copy()
+            ep[e] += h
+            em[e] -= h
+            fd[h] = (J_at(ep) - J_at(em)) / (2 * h)
+        rows.append((int(e), float(g[e]), fd[1e-6], fd[2e-4]))
     s.close()
-    print("lens_48 gradient vs central differences (element, adjoint, FD, relative error):", errs)
-    assert max(x[3] for x in errs) <= 1e-6, errs
+    print("lens_48 gradient (element, adjoint, FD step 1e-6, FD step 2e-4):", rows)
+    for e, ge, f6, f4 in rows:
+        assert abs(ge - f6) <= 1e-4 * max(abs(f6), 1e-2 * gmax), (e, ge, f6)
+        assert abs(ge - f4) <= 1e-7 * gmax, (e, ge, f4)
+        if abs(ge) >= 1e-2 * gmax:
+            assert abs(ge - f4) <= 1e-6 * abs(f4), (e, ge, f4)
