@@ -119,6 +119,10 @@ typedef struct {
                               opposite sign (none across hanging edges).  The two sides' terms
                               cancel in the assembled conforming system, so the solution is the
                               same; the local blocks A11 have no real resonances.  Default 0 */
+    int32_t tensor_cores;  /* mixed precision with edge-operator passes: 1 = the Krylov-loop pass 1
+                              [x_E; t_T] = [S_E^-1; Y^T] r_E of the complex64 inner solves runs on
+                              the tcgen05 tensor cores in TF32 (operands rounded to 10-bit
+                              mantissas, FP32 accumulation); 0 (default) = FP32 CUDA cores */
 } ddh_options;
 
 typedef struct {

@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CPP_SRCS = ["ddh_tables.cpp", "ddh_mesh.cpp", "ddh_factor.cpp", "ddh_coarse.cpp"]
 CU_SRCS = ["ddh_k_fdm_pass1_f64.cu", "ddh_k_fdm_pass1_f32.cu", "ddh_k_fdm_pass2_f64.cu", "ddh_k_fdm_pass2_f32.cu",
-           "ddh_k_edge.cu", "ddh_k_coarse.cu", "ddh_k_krylov.cu", "ddh_k_misc.cu", "ddh_api.cu",
+           "ddh_k_edge.cu", "ddh_k_tc.cu", "ddh_k_coarse.cu", "ddh_k_krylov.cu", "ddh_k_misc.cu", "ddh_api.cu",
            "ddh_noalloc.cu"]
 
 

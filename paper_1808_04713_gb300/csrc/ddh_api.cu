@@ -72,6 +72,10 @@ struct ddh_ctx {
     void* pq64 = nullptr;                          // Y = [A11^-1 A_1T]_E per element
     void* pq32 = nullptr;
     bool edge_form = false;                        // Krylov-loop passes with Y (no FDM)
+    const float* tc_W = nullptr;                   // [S_E^-1; Y^T] planes for the tensor-core pass 1
+    const int64_t* tc_off = nullptr;
+    const int* tc_items = nullptr;                 // elements by degree, descending
+    int tc_maxT = 0;
     double2* Kinv = nullptr;                       // dense coarse inverse (elimination order)
     float2* Kinv32 = nullptr;
     int gemv_form = 1;                             // single-RHS GEMV kernel (timed at upload)
@@ -152,6 +156,10 @@ static void free_model(ddh_ctx* ctx) {
     ctx->sinv64 = ctx->sinv32 = nullptr;
     ctx->pq64 = ctx->pq32 = nullptr;
     ctx->edge_form = false;
+    ctx->tc_W = nullptr;
+    ctx->tc_off = nullptr;
+    ctx->tc_items = nullptr;
+    ctx->tc_maxT = 0;
     ctx->Kinv = nullptr;
     ctx->Kinv32 = nullptr;
     ctx->refine_coarse = false;
@@ -415,6 +423,56 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, y32, &b))) return st;
         ctx->pq64 = (void*)a;
         ctx->pq32 = (void*)b;
+    }
+    // tensor-core pass 1 (mixed precision): the real and imaginary planes of W = [S_E^-1; Y^T]
+    // per element, rounded to TF32, in the no-swizzle K-major canonical layout of the MMA
+    // operands (core matrices of 8 rows x 4 values, row group g and column group c at
+    // (g * Kp/4 + c) * 32 floats); elements listed by degree, descending
+    if (ctx->opt.precision == DDH_PREC_MIXED_FP32 && ctx->opt.tensor_cores && ctx->edge_form) {
+        auto tf32 = [](double v) {
+            float f = (float)v;
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xFFFFE000u;   // nearest, ties away
+            std::memcpy(&f, &u, 4);
+            return f;
+        };
+        std::vector<int64_t> off(E);
+        int64_t tot = 0;
+        int maxT = 0;
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            off[e] = tot;
+            const int M = El.nE1 + El.nT, Kp = (El.nE1 + 7) & ~7;
+            tot += 2 * (int64_t)((M + 7) / 8) * (Kp / 4) * 32;
+            maxT = std::max(maxT, El.nT);
+        }
+        std::vector<float> Wp((size_t)std::max<int64_t>(tot, 32), 0.f);
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            const int nE = El.nE1, nT = El.nT, M = nE + nT, Kp = (nE + 7) & ~7;
+            const int64_t plane = (int64_t)((M + 7) / 8) * (Kp / 4) * 32;
+            float* re = Wp.data() + off[e];
+            float* im = re + plane;
+            for (int o = 0; o < M; ++o)
+                for (int j = 0; j < nE; ++j) {
+                    const cd w = o < nE ? m.sinv[(size_t)El.sinv_off + (size_t)j * nE + o]
+                                        : m.pq[(size_t)El.pq_off + (size_t)j * nT + (o - nE)];
+                    const int64_t k = ((int64_t)(o >> 3) * (Kp / 4) + (j >> 2)) * 32 + (o & 7) * 4 + (j & 3);
+                    re[k] = tf32(w.real());
+                    im[k] = tf32(w.imag());
+                }
+        }
+        std::vector<int> items(E);
+        for (int e = 0; e < E; ++e) items[e] = e;
+        std::stable_sort(items.begin(), items.end(), [&](int a, int b) { return m.el[a].p > m.el[b].p; });
+        const float* wp;
+        if ((st = upload(ctx, Wp, &wp))) return st;
+        ctx->tc_W = wp;
+        if ((st = upload(ctx, off, &ctx->tc_off))) return st;
+        if ((st = upload(ctx, items, &ctx->tc_items))) return st;
+        ctx->tc_maxT = maxT;
+        set_tc_limits(d.maxE1, maxT);
     }
     // coarse factor
     auto conv = [](const std::vector<cd>& v) {
@@ -873,7 +931,9 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     cudaStream_t s = ctx->stream;
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
     const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
-    if (ctx->edge_form && !(bt && has_bI)) launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s);
+    if (ctx->edge_form && !(bt && has_bI) && !bt && std::is_same<T, float>::value && ctx->tc_W)
+        launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, zsign, w.xE, w.tT, R, done, s, ctx->tc_maxT);
+    else if (ctx->edge_form && !(bt && has_bI)) launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s);
     else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
@@ -1424,6 +1484,7 @@ void ddh_default_options(ddh_options* o) {
     o->inner_tol = 1e-5;
     o->coarse_form = DDH_COARSE_AUTO;
     o->robin_modified = 0;
+    o->tensor_cores = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1771,7 +1832,9 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
         ms_out[5] = timeit([&] { launch_pre<double>(d, K.vin, w.vd, w.outE, w.mvec, K.zw, 0, R, nullptr, s); });
     } else {
         ms_out[0] = timeit([&] {
-            if (ef) launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
+            if (ef && ctx->tc_W) launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, 1.0, w.xE, w.tT, R, nullptr, s,
+                                                 ctx->tc_maxT);
+            else if (ef) launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
             else launch_pass1<float>(d, sinv, nullptr, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
         });
         ms_out[1] = timeit([&] { launch_coarse_assemble<float>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });

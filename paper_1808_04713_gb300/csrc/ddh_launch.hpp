@@ -155,6 +155,13 @@ void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int
 void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, double sign, int R, cudaStream_t st);
 void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st);
 void launch_readback(const DevModel& dm, const double2* phi, double2* z, int R, cudaStream_t st);
+// Krylov-loop pass 1 of the complex64 inner solves on tcgen05 tensor cores (TF32): W = the
+// per-element [S_E^-1; Y^T] planes in the canonical shared-memory layout (w_off: float offset
+// of element e's real plane, the imaginary plane follows), items = elements in processing order
+void launch_pass1_tc(const DevModel& dm, const float* W, const int64_t* w_off, const int* items, int n_items,
+                     const double2* z, double zsign, void* xE, void* tT, int R, const int* done, cudaStream_t st,
+                     int maxT);
+void set_tc_limits(int maxE1, int maxT);
 size_t pass_smem(int pmax, bool fp64);
 void set_smem_limits(int pmax, int maxE1);
 

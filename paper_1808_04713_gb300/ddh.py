@@ -33,7 +33,8 @@ class Options(C.Structure):
                 ("l_override", C.c_int32), ("precision", C.c_int32), ("precond", C.c_int32),
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
                 ("coarse_fp32", C.c_int32), ("local_form", C.c_int32),
-                ("inner_tol", C.c_double), ("coarse_form", C.c_int32), ("robin_modified", C.c_int32)]
+                ("inner_tol", C.c_double), ("coarse_form", C.c_int32), ("robin_modified", C.c_int32),
+                ("tensor_cores", C.c_int32)]
 
 
 class Info(C.Structure):
