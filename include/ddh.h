@@ -250,6 +250,21 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
 ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const void* u_dev, int32_t R,
                                        double* out_host);
 
+/* What the autotuners chose for R right-hand sides in `precision` (ddh_precision), valid after a
+ * solve with that R and precision (both run once per R, before the first iteration is captured):
+ *   *edge_persistent   launch form of the Krylov-loop pass 1 with explicit edge operators: 1 the
+ *                      persistent form over the degree-sorted element list, 0 one CTA per
+ *                      (element, RHS block), -1 not tuned (nested-dissection-only or FDM form);
+ *   tpr_by_degree[33]  threads sharing one output row in the persistent Krylov-loop pass 1 for
+ *                      each element degree p (1, 2, 4 or 8; 0 where no element has degree p or
+ *                      the pass has not been tuned for this R);
+ *   nd_rb[2 L]         right-hand sides per CTA of each nested-dissection level launch (forward
+ *                      levels 0 .. L-1, then backward; 0 = level not launched on its own), with
+ *                      L written to *nd_levels (0 when the dense K^-1 is in use or not yet tuned).
+ * nd_rb may be NULL; otherwise it must hold 128 entries (L <= 64).  Host arrays. */
+ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
+                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels);
+
 /* Apply one of the two operators of the dual iteration to caller-given dual vectors (for
  * checks of the hot path against a reference; the solves apply the same code):
  *   which = 0  the interface operator F nu = C^ A^-1 C^T nu (eq. complicated_schur_system,

@@ -72,6 +72,11 @@ struct ddh_ctx {
     void* pq64 = nullptr;                          // Y = [A11^-1 A_1T]_E per element
     void* pq32 = nullptr;
     bool edge_form = false;                        // Krylov-loop passes with Y (no FDM)
+    const int* edge_items = nullptr;               // elements by degree, descending (persistent edge pass)
+    std::vector<int> deg_begin, deg_count, deg_p;  // contiguous runs of equal degree in edge_items
+    std::map<int, const signed char*> edge_tpr;    // tuned threads per output row by degree, per (precision, RHS block)
+    std::map<int, std::vector<int>> edge_tpr_host;
+    std::map<int, bool> edge_persist;              // per (precision, RHS block): persistent form timed faster
     const float* tc_W = nullptr;                   // [S_E^-1; Y^T] planes for the tensor-core pass 1
     const int64_t* tc_off = nullptr;
     const int* tc_items = nullptr;                 // elements by degree, descending
@@ -156,6 +161,11 @@ static void free_model(ddh_ctx* ctx) {
     ctx->sinv64 = ctx->sinv32 = nullptr;
     ctx->pq64 = ctx->pq32 = nullptr;
     ctx->edge_form = false;
+    ctx->edge_items = nullptr;
+    ctx->deg_begin.clear(); ctx->deg_count.clear(); ctx->deg_p.clear();
+    ctx->edge_tpr.clear();
+    ctx->edge_tpr_host.clear();
+    ctx->edge_persist.clear();
     ctx->tc_W = nullptr;
     ctx->tc_off = nullptr;
     ctx->tc_items = nullptr;
@@ -423,6 +433,23 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         if ((st = upload(ctx, y32, &b))) return st;
         ctx->pq64 = (void*)a;
         ctx->pq32 = (void*)b;
+    }
+    // work list of the persistent edge pass: elements by degree, descending, and the runs of
+    // equal degree (the autotuner picks the threads per output row of each degree)
+    {
+        std::vector<int> items(E);
+        for (int e = 0; e < E; ++e) items[e] = e;
+        std::stable_sort(items.begin(), items.end(), [&](int a, int b) { return m.el[a].p > m.el[b].p; });
+        for (int i = 0; i < E; ++i) {
+            const int pe = m.el[items[i]].p;
+            if (ctx->deg_p.empty() || ctx->deg_p.back() != pe) {
+                ctx->deg_p.push_back(pe);
+                ctx->deg_begin.push_back(i);
+                ctx->deg_count.push_back(0);
+            }
+            ctx->deg_count.back()++;
+        }
+        if ((st = upload(ctx, items, &ctx->edge_items))) return st;
     }
     // tensor-core pass 1 (mixed precision): the real and imaginary planes of W = [S_E^-1; Y^T]
     // per element, rounded to TF32, in the no-swizzle K-major canonical layout of the MMA
@@ -822,6 +849,102 @@ static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
     return DDH_OK;
 }
 
+// Key of a tuned edge-pass table: precision and right-hand-side block
+static int edge_key(bool fp64, int R) {
+    const int rb = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+    return (fp64 ? 100 : 0) + rb;
+}
+
+// Per-degree autotuner of the persistent Krylov-loop pass 1: for each run of equal degree in the
+// work list, time the pass over that run alone with 1, 2, 4 and 8 threads per output row (the
+// tile shape: how many threads share one row of [S_E^-1; Y^T], the rest of the 256 take other
+// rows) and keep the fastest.  Runs once per (precision, RHS block), before any graph capture,
+// on the cleared work buffers.
+static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
+    if (!ctx->edge_form || !ctx->edge_items) return DDH_OK;
+    const int key = edge_key(fp64, R);
+    if (ctx->edge_tpr.count(key)) return DDH_OK;
+    const DevModel& d = ctx->dm;
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(w.vd, 0, sizeof(double2) * (size_t)R * std::max(1, d.n_dual), s));
+    const void* sinv = fp64 ? ctx->sinv64 : ctx->sinv32;
+    const void* Y = fp64 ? ctx->pq64 : ctx->pq32;
+    EdgeSched es;
+    es.items = ctx->edge_items;
+    std::vector<signed char> tbl(33, 0);
+    std::vector<int> host(33, 0);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (size_t g = 0; g < ctx->deg_p.size(); ++g) {
+        float best = 1e30f;
+        int pick = 0;
+        for (int tpr : {4, 2, 8, 1}) {
+            auto run = [&] {
+                if (fp64) launch_pass1_edge<double>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, &es,
+                                                    ctx->deg_begin[g], ctx->deg_count[g], tpr);
+                else launch_pass1_edge<float>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, &es,
+                                              ctx->deg_begin[g], ctx->deg_count[g], tpr);
+            };
+            run();
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) run();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < 0.97f * best) { best = ms; pick = tpr; }
+        }
+        tbl[ctx->deg_p[g]] = (signed char)pick;
+        host[ctx->deg_p[g]] = pick;
+    }
+    CK(cudaGetLastError());
+    const signed char* dt;
+    ddh_status st;
+    if ((st = upload(ctx, tbl, &dt))) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+    }
+    // then the whole pass in both launch forms: the tuned persistent one over the sorted list,
+    // and one CTA per (element, RHS block) with its fixed shape; keep the faster
+    es.tpr_p = dt;
+    float best[2] = {0, 0};
+    for (int form = 0; form < 2; ++form) {
+        auto run = [&] {
+            const EdgeSched* sp = form ? &es : nullptr;
+            if (fp64) launch_pass1_edge<double>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, sp);
+            else launch_pass1_edge<float>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, sp);
+        };
+        run();
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 5; ++rep) run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&best[form], e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    ctx->edge_tpr[key] = dt;
+    ctx->edge_tpr_host[key] = host;
+    ctx->edge_persist[key] = best[1] < best[0];
+    return DDH_OK;
+}
+
+// Work list and tuned tile shapes of the persistent edge pass for R right-hand sides; empty
+// (one CTA per task) before tuning and where that form timed faster
+static EdgeSched edge_sched(const ddh_ctx* ctx, bool fp64, int R) {
+    EdgeSched es;
+    const int key = edge_key(fp64, R);
+    const auto pt = ctx->edge_persist.find(key);
+    if (pt == ctx->edge_persist.end() || !pt->second) return es;   // one CTA per task
+    es.items = ctx->edge_items;
+    const auto it = ctx->edge_tpr.find(key);
+    es.tpr_p = it == ctx->edge_tpr.end() ? nullptr : it->second;
+    return es;
+}
+
 static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     const DevModel& d = ctx->dm;
     const size_t es = fp64 ? sizeof(double2) : sizeof(float2);
@@ -848,6 +971,7 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     w.vd = (double2*)p;
     if ((st = get_work(ctx, "mvec", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.mvec = (double2*)p;
+    if ((st = edge_tune(ctx, w, R, fp64))) return st;
     return nd_tune(ctx, w, R);
 }
 
@@ -933,7 +1057,10 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
     if (ctx->edge_form && !(bt && has_bI) && !bt && std::is_same<T, float>::value && ctx->tc_W)
         launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, zsign, w.xE, w.tT, R, done, s, ctx->tc_maxT);
-    else if (ctx->edge_form && !(bt && has_bI)) launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s);
+    else if (ctx->edge_form && !(bt && has_bI)) {
+        const EdgeSched es = edge_sched(ctx, std::is_same<T, double>::value, R);
+        launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s, &es);
+    }
     else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
@@ -1765,6 +1892,29 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
     return DDH_OK;
 }
 
+ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
+                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels) {
+    if (!ctx || !edge_persistent || !tpr_by_degree || !nd_levels || R <= 0) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored) return DDH_ERR_NOT_READY;
+    for (int p = 0; p < 33; ++p) tpr_by_degree[p] = 0;
+    const int ekey = edge_key(precision == DDH_PREC_FP64, R);
+    const auto pt = ctx->edge_persist.find(ekey);
+    *edge_persistent = pt == ctx->edge_persist.end() ? -1 : (pt->second ? 1 : 0);
+    const auto it = ctx->edge_tpr_host.find(ekey);
+    if (it != ctx->edge_tpr_host.end())
+        for (int p = 0; p < 33; ++p) tpr_by_degree[p] = it->second[p];
+    *nd_levels = 0;
+    const auto jt = ctx->nd_rb.find(R);
+    if (jt != ctx->nd_rb.end()) {
+        const int L = (int)jt->second.size() / 2;
+        if (nd_rb && L > 64) return DDH_ERR_INVALID_ARG;
+        *nd_levels = L;
+        if (nd_rb)
+            for (int i = 0; i < 2 * L; ++i) nd_rb[i] = jt->second[i];
+    }
+    return DDH_OK;
+}
+
 ddh_status ddh_apply_dual_operator(ddh_ctx* ctx, int32_t which, const void* v_dev, void* out_dev, int32_t R,
                                    int32_t precision) {
     if (!ctx) return DDH_ERR_INVALID_ARG;
@@ -1820,7 +1970,8 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
     const double2* z = K.zw;
     if (fp64) {
         ms_out[0] = timeit([&] {
-            if (ef) launch_pass1_edge<double>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
+            const EdgeSched es = edge_sched(ctx, true, R);
+            if (ef) launch_pass1_edge<double>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, &es);
             else launch_pass1<double>(d, sinv, nullptr, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
         });
         ms_out[1] = timeit([&] { launch_coarse_assemble<double>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });
@@ -1834,7 +1985,10 @@ ddh_status ddh_profile_op(ddh_ctx* ctx, int32_t R, int32_t precision, int32_t re
         ms_out[0] = timeit([&] {
             if (ef && ctx->tc_W) launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, 1.0, w.xE, w.tT, R, nullptr, s,
                                                  ctx->tc_maxT);
-            else if (ef) launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s);
+            else if (ef) {
+                const EdgeSched es = edge_sched(ctx, false, R);
+                launch_pass1_edge<float>(d, sinv, Y, z, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, &es);
+            }
             else launch_pass1<float>(d, sinv, nullptr, z, 1.0, nullptr, 0, w.xE, w.tT, R, nullptr, s);
         });
         ms_out[1] = timeit([&] { launch_coarse_assemble<float>(d, w.tT, nullptr, z, 1.0, w.t, R, nullptr, s); });

@@ -94,6 +94,135 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
     }
 }
 
+// The same pass as one persistent launch over a degree-sorted work list.  Task t is (element
+// items[item0 + t / nrb], right-hand-side block t % nrb): the heaviest elements come first, and
+// the blocks of one element are adjacent, so its S_E^-1 is reused from L2.  A CTA walks tasks
+// t = blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one task, the next task's
+// S_E^-1 is already being copied into the other of two shared-memory buffers (bulk copy,
+// mbarrier per buffer).  tpr_p[p] (1, 2, 4 or 8 threads per output row) is chosen per degree by
+// the autotuner; 0 = the default (4 up to 64 output rows, else 2); tpr_force > 0 overrides it.
+template <class T, int RB>
+__global__ void __launch_bounds__(256) k_pass1_edge_p(DevModel dm, const cpx<T>* __restrict__ sinv,
+                                                      const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
+                                                      double zsign, const double2* __restrict__ bt, int R,
+                                                      cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
+                                                      const int* __restrict__ done, const int* __restrict__ items,
+                                                      int item0, int nitems, const signed char* __restrict__ tpr_p,
+                                                      int tpr_force, int stage_off, int buf_bytes, int vs) {
+    if (done && *done) return;
+    extern __shared__ __align__(128) char smem[];
+    const int nrb = (R + RB - 1) / RB, ntask = nitems * nrb;
+    cpx<T>* rE = reinterpret_cast<cpx<T>*>(smem);     // [RB][vs]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_off);        // 2 barriers
+    __shared__ int s_fail;
+    const bool staged = stage_off > 0;
+    auto buf = [&](int b) { return reinterpret_cast<cpx<T>*>(smem + stage_off + 128 + (size_t)b * buf_bytes); };
+    auto task_elem = [&](int t) { return items[item0 + t / nrb]; };
+    // copy of task t's S_E^-1 into buffer b (thread 0); false when there is nothing to copy
+    auto issue = [&](int t, int b) {
+        const int e = task_elem(t), nE = dm.nE1[e];
+        if (nE == 0) return false;
+        const uint32_t bytes = (uint32_t)(((size_t)nE * nE * sizeof(cpx<T>) + 15) & ~(size_t)15);
+        const uint32_t bb = smem_u32(bar + b);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(buf(b))), "l"(sinv + dm.sinv_off[e]), "r"(bytes), "r"(bb)
+                     : "memory");
+        return true;
+    };
+    bool pend[2] = {false, false};        // thread 0: copy in flight per buffer
+    uint32_t uses[2] = {0, 0};            // completed phases per buffer
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        if (staged) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            if (blockIdx.x < ntask) pend[0] = issue(blockIdx.x, 0);
+        }
+    }
+    __syncthreads();
+    int k = 0;
+    for (int t = blockIdx.x; t < ntask; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int e = task_elem(t), r0 = (t % nrb) * RB;
+        const int cnt = min(RB, R - r0);
+        const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
+        if (staged && threadIdx.x == 0 && t + (int)gridDim.x < ntask) pend[b ^ 1] = issue(t + gridDim.x, b ^ 1);
+        const int64_t off = dm.off[e];
+        for (int idx = threadIdx.x; idx < cnt * nE; idx += blockDim.x) {
+            const int q = idx / nE, i = idx % nE, r = r0 + q;
+            cpx<T> v = mk<T>(0, 0);
+            const int row = dm.e1_row[e1o + i];
+            if (z && row >= 0) v = (T)(zsign * dm.e1_sign[e1o + i]) * ld<T>(z, (int64_t)r * dm.n_dual + row);
+            if (bt) v += ld<T>(bt, (int64_t)r * dm.n_local + off + dm.e1_slot[e1o + i]);
+            rE[q * vs + i] = v;
+        }
+        const cpx<T>* S = sinv + dm.sinv_off[e];
+        if (staged && nE > 0) {
+            if (threadIdx.x == 0) {
+                bool ok = !pend[b];
+                for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar + b, uses[b] & 1);
+                if (pend[b]) { pend[b] = false; ++uses[b]; }
+                if (!ok) { s_fail = 1; if (dm.err) atomicExch(dm.err, 2); }
+            }
+            S = buf(b);
+        }
+        __syncthreads();
+        if (s_fail) break;
+        const cpx<T>* Ye = Y + dm.pq_off[e];
+        const int no = nE + nT;
+        int tpr = tpr_force > 0 ? tpr_force : (tpr_p ? (int)tpr_p[dm.p[e]] : 0);
+        if (tpr <= 0) tpr = no <= 64 ? 4 : 2;
+        const int chunk = (nE + tpr - 1) / tpr;
+        for (int base = 0; base < no * tpr; base += blockDim.x) {
+            const int slot = base + threadIdx.x;
+            const int o = slot / tpr, part = slot % tpr;
+            cpx<T> a0[RB], a1[RB];
+#pragma unroll
+            for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
+            if (o < no) {
+                const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
+                const int ld = o < nE ? nE : nT;
+                const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
+                int j = j0;
+                for (; j + 1 < j1; j += 2) {
+                    const cpx<T> s0 = col0[(int64_t)j * ld], s1 = col0[(int64_t)(j + 1) * ld];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        if (q < cnt) { fma_c(a0[q], s0, rE[q * vs + j]); fma_c(a1[q], s1, rE[q * vs + j + 1]); }
+                }
+                if (j < j1) {
+                    const cpx<T> s0 = col0[(int64_t)j * ld];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RB; ++q) {
+                cpx<T> v = a0[q] + a1[q];
+                for (int sh = 1; sh < tpr; sh <<= 1) {
+                    v.x += __shfl_xor_sync(0xffffffffu, v.x, sh);
+                    v.y += __shfl_xor_sync(0xffffffffu, v.y, sh);
+                }
+                if (part == 0 && o < no && q < cnt) {
+                    if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
+                    else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // copies still in flight (after a failure) land before the CTA leaves (bounded waits)
+    if (threadIdx.x == 0)
+        for (int bb = 0; bb < 2; ++bb)
+            if (pend[bb]) {
+                bool ok = false;
+                for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar + bb, uses[bb] & 1);
+            }
+}
+
 template <class T, int RB>
 __global__ void __launch_bounds__(128) k_pass2_edge(DevModel dm, const cpx<T>* __restrict__ Y,
                                                     const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
@@ -334,16 +463,55 @@ __global__ void k_pre_rows(DevModel dm, const cpx<T>* __restrict__ outE, const d
 }
 
 // ------------------------------------------------------------------ launch wrappers
+// shared memory of the persistent edge pass: r_E block, then (when two fit) two staging buffers
+// for S_E^-1 behind two mbarriers; returns the staging offset (0 = read S_E^-1 from global)
+template <class T>
+static int edge_p_layout(int rb, int maxE1, int* buf_bytes, size_t* total) {
+    const size_t base = edge_vec_bytes<T>(rb, maxE1);
+    const size_t one = ((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127;
+    const bool fit = maxE1 > 0 && base + 128 + 2 * one <= 200 * 1024;
+    *buf_bytes = (int)one;
+    *total = fit ? base + 128 + 2 * one : base;
+    return fit ? (int)base : 0;
+}
+template <class T, int RB>
+static void edge_p_t(const DevModel& dm, const cpx<T>* S, const cpx<T>* Yp, const double2* z, double zsign,
+                     const double2* bt, void* xE, void* tT, int R, const int* done, const EdgeSched& es, int item0,
+                     int nitems, int tpr_force, cudaStream_t st) {
+    int buf = 0;
+    size_t sm = 0;
+    const int so = edge_p_layout<T>(RB, dm.maxE1, &buf, &sm);
+    const int vs = std::max(1, dm.maxE1);
+    const int ntask = nitems * ((R + RB - 1) / RB);
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pass1_edge_p<T, RB>, 256, sm);
+    const int grid = std::max(1, std::min(ntask, std::max(1, per) * std::max(1, nsm)));
+    k_pass1_edge_p<T, RB><<<grid, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, es.items,
+                                                 item0, nitems, es.tpr_p, tpr_force, so, buf, vs);
+}
 template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
-                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
+                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
+                       const EdgeSched* es, int item0, int nitems, int tpr_force) {
     const int rb = rhs_block(R);
+    const cpx<T>* S = (const cpx<T>*)sinv;
+    const cpx<T>* Yp = (const cpx<T>*)Y;
+    if (es && es->items) {
+        if (nitems < 0) nitems = dm.E;
+        switch (rb) {
+            case 8: edge_p_t<T, 8>(dm, S, Yp, z, zsign, bt, xE, tT, R, done, *es, item0, nitems, tpr_force, st); break;
+            case 4: edge_p_t<T, 4>(dm, S, Yp, z, zsign, bt, xE, tT, R, done, *es, item0, nitems, tpr_force, st); break;
+            case 2: edge_p_t<T, 2>(dm, S, Yp, z, zsign, bt, xE, tT, R, done, *es, item0, nitems, tpr_force, st); break;
+            default: edge_p_t<T, 1>(dm, S, Yp, z, zsign, bt, xE, tT, R, done, *es, item0, nitems, tpr_force, st);
+        }
+        return;
+    }
     const int so = edge_stage_off<T>(rb, dm.maxE1);
     const int ntask = dm.E * ((R + rb - 1) / rb);
     const size_t sm = edge_smem_total<T>(rb, dm.maxE1);
     const int vs = std::max(1, dm.maxE1);
-    const cpx<T>* S = (const cpx<T>*)sinv;
-    const cpx<T>* Yp = (const cpx<T>*)Y;
     switch (rb) {
         case 8: k_pass1_edge<T, 8><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
         case 4: k_pass1_edge<T, 4><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
@@ -366,8 +534,8 @@ void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, con
         default: k_pass2_edge<T, 1><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
     }
 }
-template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
-template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int);
+template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int);
 template void launch_pass2_edge<double>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
 template void launch_pass2_edge<float>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
 template <class T>
@@ -428,6 +596,10 @@ template <class T, int RB>
 static void set_edge_pass_limits(int maxE1) {
     cudaFuncSetAttribute(k_pass1_edge<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)edge_smem_total<T>(RB, maxE1));
+    int buf = 0;
+    size_t tot = 0;
+    edge_p_layout<T>(RB, maxE1, &buf, &tot);
+    cudaFuncSetAttribute(k_pass1_edge_p<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tot);
 }
 void set_edge_limits(int pmax, int maxE1) {
     (void)pmax;

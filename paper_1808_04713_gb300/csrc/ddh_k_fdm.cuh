@@ -8,12 +8,190 @@
 
 namespace ddh {
 
+// threads per CTA of the FDM passes: the shared-memory footprint (element tables, RHS blocks,
+// staged S_E^-1 and the batched interior tiles, ~110 KB at p = 20 with 8 RHS) allows two CTAs
+// per SM, so a CTA carries 8 warps to keep 16 resident per SM
+constexpr int kFdmThreads = 256;
+
+// ------------------------------------------------------------------ batched interior FDM
+// QB right-hand sides of one element per barrier interval: interior tiles [q][a][b] (n x n),
+// cross values [q][i][*] (interior rows / columns i = 0, 1), and a map from frame slots to the
+// element's type-1 edge (index) and type-2 (0x4000 | index) slots.
+template <class T>
+struct FdmBatch {
+    cpx<T>* A;      // QB n^2
+    cpx<T>* B;      // QB n^2 (scratch)
+    cpx<T>* rrow;   // QB 2n
+    cpx<T>* rcol;   // QB 2n
+    cpx<T>* rho;    // QB 2n
+    cpx<T>* kap;    // QB 2n
+    short* fidx;    // N^2
+};
+template <class T>
+__device__ inline FdmBatch<T> carve_batch(char* base, int pmax, int qb) {
+    const int N = pmax + 1, n = pmax - 1;
+    FdmBatch<T> b;
+    cpx<T>* c = reinterpret_cast<cpx<T>*>(base);
+    b.A = c; c += (size_t)qb * n * n;
+    b.B = c; c += (size_t)qb * n * n;
+    b.rrow = c; c += (size_t)qb * 2 * n;
+    b.rcol = c; c += (size_t)qb * 2 * n;
+    b.rho = c; c += (size_t)qb * 2 * n;
+    b.kap = c; c += (size_t)qb * 2 * n;
+    b.fidx = reinterpret_cast<short*>(c);
+    (void)N;
+    return b;
+}
+
+// A[q] <- dinv .* (V^T A[q] V) for q < Q (the divided spectral coefficients; B scratch)
+template <class T, class G>
+__device__ inline void spec_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int n, int Q) {
+    const int nn = n * n;
+    for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+        const int q = idx / nn, r = idx % nn, al = r / n, bb = r % n;
+        const cpx<T>* X = b.A + (size_t)q * nn;
+        cpx<T> v = mk<T>(0, 0);
+        for (int a = (al & 1); a < n; a += 2) fma_r(v, s.V[a * n + al], X[a * n + bb]);
+        b.B[idx] = v;
+    }
+    g.sync();
+    for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+        const int q = idx / nn, r = idx % nn, al = r / n, be = r % n;
+        const cpx<T>* X = b.B + (size_t)q * nn;
+        cpx<T> v = mk<T>(0, 0);
+        for (int bb = (be & 1); bb < n; bb += 2) fma_r(v, s.V[bb * n + be], X[al * n + bb]);
+        b.A[idx] = s.dinv[r] * v;
+    }
+    g.sync();
+}
+
+// cross values of V A[q] V^T: rrow[q][i][*] = row i, rcol[q][i][*] = column i (i = 0, 1)
+template <class T, class G>
+__device__ inline void cross_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int n, int Q) {
+    const int nn = n * n, n2 = 2 * n;
+    for (int idx = g.t(); idx < Q * n2; idx += g.n()) {
+        const int q = idx / n2, r = idx % n2, i = r / n, qq = r % n;
+        const cpx<T>* X = b.A + (size_t)q * nn;
+        cpx<T> w = mk<T>(0, 0), z = mk<T>(0, 0);
+        for (int al = (i & 1); al < n; al += 2) fma_r(w, s.V[i * n + al], X[al * n + qq]);
+        for (int be = (i & 1); be < n; be += 2) fma_r(z, s.V[i * n + be], X[qq * n + be]);
+        b.rho[idx] = w;
+        b.kap[idx] = z;
+    }
+    g.sync();
+    for (int idx = g.t(); idx < Q * n2; idx += g.n()) {
+        const int q = idx / n2, r = idx % n2, i = r / n, qq = r % n;
+        const cpx<T>* rh = b.rho + (size_t)q * n2 + i * n;
+        const cpx<T>* kp = b.kap + (size_t)q * n2 + i * n;
+        cpx<T> rr = mk<T>(0, 0), cc = mk<T>(0, 0);
+        for (int be = (qq & 1); be < n; be += 2) fma_r(rr, s.V[qq * n + be], rh[be]);
+        for (int al = (qq & 1); al < n; al += 2) fma_r(cc, s.V[qq * n + al], kp[al]);
+        b.rrow[idx] = rr;
+        b.rcol[idx] = cc;
+    }
+    g.sync();
+}
+
+// A[q] <- V A[q] V^T (full interior output; B scratch)
+template <class T, class G>
+__device__ inline void full_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int n, int Q) {
+    const int nn = n * n;
+    for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+        const int q = idx / nn, r = idx % nn, a = r / n, be = r % n;
+        const cpx<T>* X = b.A + (size_t)q * nn;
+        cpx<T> v = mk<T>(0, 0);
+        for (int al = (a & 1); al < n; al += 2) fma_r(v, s.V[a * n + al], X[al * n + be]);
+        b.B[idx] = v;
+    }
+    g.sync();
+    for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+        const int q = idx / nn, r = idx % nn, a = r / n, bb = r % n;
+        const cpx<T>* X = b.B + (size_t)q * nn;
+        cpx<T> v = mk<T>(0, 0);
+        for (int be = (bb & 1); be < n; be += 2) fma_r(v, s.V[bb * n + be], X[a * n + be]);
+        b.A[idx] = v;
+    }
+    g.sync();
+}
+
+// A tile that is zero except on the cross, where it holds the cross values of one right-hand
+// side (interior rows 0, 1 from rrow, interior columns 0, 1 below them from rcol)
+template <class T>
+struct CrossTile {
+    const cpx<T>* rrow;
+    const cpx<T>* rcol;
+    int n;
+    __device__ __forceinline__ cpx<T> operator()(int c, int d) const {
+        if (c < 2 || d < 2) return mk<T>(0, 0);
+        const int ci = c - 2, di = d - 2;
+        if (ci < 2) return rrow[ci * n + di];
+        if (di < 2) return rcol[di * n + ci];
+        return mk<T>(0, 0);
+    }
+};
+
+// The frame (vertex and edge slots) of one right-hand side: type-1 edge values xe, type-2
+// values ut; zero in the interior and on the edge coefficients above an edge's trace degree
+// (eliminated: in neither slot list, map entry -1)
+template <class T>
+struct FrameTile {
+    const short* fidx;
+    const cpx<T>* xe;
+    const cpx<T>* ut;
+    int N;
+    __device__ __forceinline__ cpx<T> operator()(int c, int d) const {
+        if (c >= 2 && d >= 2) return mk<T>(0, 0);
+        const int f = fidx[c + N * d];
+        if (f < 0) return mk<T>(0, 0);
+        return (f & 0x4000) ? ut[f & 0x3FFF] : xe[f];
+    }
+};
+
+// Interior coupling of the frame values (cross_coupling for QB right-hand sides at once):
+// rrow[q] / rcol[q] = sign * (interior rows / columns 0, 1 of A_IF Phi_F)
+template <class T, class G>
+__device__ inline void cross_coupling_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int p, T ce, T sign,
+                                        const cpx<T>* xe, const cpx<T>* ut, int stride, int Q) {
+    const int N = p + 1, n = p - 1, n2 = 2 * n;
+    for (int idx = g.t(); idx < Q * n2; idx += g.n()) {
+        const int q = idx / n2, r = idx % n2, v = r / n, be = r % n;
+        const FrameTile<T> F{b.fidx, xe + q * stride, ut + q * stride, N};
+        const int B = be + 2;
+        cpx<T> x = F(v, B);
+        cpx<T> acc = mk<T>(0, 0);
+        for (int d = B - 2; d <= B + 2; d += 2)
+            if (d >= 2 && d <= p) fma_r(acc, s.Mt[d * N + B], F(v, d));
+        for (int w = 0; w < 2; ++w) fma_r(acc, s.Mt[w * N + B], F(v, w));
+        fma_r(x, ce, acc);
+        b.rho[idx] = x;
+        const int A = be + 2;
+        cpx<T> y = F(A, v);
+        cpx<T> acc2 = mk<T>(0, 0);
+        for (int c = A - 2; c <= A + 2; c += 2)
+            if (c >= 2 && c <= p) fma_r(acc2, s.Mt[A * N + c], F(c, v));
+        fma_r(y, ce, acc2);
+        b.kap[idx] = y;
+    }
+    g.sync();
+    for (int idx = g.t(); idx < Q * n2; idx += g.n()) {
+        const int q = idx / n2, r = idx % n2, i = r / n, qq = r % n;
+        const cpx<T>* rh = b.rho + (size_t)q * n2;
+        const cpx<T>* kp = b.kap + (size_t)q * n2;
+        cpx<T> rr = mk<T>(0, 0), cc = mk<T>(0, 0);
+        for (int v = 0; v < 2; ++v) fma_r(rr, s.Mt[(i + 2) * N + v], rh[v * n + qq]);
+        for (int v = 0; v < 2; ++v) fma_r(cc, s.Mt[v * N + i + 2], kp[v * n + qq]);
+        b.rrow[idx] = sign * rr;
+        b.rcol[idx] = sign * cc;
+    }
+    g.sync();
+}
+
 // ------------------------------------------------------------------ pass 1
 // y1 = A11^-1 [r_E; r_I] with r_E = s * C1^T z + b_E, r_I = b_I (flag), then
 // tT = (A Phi)_T with Phi = [x_E; y_I; 0] (i.e. A_T1 y1).  Writes x_E and tT.
 // One CTA per (element, block of RB right-hand sides).
 template <class T, int RB>
-__global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __restrict__ sinv,
+__global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                const cpx<T>* __restrict__ Y,
                                                const double2* __restrict__ z, double zsign,
                                                const double2* __restrict__ bt, int has_bI, int R,
@@ -55,20 +233,27 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
     }
     g.sync();
     if (bt && has_bI) {
-        // r_E -= A_EI (A_II^-1 b_I) for every RHS of the block
-        for (int q = 0; q < cnt; ++q) {
-            for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
-            interior_load_cross<T>(g, s, bt, (int64_t)(r0 + q) * dm.n_local + off, p, ce);
-            cross_to_tile<T>(g, s, p, (T)1);
-            for (int i = g.t(); i < nE; i += g.n()) {
-                const int slot = dm.e1_slot[e1o + i];
-                rE[q * stride + i] -= apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+        // r_E -= A_EI (A_II^-1 b_I) and cT = A_TI (A_II^-1 b_I) for every RHS of the block, QB
+        // right-hand sides per interior transform; only the cross of A_II^-1 b_I is needed
+        const int QB = fdm_qb<T>(dm.pmax, RB), nn = n * n;
+        const FdmBatch<T> bb = carve_batch<T>(smem + pass_elem_bytes<T>(dm.pmax, RB), dm.pmax, QB);
+        for (int q0 = 0; q0 < cnt; q0 += QB) {
+            const int Q = min(QB, cnt - q0);
+            for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+                const int q = idx / nn, r = idx % nn, a = r / n, b = r % n;
+                bb.A[idx] = ld<T>(bt, (int64_t)(r0 + q0 + q) * dm.n_local + off + (a + 2) + N * (b + 2));
             }
-            if (Y)
-                for (int i = g.t(); i < nT; i += g.n()) {
-                    const int slot = dm.t_slot[to + i];
-                    cT[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
-                }
+            g.sync();
+            spec_b<T>(g, s, bb, n, Q);
+            cross_b<T>(g, s, bb, n, Q);
+            for (int idx = g.t(); idx < Q * (nE + nT); idx += g.n()) {
+                const int q = idx / (nE + nT), i = idx % (nE + nT);
+                const CrossTile<T> X{bb.rrow + (size_t)q * 2 * n, bb.rcol + (size_t)q * 2 * n, n};
+                const int slot = i < nE ? dm.e1_slot[e1o + i] : dm.t_slot[to + i - nE];
+                const cpx<T> v = apply_A_entry_f<T>(X, s.Mt, p, ce, gam, slot % N, slot / N, false);
+                if (i < nE) rE[(q0 + q) * stride + i] -= v;
+                else if (Y) cT[(q0 + q) * stride + (i - nE)] = v;
+            }
             g.sync();
         }
     }
@@ -128,7 +313,7 @@ __global__ void __launch_bounds__(128) k_pass1(DevModel dm, const cpx<T>* __rest
 // element solution (interpolatory basis) phi = [x1_E; x1_I; u_T], x1_I = A_II^-1 (b_I -
 // A_IE x1_E - A_IT u_T), into phi_out.  One CTA per (element, block of RB RHS).
 template <class T, int RB>
-__global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __restrict__ sinv,
+__global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                const cpx<T>* __restrict__ Y,
                                                const double2* __restrict__ x2, const cpx<T>* __restrict__ xE_in,
                                                cpx<T>* __restrict__ xE_out, int recover,
@@ -217,34 +402,35 @@ __global__ void __launch_bounds__(128) k_pass2(DevModel dm, const cpx<T>* __rest
     }
     g.sync();
     if (!recover) return;
-    for (int q = 0; q < cnt; ++q) {
-        const int r = r0 + q;
-        // full recovery: tile = [x1_E; 0; u_T]; x1_I = A_II^-1 (b_I - coupling)
-        for (int i = g.t(); i < N * N; i += g.n()) s.tile[i] = mk<T>(0, 0);
-        g.sync();
-        for (int i = g.t(); i < nT; i += g.n()) s.tile[dm.t_slot[to + i]] = uT[q * stride + i];
-        for (int i = g.t(); i < nE; i += g.n()) s.tile[dm.e1_slot[e1o + i]] = sE[q * stride + i];
-        g.sync();
-        cross_coupling<T>(g, s, p, ce, (T)-1);
-        for (int idx = g.t(); idx < n * n; idx += g.n()) {
-            const int a = idx / n, b = idx % n;
+    // full recovery, QB right-hand sides per interior transform: frame = [x1_E; u_T] (read through
+    // the slot map), x1_I = A_II^-1 (b_I - A_IF frame)
+    const int QB = fdm_qb<T>(dm.pmax, RB), nn = n * n;
+    const FdmBatch<T> bb = carve_batch<T>(smem + pass_elem_bytes<T>(dm.pmax, RB), dm.pmax, QB);
+    for (int i = g.t(); i < N * N; i += g.n()) bb.fidx[i] = -1;
+    g.sync();
+    for (int i = g.t(); i < nE; i += g.n()) bb.fidx[dm.e1_slot[e1o + i]] = (short)i;
+    for (int i = g.t(); i < nT; i += g.n()) bb.fidx[dm.t_slot[to + i]] = (short)(0x4000 | i);
+    g.sync();
+    for (int q0 = 0; q0 < cnt; q0 += QB) {
+        const int Q = min(QB, cnt - q0);
+        cross_coupling_b<T>(g, s, bb, p, ce, (T)-1, sE + q0 * stride, uT + q0 * stride, stride, Q);
+        for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
+            const int q = idx / nn, r = idx % nn, a = r / n, b = r % n;
             cpx<T> v = mk<T>(0, 0);
-            if (bt && has_bI) v = ld<T>(bt, (int64_t)r * dm.n_local + dm.off[e] + (a + 2) + N * (b + 2));
-            if (a < 2) v += s.rrow[a * n + b];
-            if (b < 2) v += s.rcol[b * n + a];
-            s.tmp[idx] = v;
+            if (bt && has_bI) v = ld<T>(bt, (int64_t)(r0 + q0 + q) * dm.n_local + dm.off[e] + (a + 2) + N * (b + 2));
+            if (a < 2) v += bb.rrow[(size_t)q * 2 * n + a * n + b];
+            if (b < 2) v += bb.rcol[(size_t)q * 2 * n + b * n + a];
+            bb.A[idx] = v;
         }
         g.sync();
-        spec_from_full<T>(g, s, n);
-        spec_divide<T>(g, s, n);
-        full_from_spec<T>(g, s, n);
-        const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
-        for (int idx = g.t(); idx < N * N; idx += g.n()) {
-            const int a = idx % N, b = idx / N;
+        spec_b<T>(g, s, bb, n, Q);
+        full_b<T>(g, s, bb, n, Q);
+        for (int idx = g.t(); idx < Q * N * N; idx += g.n()) {
+            const int q = idx / (N * N), r = idx % (N * N), a = r % N, b = r / N;
             cpx<T> v;
-            if (a >= 2 && b >= 2) v = s.spec[(a - 2) * n + (b - 2)];
-            else v = s.tile[idx];
-            st<T>(phi_out, base + idx, v);
+            if (a >= 2 && b >= 2) v = bb.A[(size_t)q * nn + (a - 2) * n + (b - 2)];
+            else v = FrameTile<T>{bb.fidx, sE + (q0 + q) * stride, uT + (q0 + q) * stride, N}(a, b);
+            st<T>(phi_out, (int64_t)(r0 + q0 + q) * dm.n_local + dm.off[e] + r, v);
         }
         g.sync();
     }
@@ -261,10 +447,10 @@ void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const dou
     const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     switch (rb) {
-        case 8: k_pass1<T, 8><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 4: k_pass1<T, 4><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 2: k_pass1<T, 2><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        default: k_pass1<T, 1><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
+        case 8: k_pass1<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 4: k_pass1<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        case 2: k_pass1<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
+        default: k_pass1<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
     }
 }
 // shared memory of the edge-operator pass 1: r_E and x_E blocks, then (when it fits) the
@@ -281,10 +467,10 @@ void launch_pass2(const DevModel& dm, const void* sinv, const void* Y, const dou
     const cpx<T>* xi = (const cpx<T>*)xE_in;
     cpx<T>* xo = (cpx<T>*)xE_out;
     switch (rb) {
-        case 8: k_pass2<T, 8><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 4: k_pass2<T, 4><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 2: k_pass2<T, 2><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        default: k_pass2<T, 1><<<g, 128, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
+        case 8: k_pass2<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 4: k_pass2<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        case 2: k_pass2<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
+        default: k_pass2<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
     }
 }
 // dynamic shared-memory limits of one pass in precision T, for every RHS block size

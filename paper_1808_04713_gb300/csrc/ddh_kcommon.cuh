@@ -86,8 +86,26 @@ __device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, con
 // right-hand sides per CTA of the element kernels
 inline int rhs_block(int R) { return R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1)); }
 
+// FDM passes: right-hand sides transformed together per barrier interval (QB of them), sized so
+// that their tiles take at most about 48 KB of shared memory
 template <class T>
-inline size_t pass_smem_t(int pmax, int rb) { return (elem_smem_bytes<T>(pmax, 3 * rb * 4 * (pmax + 1)) + 127) & ~(size_t)127; }
+__host__ __device__ inline int fdm_qb(int pmax, int rb) {
+    const int n = pmax - 1;
+    const size_t per = sizeof(cpx<T>) * (size_t)(2 * n * n + 8 * n);
+    const int q = (int)((48 * 1024) / per);
+    return q < 1 ? 1 : (q > rb ? rb : q);
+}
+template <class T>
+__host__ __device__ inline size_t fdm_batch_bytes(int pmax, int qb) {
+    const int N = pmax + 1, n = pmax - 1;
+    return ((sizeof(cpx<T>) * (size_t)qb * (2 * n * n + 8 * n) + sizeof(short) * (size_t)N * N + 127) & ~(size_t)127);
+}
+template <class T>
+__host__ __device__ inline size_t pass_elem_bytes(int pmax, int rb) {
+    return (elem_smem_bytes<T>(pmax, 3 * rb * 4 * (pmax + 1)) + 127) & ~(size_t)127;
+}
+template <class T>
+inline size_t pass_smem_t(int pmax, int rb) { return pass_elem_bytes<T>(pmax, rb) + fdm_batch_bytes<T>(pmax, fdm_qb<T>(pmax, rb)); }
 // shared-memory staging of S_E^-1 when it fits: returns the staging offset (0 = no staging)
 template <class T>
 inline int pass_stage_off(int pmax, int rb, int maxE1) {

@@ -149,10 +149,11 @@ __device__ __forceinline__ T kt(int a, int c) {
     return a == c ? (T)1 : (T)0;
 }
 
-// (A Phi)[a][b] from the tile; gam[s] = imaginary part of gamma_eff on side s (0 if interior).
-template <class T>
-__device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ce, const T* gam,
-                                        int a, int b, bool stiff_only, bool no_stiff = false) {
+// (A Phi)[a][b] with Phi read through `tile(c, d)`; gam[s] = imaginary part of gamma_eff on
+// side s (0 if none).
+template <class T, class F>
+__device__ inline cpx<T> apply_A_entry_f(const F& tile, const T* Mt, int p, T ce, const T* gam,
+                                          int a, int b, bool stiff_only, bool no_stiff = false) {
     const int N = p + 1;
     int ca[6], cb[6];
     const int na = cand_list(a, p, ca), nb = cand_list(b, p, cb);
@@ -165,20 +166,35 @@ __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T
             const T Mbd = Mt[b * N + d];
             T w = no_stiff ? (T)0 : Kac * Mbd + Mac * kt<T>(b, d);
             if (!stiff_only) w += ce * Mac * Mbd;
-            if (w != (T)0) fma_r(acc, w, tile[c + N * d]);
+            if (w != (T)0) fma_r(acc, w, tile(c, d));
         }
     }
     if (!stiff_only) {
         cpx<T> rob = mk<T>(0, 0);
-        if (a == 1 && gam[0] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile[1 + N * cb[j]]); rob += gam[0] * s; }
-        if (a == 0 && gam[1] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile[0 + N * cb[j]]); rob += gam[1] * s; }
-        if (b == 1 && gam[2] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile[ca[i] + N * 1]); rob += gam[2] * s; }
-        if (b == 0 && gam[3] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile[ca[i] + N * 0]); rob += gam[3] * s; }
+        if (a == 1 && gam[0] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile(1, cb[j])); rob += gam[0] * s; }
+        if (a == 0 && gam[1] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile(0, cb[j])); rob += gam[1] * s; }
+        if (b == 1 && gam[2] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile(ca[i], 1)); rob += gam[2] * s; }
+        if (b == 0 && gam[3] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile(ca[i], 0)); rob += gam[3] * s; }
         // gamma is purely imaginary: i*g*(x + i y) = (-g y, g x)
         acc.x -= rob.y;
         acc.y += rob.x;
     }
+    (void)N;
     return acc;
+}
+
+template <class T>
+struct TileRef {
+    const cpx<T>* tile;
+    int N;
+    __device__ __forceinline__ cpx<T> operator()(int c, int d) const { return tile[c + N * d]; }
+};
+
+// (A Phi)[a][b] from the tile (N x N, column-major)
+template <class T>
+__device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ce, const T* gam,
+                                        int a, int b, bool stiff_only, bool no_stiff = false) {
+    return apply_A_entry_f<T>(TileRef<T>{tile, p + 1}, Mt, p, ce, gam, a, b, stiff_only, no_stiff);
 }
 
 // Interior coupling of the frame values: coupling = Mt_BV X + Y Mt_VB with

@@ -26,11 +26,21 @@ struct KrylovDev {
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign, const double2* bt,
                   int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+// Work list of the persistent edge pass: elements by degree, descending, and the tuned threads
+// per output row of each degree (index p; 0 = default)
+struct EdgeSched {
+    const int* items = nullptr;
+    const signed char* tpr_p = nullptr;
+};
 // Krylov-loop passes with the explicit edge operators Y = [A11^-1 A_1T]_E (no FDM; pass 1
-// requires a load without interior components, pass 2 no recovery)
+// requires a load without interior components, pass 2 no recovery).  With es (and es->items)
+// pass 1 is one persistent launch over items[item0 .. item0 + nitems) (nitems < 0: all
+// elements) with the S_E^-1 copy of the next task in flight; tpr_force > 0 overrides the
+// per-degree threads per output row (autotuning)
 template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
-                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+                       const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
+                       const EdgeSched* es = nullptr, int item0 = 0, int nitems = -1, int tpr_force = 0);
 template <class T>
 void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
                        const int* done, cudaStream_t st);

@@ -68,6 +68,7 @@ _SIGS = {
     "ddh_primal_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_primal_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_apply_dual_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "ddh_get_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
     "ddh_profile_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "ddh_last_error": (C.c_char_p, [C.c_void_p]),
@@ -251,6 +252,19 @@ class DDH:
         self._check(self.lib.ddh_apply_dual_operator(self.h, int(which), _ptr(v), _ptr(out), int(v.shape[0]),
                                                      int(precision)))
         return out
+
+    def get_tuning(self, R: int, precision: int = PREC_FP64) -> dict:
+        """Autotuner choices for R right-hand sides: the launch form of the edge pass (1
+        persistent, 0 one CTA per task, -1 untuned), its threads per output row by degree, and
+        the right-hand-side block of each nested-dissection level launch."""
+        tpr = np.zeros(33, np.int32)
+        nd = np.zeros(128, np.int32)
+        L = C.c_int32()
+        ep = C.c_int32()
+        self._check(self.lib.ddh_get_tuning(self.h, int(R), int(precision), C.byref(ep), tpr.ctypes.data,
+                                            nd.ctypes.data, C.byref(L)))
+        return {"edge_persistent": int(ep.value), "tpr_by_degree": {int(p): int(t) for p, t in enumerate(tpr) if t},
+                "nd_rb_forward": nd[:L.value].tolist(), "nd_rb_backward": nd[L.value:2 * L.value].tolist()}
 
     def profile_op(self, R: int, precision: int = PREC_FP64, reps: int = 20) -> np.ndarray:
         """Average ms per launch: pass1, coarse assembly, coarse solve, pass2, jump gather, precond."""
