@@ -123,6 +123,11 @@ typedef struct {
                               [x_E; t_T] = [S_E^-1; Y^T] r_E of the complex64 inner solves runs on
                               the tcgen05 tensor cores in TF32 (operands rounded to 10-bit
                               mantissas, FP32 accumulation); 0 (default) = FP32 CUDA cores */
+    int32_t inner_krylov_fp32; /* mixed precision: 1 (default) = the inner dual FGMRES keeps its
+                              Krylov basis in complex64 and runs the CGS2 projections, dot
+                              products and norms in FP32 (per-chunk partial sums, the Hessenberg
+                              column, the Givens rotations and the iterate update stay FP64);
+                              0 = complex128 basis and FP64 arithmetic, as the outer FGMRES */
 } ddh_options;
 
 typedef struct {
@@ -260,10 +265,13 @@ ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const vo
  *                      the pass has not been tuned for this R);
  *   nd_rb[2 L]         right-hand sides per CTA of each nested-dissection level launch (forward
  *                      levels 0 .. L-1, then backward; 0 = level not launched on its own), with
- *                      L written to *nd_levels (0 when the dense K^-1 is in use or not yet tuned).
+ *                      L written to *nd_levels (0 when the dense K^-1 is in use or not yet tuned);
+ *   *nd_chains         2 when the per-level solve runs as two chains over the two halves of the
+ *                      right-hand sides on forked streams (their level launches then use the
+ *                      tuning of R/2), 1 for one chain, 0 when not tuned.
  * nd_rb may be NULL; otherwise it must hold 128 entries (L <= 64).  Host arrays. */
 ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
-                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels);
+                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels, int32_t* nd_chains);
 
 /* Apply one of the two operators of the dual iteration to caller-given dual vectors (for
  * checks of the hot path against a reference; the solves apply the same code):

@@ -35,6 +35,7 @@ struct GraphKey {
 struct KState {
     KrylovDev K{};
     int R = 0, m = 0, nd = 0;
+    bool b32 = false;           // complex64 basis (K.Vf)
     std::vector<void*> allocs;
     double2* r = nullptr;
     double* nrm2 = nullptr;
@@ -96,6 +97,9 @@ struct ddh_ctx {
     std::vector<int> nd_fwd_off, nd_fwd_n, nd_fwd_rows;   // per level: first item, items, staged rows
     std::vector<int> nd_bwd_off, nd_bwd_n, nd_bwd_rows;
     std::map<int, std::vector<int>> nd_rb;         // per R: tuned RHS block of each level (fwd, then bwd)
+    std::map<int, int> nd_chains;                  // per R: 2 = two half-R level chains on forked streams
+    cudaStream_t stream2 = nullptr;                // second stream of the forked coarse solve
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     NDSched nd_sched;                              // one-launch schedule of the same items
     bool nd_levels = false;                        // one launch per tree level instead
     bool coarse32 = false;                         // current inner solves use the complex64 copy
@@ -131,6 +135,17 @@ void ctx_add_launches(ddh_ctx* c, int n) { c->launches += n; }
         if (e_ != cudaSuccess) {                                                 \
             ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
             return DDH_ERR_CUDA;                                                 \
+        }                                                                        \
+    } while (0)
+
+// for void helpers: record the failure and return; the error stays pending for the caller's
+// CK(cudaGetLastError())
+#define CK_VOID(call)                                                            \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) {                                                 \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            return;                                                              \
         }                                                                        \
     } while (0)
 
@@ -801,6 +816,13 @@ struct Work {
 // CTA) and keep the fastest.  A level of few large fronts runs faster with small blocks (more
 // CTAs), a level of many small fronts with large ones (each staged vector serves more
 // right-hand sides).  Runs once per R, before any graph capture, on the work buffers (cleared).
+static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done);
+
+// Autotuner of the per-level nested-dissection solve for R right-hand sides: for each level
+// launch, the right-hand sides per CTA (powers of two up to the level's limit), then whether two
+// chains over the two halves of the right-hand sides, on forked streams, beat one chain (the
+// tail of one chain's level launch overlaps the other chain's work).  Runs once per R, before
+// any graph capture, on cleared work buffers.
 static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
     if (ctx->Kinv || !ctx->nd_levels || ctx->nd_rb.count(R)) return DDH_OK;
     const int L = (int)ctx->nd_fwd_rows.size();
@@ -842,10 +864,32 @@ static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
                 if (ms < 0.97f * tbest) { tbest = ms; best[(size_t)dir * L + lv] = rb; }
             }
         }
+    CK(cudaGetLastError());
+    ctx->nd_rb[R] = best;
+    ctx->nd_chains[R] = 1;
+    if (R >= 4 && R % 2 == 0 && ctx->stream2) {
+        ddh_status st;
+        if ((st = nd_tune(ctx, w, R / 2))) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+        float tm[2] = {0, 0};
+        for (int form = 0; form < 2; ++form) {
+            ctx->nd_chains[R] = form + 1;
+            auto run = [&] { coarse_solve_once(ctx, w.t, w.x2, w.ctmp, R, nullptr); };
+            run();
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 5; ++rep) run();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&tm[form], e0, e1);
+        }
+        ctx->nd_chains[R] = tm[1] < 0.97f * tm[0] ? 2 : 1;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
-    ctx->nd_rb[R] = best;
     return DDH_OK;
 }
 
@@ -996,6 +1040,9 @@ static void coarse_solve(ddh_ctx* ctx, const double2* t, double2* x2, double2* t
     ctx->launches += 2;
 }
 
+static void nd_level_chain(ddh_ctx* ctx, const NDDev& D, bool f32nd, const double2* t, double2* y, double2* x2,
+                           double2* u, int R, const int* done, cudaStream_t s);
+
 static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done) {
     const int nc = ctx->dm.n_coarse;
     cudaStream_t s = ctx->stream;
@@ -1016,6 +1063,28 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
         ctx->launches++;
         return;
     }
+    const auto ch = ctx->nd_chains.find(R);
+    if (ch != ctx->nd_chains.end() && ch->second == 2) {
+        // two chains over right-hand sides [0, R/2) and [R/2, R) (vectors are [R][n], so a half
+        // is a pointer offset); the second runs on stream2 between a fork and a join event
+        const int Ra = R / 2;
+        const int64_t ul = D.u_len;
+        CK_VOID(cudaEventRecord(ctx->ev_fork, s));
+        CK_VOID(cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork, 0));
+        nd_level_chain(ctx, D, f32nd, t + (size_t)Ra * nc, y + (size_t)Ra * nc, x2 + (size_t)Ra * nc,
+                       u + (size_t)Ra * ul, R - Ra, done, ctx->stream2);
+        nd_level_chain(ctx, D, f32nd, t, y, x2, u, Ra, done, s);
+        CK_VOID(cudaEventRecord(ctx->ev_join, ctx->stream2));
+        CK_VOID(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+        return;
+    }
+    nd_level_chain(ctx, D, f32nd, t, y, x2, u, R, done, s);
+}
+
+// The per-level launches of one nested-dissection solve for right-hand sides [0, R) of t, y,
+// x2 and u, on stream s
+static void nd_level_chain(ddh_ctx* ctx, const NDDev& D, bool f32nd, const double2* t, double2* y, double2* x2,
+                           double2* u, int R, const int* done, cudaStream_t s) {
     const int L = (int)ctx->nd_fwd_rows.size();
     // subtree launches pay off when the launches are latency-bound (few right-hand sides); with
     // more right-hand sides the serial node chain inside a subtree costs more than it saves
@@ -1107,12 +1176,15 @@ void KState::release() {
     h_ctl = nullptr;
     h_resid = nullptr;
     R = m = nd = 0;
+    b32 = false;
+    K.V = nullptr;
+    K.Vf = nullptr;
     iter_hint = 0;
 }
 
-static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) {
+static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m, bool b32 = false) {
     nd = std::max(1, nd);
-    if (ks.R == R && ks.m == m && ks.nd == nd) return DDH_OK;
+    if (ks.R == R && ks.m == m && ks.nd == nd && ks.b32 == b32) return DDH_OK;
     cudaStreamSynchronize(ctx->stream);
     ks.release();
     KrylovDev& K = ks.K;
@@ -1129,7 +1201,11 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     };
     void* p;
     bool ok = true;
-    ok &= al(sizeof(double2) * (size_t)R * (m + 1) * nd, &p); K.V = (double2*)p;
+    if (b32) {
+        ok &= al(sizeof(float2) * (size_t)R * (m + 1) * nd, &p); K.Vf = (float2*)p; K.V = nullptr;
+    } else {
+        ok &= al(sizeof(double2) * (size_t)R * (m + 1) * nd, &p); K.V = (double2*)p; K.Vf = nullptr;
+    }
     ok &= al(sizeof(double2) * (size_t)R * m * nd, &p); K.Zb = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * m * (m + 1), &p); K.H = (double2*)p;
     ok &= al(sizeof(double) * (size_t)R * m, &p); K.cs = (double*)p;
@@ -1156,7 +1232,7 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m) 
     if (!ok) { ctx->err = "cudaMalloc failed (Krylov state)"; return DDH_ERR_OOM; }
     CK(cudaMallocHost((void**)&ks.h_ctl, sizeof(int) * (4 + 2 * (size_t)R)));
     CK(cudaMallocHost((void**)&ks.h_resid, sizeof(double) * (size_t)R));
-    ks.R = R; ks.m = m; ks.nd = nd;
+    ks.R = R; ks.m = m; ks.nd = nd; ks.b32 = b32;
     return DDH_OK;
 }
 
@@ -1241,13 +1317,13 @@ static void host_upper_solve(int n, int m, const std::complex<double>* Hcols, co
 // (Givens estimate) or after maxit iterations; x_out receives the iterates.
 static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, const double2* bvec, double2* x_out,
                              int nd, int R, int m, double tol, int maxit, int check_every,
-                             std::vector<int>& its, std::vector<double>& res, bool warm = false) {
+                             std::vector<int>& its, std::vector<double>& res, bool warm = false, bool b32 = false) {
     its.assign(R, 0);
     res.assign(R, 0.0);
     if (!warm) CK(cudaMemsetAsync(x_out, 0, sizeof(double2) * (size_t)R * std::max(1, nd), ctx->stream));
     if (nd == 0) return DDH_OK;
     ddh_status st;
-    if ((st = ensure_krylov(ctx, ks, nd, R, m))) return st;
+    if ((st = ensure_krylov(ctx, ks, nd, R, m, b32))) return st;
     KrylovDev& K = ks.K;
     K.tol = tol;
     if (ks.graph_tol != tol) {            // tol is a kernel parameter of the captured graph
@@ -1291,7 +1367,8 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
             g0[(size_t)i * (m + 1)] = make_double2(active[i] ? nr : 0.0, 0);
             rd[i] = active[i] ? 0 : 1;
             const double sc = (active[i] && nr > 0) ? 1.0 / nr : 0.0;
-            launch_axpby(r + (size_t)i * nd, sc, nullptr, 0.0, K.V + (size_t)i * (m + 1) * nd, nd, ctx->stream);
+            if (K.Vf) launch_scale_f32(r + (size_t)i * nd, sc, K.Vf + (size_t)i * (m + 1) * nd, nd, ctx->stream);
+            else launch_axpby(r + (size_t)i * nd, sc, nullptr, 0.0, K.V + (size_t)i * (m + 1) * nd, nd, ctx->stream);
             ctx->launches++;
         }
         CK(cudaMemcpyAsync(K.g, g0.data(), sizeof(double2) * g0.size(), cudaMemcpyHostToDevice, ctx->stream));
@@ -1408,7 +1485,9 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
     // (the interior FDM terms of the load are skipped when the load has no interior part)
     const int has_bI = interior ? 1 : 0;
     apply_op<T>(ctx, w, nullptr, 0.0, bt, has_bI, (double2*)g, nullptr, R, nullptr);
-    if ((st = ensure_krylov(ctx, ctx->kin, d.n_dual, R, restart))) return st;
+    // the inner solves of the mixed form keep their Krylov basis in complex64
+    const bool b32 = std::is_same<T, float>::value && ctx->opt.inner_krylov_fp32 != 0;
+    if ((st = ensure_krylov(ctx, ctx->kin, d.n_dual, R, restart, b32))) return st;
     KrylovOps ops = dual_ops<T>(ctx, w);
     double tol_d = tol;
     double last_worst = 1e300;
@@ -1419,7 +1498,7 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
         int left = maxit;
         for (int i = 0; i < R; ++i) left = std::min(left, maxit - its[i]);
         if ((st = fgmres_run(ctx, ctx->kin, ops, (const double2*)g, (double2*)nu, d.n_dual, R, restart, tol_d,
-                             std::max(1, left), check_every, its_c, res_c, round > 0)))
+                             std::max(1, left), check_every, its_c, res_c, round > 0, b32)))
             return st;
         for (int i = 0; i < R; ++i) its[i] += its_c[i];
         res = res_c;
@@ -1612,6 +1691,7 @@ void ddh_default_options(ddh_options* o) {
     o->coarse_form = DDH_COARSE_AUTO;
     o->robin_modified = 0;
     o->tensor_cores = 0;
+    o->inner_krylov_fp32 = 1;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1627,6 +1707,15 @@ ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
     } else {
         if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return DDH_ERR_CUDA; }
         ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        delete ctx;
+        return DDH_ERR_CUDA;
     }
     *out = ctx;
     return DDH_OK;
@@ -1893,8 +1982,10 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
 }
 
 ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
-                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels) {
-    if (!ctx || !edge_persistent || !tpr_by_degree || !nd_levels || R <= 0) return DDH_ERR_INVALID_ARG;
+                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels, int32_t* nd_chains) {
+    if (!ctx || !edge_persistent || !tpr_by_degree || !nd_levels || !nd_chains || R <= 0) return DDH_ERR_INVALID_ARG;
+    const auto ct = ctx->nd_chains.find(R);
+    *nd_chains = ct == ctx->nd_chains.end() ? 0 : ct->second;
     if (!ctx->factored) return DDH_ERR_NOT_READY;
     for (int p = 0; p < 33; ++p) tpr_by_degree[p] = 0;
     const int ekey = edge_key(precision == DDH_PREC_FP64, R);
@@ -2019,6 +2110,9 @@ void ddh_destroy(ddh_ctx* ctx) {
     cudaSetDevice(ctx->device);
     free_model(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaStreamDestroy(ctx->stream2);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 

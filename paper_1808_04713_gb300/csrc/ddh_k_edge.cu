@@ -415,8 +415,13 @@ __global__ void __launch_bounds__(128) k_pre_elem_kry(DevModel dm, KrylovDev K, 
         const int row = dm.e1_row[e1o + i];
         cpx<T> val = mk<T>(0, 0);
         if (row >= 0) {
-            const double2* v = K.V + ((int64_t)(r0 + q) * (K.m + 1) + jj) * K.nd;
-            val = (T)(0.5 * dm.e1_sign[e1o + i]) * ld<T>(v, row);
+            const int64_t at = ((int64_t)(r0 + q) * (K.m + 1) + jj) * K.nd + row;
+            if (K.Vf) {
+                const float2 x = K.Vf[at];
+                val = (T)(0.5 * dm.e1_sign[e1o + i]) * mk<T>((T)x.x, (T)x.y);
+            } else {
+                val = (T)(0.5 * dm.e1_sign[e1o + i]) * ld<T>(K.V, at);
+            }
         }
         in[q * nE + i] = val;
     }

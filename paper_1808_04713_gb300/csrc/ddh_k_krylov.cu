@@ -8,6 +8,22 @@ namespace ddh {
 // ------------------------------------------------------------------ FGMRES (FP64)
 // State layout per RHS r: V[r][j][nd] (j <= m), Zb[r][j][nd] (j < m), H[r][j][m+1] column j,
 // cs[r][m], sn[r][m], g[r][m+1], bnorm[r]; ctl = {j, all_done, ...}; done[r]; iters[r].
+// The basis is complex128 (V) or, for the inner solves of the mixed form, complex64 (Vf, V
+// null); the orthogonalisation kernels are templates on the basis element B and compute in its
+// precision.  Partial dots, the Hessenberg column, the rotations and the iterate update are
+// FP64 either way.
+
+template <class B> struct BasisT;
+template <> struct BasisT<double2> { using S = double; };
+template <> struct BasisT<float2> { using S = float; };
+template <class B> __device__ __forceinline__ B* basis(const KrylovDev& K);
+template <> __device__ __forceinline__ double2* basis<double2>(const KrylovDev& K) { return K.V; }
+template <> __device__ __forceinline__ float2* basis<float2>(const KrylovDev& K) { return K.Vf; }
+template <class B> __device__ __forceinline__ B to_b(double2 v);
+template <> __device__ __forceinline__ double2 to_b<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 to_b<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_d(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d(float2 v) { return make_double2((double)v.x, (double)v.y); }
 
 
 __global__ void k_fetch(KrylovDev K) {
@@ -15,7 +31,8 @@ __global__ void k_fetch(KrylovDev K) {
     const int j = K.ctl[0];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y;
     if (i >= K.nd) return;
-    K.vin[(int64_t)r * K.nd + i] = K.V[((int64_t)r * (K.m + 1) + j) * K.nd + i];
+    const int64_t at = ((int64_t)r * (K.m + 1) + j) * K.nd + i;
+    K.vin[(int64_t)r * K.nd + i] = K.Vf ? to_d(K.Vf[at]) : K.V[at];
 }
 
 __global__ void k_store(KrylovDev K) {
@@ -38,19 +55,22 @@ __global__ void k_store(KrylovDev K) {
 // with the exact norm of the stored vector, so V_{j+1} has unit norm to rounding either way.
 
 // warp-per-basis-vector partial dots of the chunk: partial[r][chunk][i] = sum conj(V_i) ws
+template <class B>
 __device__ __forceinline__ void cgs_chunk_dots(const KrylovDev& K, int j, int r, int chunk, int q0, int rows,
-                                               const double2* ws) {
+                                               const B* ws) {
+    using S = typename BasisT<B>::S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const B* Vb = basis<B>(K);
     for (int i = warp; i <= j; i += nw) {
-        const double2* v = K.V + ((int64_t)r * (K.m + 1) + i) * K.nd + q0;
-        double sx = 0, sy = 0;
+        const B* v = Vb + ((int64_t)r * (K.m + 1) + i) * K.nd + q0;
+        S sx = 0, sy = 0;
         for (int t = lane; t < rows; t += 32) {
-            const double2 a = v[t], b = ws[t];
+            const B a = v[t], b = ws[t];
             sx = fma(a.x, b.x, fma(a.y, b.y, sx));
             sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
         }
         for (int o = 16; o > 0; o >>= 1) { sx += __shfl_xor_sync(0xffffffffu, sx, o); sy += __shfl_xor_sync(0xffffffffu, sy, o); }
-        if (lane == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + i] = make_double2(sx, sy);
+        if (lane == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + i] = make_double2((double)sx, (double)sy);
     }
 }
 
@@ -107,29 +127,31 @@ __device__ __forceinline__ void cgs_reduce(const KrylovDev& K, int j, int r, dou
     }
 }
 
+template <class B>
 __global__ void __launch_bounds__(256) k_cgs_first(KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
     const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
-    extern __shared__ __align__(16) double2 ws[];          // [K.chunk]
+    extern __shared__ __align__(16) double2 ws_raw[];
+    B* ws = reinterpret_cast<B*>(ws_raw);                  // [K.chunk]
     __shared__ int last_f;
-    for (int t = threadIdx.x; t < rows; t += blockDim.x) ws[t] = K.w[(int64_t)r * K.nd + q0 + t];
+    for (int t = threadIdx.x; t < rows; t += blockDim.x) ws[t] = to_b<B>(K.w[(int64_t)r * K.nd + q0 + t]);
     __syncthreads();
-    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    cgs_chunk_dots<B>(K, j, r, chunk, q0, rows, ws);
     if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
 }
 
 // Jump gather w = C^ x fused with the first CGS pass: the CTA that forms rows
 // [q0, q0 + 128) of w also takes their partial dots with V_0..V_j (chunk = 128 rows).
-template <class T>
+template <class T, class B>
 __global__ void __launch_bounds__(128) k_jump_gather_dots(DevModel dm, const cpx<T>* __restrict__ xE,
                                                           const double2* __restrict__ x2, KrylovDev K) {
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
     const int q0 = chunk * 128, rows = min(128, K.nd - q0);
-    __shared__ double2 ws[128];
+    __shared__ B ws[128];
     __shared__ int last_f;
     if ((int)threadIdx.x < rows) {
         const int row = q0 + threadIdx.x;
@@ -144,40 +166,44 @@ __global__ void __launch_bounds__(128) k_jump_gather_dots(DevModel dm, const cpx
         }
         const double2 wv = make_double2(sx, sy);
         K.w[(int64_t)r * K.nd + row] = wv;
-        ws[threadIdx.x] = wv;
+        ws[threadIdx.x] = to_b<B>(wv);
     }
     __syncthreads();
-    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    cgs_chunk_dots<B>(K, j, r, chunk, q0, rows, ws);
     if (cgs_last_chunk(K, r, &last_f)) cgs_reduce(K, j, r, K.hcol + (int64_t)r * (K.m + 1), false);
 }
+template <class B>
 __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
+    using S = typename BasisT<B>::S;
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
     const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
-    extern __shared__ __align__(16) double2 ws[];          // [K.chunk]
-    __shared__ double2 h[256];
+    extern __shared__ __align__(16) double2 ws_raw[];
+    B* ws = reinterpret_cast<B*>(ws_raw);                  // [K.chunk]
+    __shared__ B h[256];
     __shared__ double red[8];
     __shared__ int last_f;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = K.hcol[(int64_t)r * (K.m + 1) + i];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = to_b<B>(K.hcol[(int64_t)r * (K.m + 1) + i]);
     __syncthreads();
-    double nrm = 0;
+    const B* Vb = basis<B>(K);
+    S nrm = 0;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
         const int64_t q = q0 + t;
-        double2 w = K.w[(int64_t)r * K.nd + q];
+        B w = to_b<B>(K.w[(int64_t)r * K.nd + q]);
         for (int i = 0; i <= j; ++i) {
-            const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
-            const double2 hh = h[i];
+            const B v = Vb[((int64_t)r * (K.m + 1) + i) * K.nd + q];
+            const B hh = h[i];
             w.x -= v.x * hh.x - v.y * hh.y;
             w.y -= v.x * hh.y + v.y * hh.x;
         }
-        K.w[(int64_t)r * K.nd + q] = w;
+        K.w[(int64_t)r * K.nd + q] = to_d(w);
         ws[t] = w;
         nrm += w.x * w.x + w.y * w.y;
     }
-    nrm = block_sum(nrm, red);          // also orders the ws writes before the dots
-    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nrm, 0.0);
-    cgs_chunk_dots(K, j, r, chunk, q0, rows, ws);
+    const double nrm_b = block_sum((double)nrm, red);   // also orders the ws writes before the dots
+    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nrm_b, 0.0);
+    cgs_chunk_dots<B>(K, j, r, chunk, q0, rows, ws);
     if (cgs_last_chunk(K, r, &last_f)) {
         double2* h2 = K.h2 + (int64_t)r * (K.m + 1);
         cgs_reduce(K, j, r, h2, true);           // h2[0..j]; h2[j+1] = (||w1||^2, 0)
@@ -196,36 +222,40 @@ __global__ void __launch_bounds__(256) k_cgs_second(KrylovDev K) {
     }
 }
 
+template <class B>
 __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
+    using S = typename BasisT<B>::S;
     if (K.ctl[1]) return;
     const int j = K.ctl[0];
     const int chunk = blockIdx.x, r = blockIdx.y;
     const int q0 = chunk * K.chunk, rows = min(K.chunk, K.nd - q0);
-    __shared__ double2 h[256];
+    __shared__ B h[256];
     __shared__ double red[8];
     __shared__ int last_f;
     __shared__ double hn_s;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = K.h2[(int64_t)r * (K.m + 1) + i];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h[i] = to_b<B>(K.h2[(int64_t)r * (K.m + 1) + i]);
     __syncthreads();
     const double hp = K.hn[r];
     const double sc = hp > 0 ? 1.0 / hp : 1.0;
-    double2* vnew = K.V + ((int64_t)r * (K.m + 1) + j + 1) * K.nd;
-    double nv = 0;
+    const S scs = (S)sc;
+    B* Vb = basis<B>(K);
+    B* vnew = Vb + ((int64_t)r * (K.m + 1) + j + 1) * K.nd;
+    S nv = 0;
     for (int t = threadIdx.x; t < rows; t += blockDim.x) {
         const int64_t q = q0 + t;
-        double2 w = K.w[(int64_t)r * K.nd + q];
+        B w = to_b<B>(K.w[(int64_t)r * K.nd + q]);
         for (int i = 0; i <= j; ++i) {
-            const double2 v = K.V[((int64_t)r * (K.m + 1) + i) * K.nd + q];
-            const double2 hh = h[i];
+            const B v = Vb[((int64_t)r * (K.m + 1) + i) * K.nd + q];
+            const B hh = h[i];
             w.x -= v.x * hh.x - v.y * hh.y;
             w.y -= v.x * hh.y + v.y * hh.x;
         }
-        w.x *= sc; w.y *= sc;
+        w.x *= scs; w.y *= scs;
         vnew[q] = w;
         nv += w.x * w.x + w.y * w.y;
     }
-    nv = block_sum(nv, red);
-    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nv, 0.0);
+    const double nv_b = block_sum((double)nv, red);
+    if (threadIdx.x == 0) K.partial[((int64_t)r * K.nchunk + chunk) * (K.m + 1) + K.m] = make_double2(nv_b, 0.0);
     if (!cgs_last_chunk(K, r, &last_f)) return;
 
     // ---- last CTA of right-hand side r: exact norm, Hessenberg column, Givens
@@ -240,11 +270,14 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
     __syncthreads();
     const double nvt = nvs.x;
     const double hn = nvt > 0 ? sqrt(nvt) / sc : 0.0;
-    if (nvt > 0 && fabs(nvt - 1.0) > 1e-12) {
+    // a complex64 basis vector's norm is only known to FP32 rounding: rescale it only when the
+    // estimate was far off
+    const double rescale_gap = sizeof(S) == 4 ? 1e-3 : 1e-12;
+    if (nvt > 0 && fabs(nvt - 1.0) > rescale_gap) {
         // the Pythagorean estimate was off (near breakdown): rescale V_{j+1} to unit norm
-        const double f = 1.0 / sqrt(nvt);
+        const S f = (S)(1.0 / sqrt(nvt));
         for (int q = threadIdx.x; q < K.nd; q += blockDim.x) {
-            double2 v = __ldcg(vnew + q);
+            B v = __ldcg(vnew + q);
             v.x *= f; v.y *= f;
             vnew[q] = v;
         }
@@ -321,7 +354,8 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
 template <class T>
 void launch_jump_gather_dots(const DevModel& dm, const void* xE, const double2* x2, const KrylovDev& K,
                              cudaStream_t st) {
-    k_jump_gather_dots<T><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
+    if (K.Vf) k_jump_gather_dots<T, float2><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
+    else k_jump_gather_dots<T, double2><<<dim3(K.nchunk, K.R), 128, 0, st>>>(dm, (const cpx<T>*)xE, x2, K);
 }
 template void launch_jump_gather_dots<double>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
 template void launch_jump_gather_dots<float>(const DevModel&, const void*, const double2*, const KrylovDev&, cudaStream_t);
@@ -348,6 +382,12 @@ __global__ void k_axpby(const double2* x, double a, const double2* y, double b, 
     const double2 xv = x[i];
     const double2 yv = y ? y[i] : make_double2(0, 0);
     out[i] = make_double2(a * xv.x + b * yv.x, a * xv.y + b * yv.y);
+}
+__global__ void k_scale_f32(const double2* x, double a, float2* out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 xv = x[i];
+    out[i] = make_float2((float)(a * xv.x), (float)(a * xv.y));
 }
 
 // ||x_r||^2 in two fixed-order stages (no atomics, so the result is the same on every run):
@@ -378,13 +418,18 @@ __global__ void k_norm2_sum(const double* __restrict__ part, int nb, double* __r
 }
 
 // ------------------------------------------------------------------ launch wrappers
-void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first) {
+template <class B>
+static void iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first) {
     const dim3 gc(K.nchunk, K.R);
     const int nt = std::min(K.chunk, 256);
-    const size_t sm = sizeof(double2) * (size_t)K.chunk;
-    if (!skip_first) k_cgs_first<<<gc, nt, sm, st>>>(K);
-    k_cgs_second<<<gc, nt, sm, st>>>(K);
-    k_cgs_final<<<gc, nt, 0, st>>>(K);
+    const size_t sm = sizeof(B) * (size_t)K.chunk;
+    if (!skip_first) k_cgs_first<B><<<gc, nt, sm, st>>>(K);
+    k_cgs_second<B><<<gc, nt, sm, st>>>(K);
+    k_cgs_final<B><<<gc, nt, 0, st>>>(K);
+}
+void launch_krylov_iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first) {
+    if (K.Vf) iter_tail<float2>(K, st, skip_first);
+    else iter_tail<double2>(K, st, skip_first);
 }
 void launch_fetch(const KrylovDev& K, cudaStream_t st) {
     k_fetch<<<dim3((K.nd + 255) / 256, K.R), 256, 0, st>>>(K);
@@ -398,6 +443,9 @@ void launch_update(const double2* Zb, const double2* y, const int* nit, double2*
 void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st) {
     k_axpby<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, a, y, b, out, n);
 }
+void launch_scale_f32(const double2* x, double a, float2* out, int64_t n, cudaStream_t st) {
+    k_scale_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, a, out, n);
+}
 void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R, cudaStream_t st) {
     k_norm2<<<dim3(64, R), 256, 0, st>>>(x, n, part);
     k_norm2_sum<<<R, 32, 0, st>>>(part, 64, out);
@@ -405,8 +453,10 @@ void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R,
 
 
 void set_krylov_limits() {
-    cudaFuncSetAttribute(k_cgs_first, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
-    cudaFuncSetAttribute(k_cgs_second, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
+    cudaFuncSetAttribute(k_cgs_first<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
+    cudaFuncSetAttribute(k_cgs_second<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));
+    cudaFuncSetAttribute(k_cgs_first<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(float2));
+    cudaFuncSetAttribute(k_cgs_second<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(float2));
 }
 
 }  // namespace ddh

@@ -15,6 +15,7 @@ constexpr int kCgsShortRows = 128;
 
 struct KrylovDev {
     double2* V; double2* Zb; double2* H; double* cs; double2* sn; double2* g; double* bnorm;
+    float2* Vf;   // complex64 basis in place of V (then V is null): FP32 orthogonalisation
     double* resid; int* ctl; int* rdone; int* iters; double2* partial; double2* hcol; double2* w;
     double2* vin; double2* zw;
     double2* h2; double* hn; int* cnt;   // second CGS projection, norm estimate, chunk counters
@@ -159,6 +160,8 @@ void launch_fetch(const KrylovDev& K, cudaStream_t st);
 void launch_store(const KrylovDev& K, cudaStream_t st);
 void launch_update(const double2* Zb, const double2* y, const int* nit, double2* nu, int nd, int m, int R, cudaStream_t st);
 void launch_axpby(const double2* x, double a, const double2* y, double b, double2* out, int64_t n, cudaStream_t st);
+// out = a x rounded to complex64 (the first vector of a complex64 Krylov basis)
+void launch_scale_f32(const double2* x, double a, float2* out, int64_t n, cudaStream_t st);
 // out[r] = ||x_r||^2 (deterministic; part: R x 64 doubles of scratch)
 void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R, cudaStream_t st);
 void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st);

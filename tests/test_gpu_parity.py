@@ -147,12 +147,15 @@ def test_errors_are_reported():
 # ---------------------------------------------------------------- mixed precision
 @pytest.mark.parametrize("name", ["plane_2x2", "uniform4_mixed_p", "hanging_mixed_p", "hanging_corner"])
 @pytest.mark.parametrize("coarse32", [0, 1])
-def test_mixed_precision_matches_fp64_oracle(name, coarse32):
+@pytest.mark.parametrize("kry32", [0, 1])
+def test_mixed_precision_matches_fp64_oracle(name, coarse32, kry32):
     """complex64 local solves inside FP64 flexible GMRES on the primal system: the final FP64
     primal residual reaches 1e-10 and the solution matches the FP64 oracle to within the
-    conditioning of the primal system (stated bound 1e-8 relative)."""
+    conditioning of the primal system (stated bound 1e-8 relative), with the inner Krylov
+    basis in complex128 or complex64."""
     w = SMALL[name]()
-    s = _solver(w, tol=1e-10, precision=ddh.PREC_MIXED_FP32, inner_iters=12, coarse_fp32=coarse32)
+    s = _solver(w, tol=1e-10, precision=ddh.PREC_MIXED_FP32, inner_iters=12, coarse_fp32=coarse32,
+                inner_krylov_fp32=kry32)
     u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
     prob = dd.problem_from_workload(w)
     ref = dd.Conforming(prob).solve_direct()
