@@ -297,7 +297,8 @@ def run_ours(args):
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     # ---- headline: mixed + batched on random_eps_64 (8 RHS)
-    w, s = _context(WORKLOAD, ddh.PREC_MIXED_FP32, local, stream)
+    pins = {k: v for k, v in (("edge_launch", args.edge_launch), ("nd_chains", args.nd_chains)) if v}
+    w, s = _context(WORKLOAD, ddh.PREC_MIXED_FP32, local, stream, **pins)
     info = s.info()
     R = w.n_rhs
     with torch.cuda.stream(stream):
@@ -342,6 +343,7 @@ def run_ours(args):
     e2e_same = bool(torch.equal(uh, u.cpu()))     # repeated solves are bit-identical
     comp = s.profile_op(R, ddh.PREC_MIXED_FP32, reps=10)
     roof = roofline(comp, info, R, 20, False, "coarse solve (nested dissection, FP64: k_nd_forward/backward levels)")
+    tuning = s.get_tuning(R, ddh.PREC_MIXED_FP32)
     clocks = clk.summary()
     s.close()
     del u, b
@@ -403,7 +405,8 @@ def run_ours(args):
                        "h2d_bytes_per_step": int(16 * R * info.n_local),
                        "d2h_bytes_per_step": int(16 * R * info.n_local),
                        "result_identical_to_device_solve": e2e_same},
-               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks}
+               "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+               "tuning": tuning}
         out.update(extras)
         print(json.dumps(out))
     if ws > 1:
@@ -449,6 +452,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="time only the headline form (no plain FP64, disk_hanging or plane_16x16 lines)")
+    ap.add_argument("--edge-launch", type=int, default=0,
+                    help="profiling runs: pin the edge-pass launch form (ddh_edge_launch; 0 = autotuned)")
+    ap.add_argument("--nd-chains", type=int, default=0,
+                    help="profiling runs: pin the nested-dissection chain count (0 = autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -78,6 +78,12 @@ typedef enum { DDH_LOCAL_EDGE = 0, DDH_LOCAL_FDM = 1 } ddh_local_form;
 typedef enum { DDH_COARSE_AUTO = 0, DDH_COARSE_DENSE = 1, DDH_COARSE_ND = 2,
                DDH_COARSE_ND_LEVELS = 3 } ddh_coarse_form;
 
+/* Launch form of the Krylov-loop pass 1 with explicit edge operators: chosen by timing both
+ * (AUTO), one CTA per (element, RHS block), or one persistent launch over the elements sorted by
+ * degree with the tuned threads per output row of each degree. */
+typedef enum { DDH_EDGE_LAUNCH_AUTO = 0, DDH_EDGE_LAUNCH_PER_TASK = 1,
+               DDH_EDGE_LAUNCH_PERSISTENT = 2 } ddh_edge_launch;
+
 typedef struct {
     double tol;            /* relative residual target (default 1e-10) */
     int32_t maxit;         /* total Krylov iterations per RHS (default 300) */
@@ -128,6 +134,12 @@ typedef struct {
                               products and norms in FP32 (per-chunk partial sums, the Hessenberg
                               column, the Givens rotations and the iterate update stay FP64);
                               0 = complex128 basis and FP64 arithmetic, as the outer FGMRES */
+    int32_t edge_launch;   /* launch form of the edge pass, a ddh_edge_launch value (default
+                              DDH_EDGE_LAUNCH_AUTO) */
+    int32_t nd_chains;     /* per-level nested-dissection solve: 0 (default) = the autotuner picks
+                              1, 2 or 4 chains over equal shares of the right-hand sides on forked
+                              streams; 1, 2 or 4 = that many (fewer when R is not a multiple with
+                              at least 2 right-hand sides per chain) */
 } ddh_options;
 
 typedef struct {
@@ -260,18 +272,26 @@ ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_dev, const vo
  *   *edge_persistent   launch form of the Krylov-loop pass 1 with explicit edge operators: 1 the
  *                      persistent form over the degree-sorted element list, 0 one CTA per
  *                      (element, RHS block), -1 not tuned (nested-dissection-only or FDM form);
+ *   *edge_cta_threads  CTA size of the one-CTA-per-task form (0 when not tuned);
  *   tpr_by_degree[33]  threads sharing one output row in the persistent Krylov-loop pass 1 for
- *                      each element degree p (1, 2, 4 or 8; 0 where no element has degree p or
- *                      the pass has not been tuned for this R);
+ *                      each element degree p (2 or 4; 0 where no element has degree p or the
+ *                      pass has not been tuned for this R).  None of the shapes reported here
+ *                      (threads per row, CTA size, launch form, RHS block, chain count, FDM
+ *                      batch and staging) changes the result bits: each sum runs in an order
+ *                      fixed by the problem alone;
  *   nd_rb[2 L]         right-hand sides per CTA of each nested-dissection level launch (forward
  *                      levels 0 .. L-1, then backward; 0 = level not launched on its own), with
  *                      L written to *nd_levels (0 when the dense K^-1 is in use or not yet tuned);
- *   *nd_chains         2 when the per-level solve runs as two chains over the two halves of the
- *                      right-hand sides on forked streams (their level launches then use the
- *                      tuning of R/2), 1 for one chain, 0 when not tuned.
+ *   *nd_chains         number of chains (1, 2 or 4) the per-level solve runs as, over equal
+ *                      shares of the right-hand sides on forked streams (with k chains the
+ *                      level launches use the tuning of R/k), 0 when not tuned;
+ *   fdm_shape[4]       the FDM RHS pass and recovery: right-hand sides per batched interior
+ *                      transform and whether S_E^-1 is staged in shared memory (1) or read from
+ *                      global memory (0), for pass 1 then pass 2 (0, -1 when not tuned).
  * nd_rb may be NULL; otherwise it must hold 128 entries (L <= 64).  Host arrays. */
 ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
-                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels, int32_t* nd_chains);
+                          int32_t* edge_cta_threads, int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels,
+                          int32_t* nd_chains, int32_t* fdm_shape);
 
 /* Apply one of the two operators of the dual iteration to caller-given dual vectors (for
  * checks of the hot path against a reference; the solves apply the same code):

@@ -46,7 +46,6 @@ struct KState {
     double* h_resid = nullptr;  // pinned: resid[R]
     std::map<GraphKey, cudaGraphExec_t> graphs;
     std::map<GraphKey, int64_t> graph_kernels;
-    double graph_tol = -1;
     // iterations of the first cycle of the previous cold-started run: the next run replays
     // that many minus one before its first poll (replays past convergence do nothing)
     int iter_hint = 0;
@@ -78,6 +77,8 @@ struct ddh_ctx {
     std::map<int, const signed char*> edge_tpr;    // tuned threads per output row by degree, per (precision, RHS block)
     std::map<int, std::vector<int>> edge_tpr_host;
     std::map<int, bool> edge_persist;              // per (precision, RHS block): persistent form timed faster
+    std::map<int, int> edge_nt;                    // per (precision, RHS block): CTA size of the one-CTA form
+    std::map<int, FdmCfg> fdm1, fdm2;              // per (precision, RHS block): shapes of the FDM passes
     const float* tc_W = nullptr;                   // [S_E^-1; Y^T] planes for the tensor-core pass 1
     const int64_t* tc_off = nullptr;
     const int* tc_items = nullptr;                 // elements by degree, descending
@@ -97,9 +98,9 @@ struct ddh_ctx {
     std::vector<int> nd_fwd_off, nd_fwd_n, nd_fwd_rows;   // per level: first item, items, staged rows
     std::vector<int> nd_bwd_off, nd_bwd_n, nd_bwd_rows;
     std::map<int, std::vector<int>> nd_rb;         // per R: tuned RHS block of each level (fwd, then bwd)
-    std::map<int, int> nd_chains;                  // per R: 2 = two half-R level chains on forked streams
-    cudaStream_t stream2 = nullptr;                // second stream of the forked coarse solve
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::map<int, int> nd_chains;                  // per R: level chains (1, 2 or 4) over equal RHS shares
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // side streams of the forked coarse solve
+    cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
     NDSched nd_sched;                              // one-launch schedule of the same items
     bool nd_levels = false;                        // one launch per tree level instead
     bool coarse32 = false;                         // current inner solves use the complex64 copy
@@ -181,6 +182,9 @@ static void free_model(ddh_ctx* ctx) {
     ctx->edge_tpr.clear();
     ctx->edge_tpr_host.clear();
     ctx->edge_persist.clear();
+    ctx->edge_nt.clear();
+    ctx->fdm1.clear();
+    ctx->fdm2.clear();
     ctx->tc_W = nullptr;
     ctx->tc_off = nullptr;
     ctx->tc_items = nullptr;
@@ -200,6 +204,7 @@ static void free_model(ddh_ctx* ctx) {
     ctx->nd_sched = NDSched();
     ctx->nd_levels = false;
     ctx->nd_rb.clear();
+    ctx->nd_chains.clear();
     ctx->kc_ptr = ctx->kc_col = nullptr;
     ctx->kc_val = nullptr;
     ctx->gx = ctx->gw = nullptr;
@@ -250,7 +255,10 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         geo[3 * e] = El.x0; geo[3 * e + 1] = El.y0; geo[3 * e + 2] = El.h;
     }
     d.pmax = pmax;
-    for (int e = 0; e < E; ++e) d.maxE1 = std::max(d.maxE1, m.el[e].nE1);
+    for (int e = 0; e < E; ++e) {
+        d.maxE1 = std::max(d.maxE1, m.el[e].nE1);
+        d.maxNo = std::max(d.maxNo, m.el[e].nE1 + m.el[e].nT);
+    }
     if ((st = upload(ctx, p, &d.p))) return st;
     if ((st = upload(ctx, off, &d.off))) return st;
     if ((st = upload(ctx, e1o, &d.e1_off))) return st;
@@ -819,10 +827,10 @@ struct Work {
 static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, double2* tmp, int R, const int* done);
 
 // Autotuner of the per-level nested-dissection solve for R right-hand sides: for each level
-// launch, the right-hand sides per CTA (powers of two up to the level's limit), then whether two
-// chains over the two halves of the right-hand sides, on forked streams, beat one chain (the
-// tail of one chain's level launch overlaps the other chain's work).  Runs once per R, before
-// any graph capture, on cleared work buffers.
+// launch, the right-hand sides per CTA (powers of two up to the level's limit), then how many
+// chains (1, 2 or 4, over equal shares of the right-hand sides, on forked streams) run fastest
+// (the tail of one chain's level launch overlaps the other chains' work).  Runs once per R,
+// before any graph capture, on cleared work buffers.
 static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
     if (ctx->Kinv || !ctx->nd_levels || ctx->nd_rb.count(R)) return DDH_OK;
     const int L = (int)ctx->nd_fwd_rows.size();
@@ -867,26 +875,30 @@ static ddh_status nd_tune(ddh_ctx* ctx, const Work& w, int R) {
     CK(cudaGetLastError());
     ctx->nd_rb[R] = best;
     ctx->nd_chains[R] = 1;
-    if (R >= 4 && R % 2 == 0 && ctx->stream2) {
+    float tbest = 1e30f;
+    int pick = 1;
+    const int pin = ctx->opt.nd_chains;
+    for (int k : {1, 2, 4}) {
+        if (k > 1 && (R % k != 0 || R / k < 2)) continue;
+        if (pin > 0 && k != pin && k != 1) continue;      // a pinned count (or 1 where it does not fit)
         ddh_status st;
-        if ((st = nd_tune(ctx, w, R / 2))) {
+        if (k > 1 && (st = nd_tune(ctx, w, R / k))) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return st;
         }
-        float tm[2] = {0, 0};
-        for (int form = 0; form < 2; ++form) {
-            ctx->nd_chains[R] = form + 1;
-            auto run = [&] { coarse_solve_once(ctx, w.t, w.x2, w.ctmp, R, nullptr); };
-            run();
-            cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 5; ++rep) run();
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&tm[form], e0, e1);
-        }
-        ctx->nd_chains[R] = tm[1] < 0.97f * tm[0] ? 2 : 1;
+        ctx->nd_chains[R] = k;
+        auto run = [&] { coarse_solve_once(ctx, w.t, w.x2, w.ctmp, R, nullptr); };
+        run();
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 5; ++rep) run();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < 0.97f * tbest || (pin > 0 && k == pin)) { tbest = ms; pick = k; }
     }
+    ctx->nd_chains[R] = pick;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
@@ -900,10 +912,10 @@ static int edge_key(bool fp64, int R) {
 }
 
 // Per-degree autotuner of the persistent Krylov-loop pass 1: for each run of equal degree in the
-// work list, time the pass over that run alone with 1, 2, 4 and 8 threads per output row (the
-// tile shape: how many threads share one row of [S_E^-1; Y^T], the rest of the 256 take other
-// rows) and keep the fastest.  Runs once per (precision, RHS block), before any graph capture,
-// on the cleared work buffers.
+// work list, time the pass over that run alone with 4 and 2 threads per output row (the tile
+// shape: how many threads share one row of [S_E^-1; Y^T], the rest of the 256 take other rows;
+// both shapes give the same bits) and keep the faster.  Runs once per (precision, RHS block),
+// before any graph capture, on the cleared work buffers.
 static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
     if (!ctx->edge_form || !ctx->edge_items) return DDH_OK;
     const int key = edge_key(fp64, R);
@@ -923,7 +935,7 @@ static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
     for (size_t g = 0; g < ctx->deg_p.size(); ++g) {
         float best = 1e30f;
         int pick = 0;
-        for (int tpr : {4, 2, 8, 1}) {
+        for (int tpr : {4, 2}) {
             auto run = [&] {
                 if (fp64) launch_pass1_edge<double>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, &es,
                                                     ctx->deg_begin[g], ctx->deg_count[g], tpr);
@@ -950,13 +962,19 @@ static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
         cudaEventDestroy(e1);
         return st;
     }
-    // then the whole pass in both launch forms: the tuned persistent one over the sorted list,
-    // and one CTA per (element, RHS block) with its fixed shape; keep the faster
+    // then the whole pass in each launch form: the tuned persistent one over the sorted list, and
+    // one CTA per (element, RHS block) with 256 threads or with the size rule of the launcher
+    // (two threads per output row of the widest element); keep the fastest
     es.tpr_p = dt;
-    float best[2] = {0, 0};
-    for (int form = 0; form < 2; ++form) {
+    const int nt_rule = edge_cta_threads(d.maxNo);
+    const int forms[3][2] = {{1, 0}, {0, 256}, {0, nt_rule}};     // {persistent, CTA threads}
+    float tm[3] = {1e30f, 1e30f, 1e30f};
+    for (int f = 0; f < 3; ++f) {
+        if (f == 2 && nt_rule == 256) continue;
+        EdgeSched one;
+        one.cta_threads = forms[f][1];
+        const EdgeSched* sp = forms[f][0] ? &es : &one;
         auto run = [&] {
-            const EdgeSched* sp = form ? &es : nullptr;
             if (fp64) launch_pass1_edge<double>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, sp);
             else launch_pass1_edge<float>(d, sinv, Y, w.vd, 1.0, nullptr, w.xE, w.tT, R, nullptr, s, sp);
         };
@@ -965,15 +983,103 @@ static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
         for (int rep = 0; rep < 5; ++rep) run();
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&best[form], e0, e1);
+        cudaEventElapsedTime(&tm[f], e0, e1);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
     ctx->edge_tpr[key] = dt;
     ctx->edge_tpr_host[key] = host;
-    ctx->edge_persist[key] = best[1] < best[0];
+    const int one_best = tm[2] < tm[1] ? 2 : 1;
+    ctx->edge_nt[key] = forms[one_best][1];
+    ctx->edge_persist[key] = ctx->opt.edge_launch == DDH_EDGE_LAUNCH_AUTO ? tm[0] < tm[one_best]
+                                                                         : ctx->opt.edge_launch == DDH_EDGE_LAUNCH_PERSISTENT;
     return DDH_OK;
+}
+
+// Autotuner of the FDM passes (the RHS pass with an interior load, and the recovery): for one
+// block of right-hand sides it times each pass with 1, 1/2, 1/4 and all of the largest batch of
+// interior transforms per barrier interval, with and without S_E^-1 staged in shared memory, and
+// keeps the fastest.  Smaller batches and no staging cut the shared memory per CTA, so more CTAs
+// share an SM.  The scratch loads live only for the tuning.  Runs once per (precision, RHS
+// block), before any graph capture.
+static ddh_status fdm_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
+    const int key = edge_key(fp64, R);
+    if (ctx->fdm1.count(key)) return DDH_OK;
+    const DevModel& d = ctx->dm;
+    cudaStream_t s = ctx->stream;
+    const int rb = R >= 8 ? 8 : (R >= 4 ? 4 : (R >= 2 ? 2 : 1));
+    const size_t lb = sizeof(double2) * (size_t)rb * d.n_local;
+    void *bt = nullptr, *phi = nullptr;
+    if (cudaMalloc(&bt, lb) != cudaSuccess || cudaMalloc(&phi, lb) != cudaSuccess) {
+        cudaGetLastError();                        // no room for the scratch loads: keep the defaults
+        if (bt) cudaFree(bt);
+        ctx->fdm1[key] = FdmCfg();
+        ctx->fdm2[key] = FdmCfg();
+        return DDH_OK;
+    }
+    CK(cudaMemsetAsync(bt, 0, lb, s));
+    CK(cudaMemsetAsync(w.vd, 0, sizeof(double2) * (size_t)rb * std::max(1, d.n_dual), s));
+    CK(cudaMemsetAsync(w.x2, 0, sizeof(double2) * (size_t)rb * std::max(1, d.n_coarse), s));
+    const void* sinv = fp64 ? ctx->sinv64 : ctx->sinv32;
+    const void* Y = ctx->edge_form ? (fp64 ? ctx->pq64 : ctx->pq32) : nullptr;
+    const int qmax = fdm_qb_max(d.pmax, rb, fp64);
+    std::vector<FdmCfg> cands;
+    for (int q : {qmax, qmax / 2, qmax / 4, 1}) {
+        if (q < 1) continue;
+        bool dup = false;
+        for (const FdmCfg& c : cands) dup |= c.qb == q;
+        if (dup) continue;
+        for (int st : {-1, 0}) {
+            FdmCfg c;
+            c.qb = q;
+            c.stage = st;
+            cands.push_back(c);
+        }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int pass = 1; pass <= 2; ++pass) {
+        float best = 1e30f;
+        FdmCfg pick;
+        for (const FdmCfg& c : cands) {
+            if (pass == 2 && Y && c.stage == 0) continue;     // pass 2 with Y reads no S_E^-1
+            auto run = [&] {
+                if (pass == 1) {
+                    if (fp64) launch_pass1<double>(d, sinv, Y, w.vd, 1.0, (const double2*)bt, 1, w.xE, w.tT, rb, nullptr, s, c);
+                    else launch_pass1<float>(d, sinv, Y, w.vd, 1.0, (const double2*)bt, 1, w.xE, w.tT, rb, nullptr, s, c);
+                } else {
+                    if (fp64) launch_pass2<double>(d, sinv, Y, w.x2, w.xE, w.xE2, 1, (const double2*)bt, 1, (double2*)phi, rb,
+                                                   nullptr, s, c);
+                    else launch_pass2<float>(d, sinv, Y, w.x2, w.xE, w.xE2, 1, (const double2*)bt, 1, (double2*)phi, rb,
+                                             nullptr, s, c);
+                }
+            };
+            run();
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) run();
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < 0.97f * best) { best = ms; pick = c; }
+        }
+        (pass == 1 ? ctx->fdm1 : ctx->fdm2)[key] = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaStreamSynchronize(s));
+    cudaFree(bt);
+    cudaFree(phi);
+    CK(cudaGetLastError());
+    return DDH_OK;
+}
+
+static FdmCfg fdm_cfg(const ddh_ctx* ctx, bool fp64, int R, int pass) {
+    const auto& m = pass == 1 ? ctx->fdm1 : ctx->fdm2;
+    const auto it = m.find(edge_key(fp64, R));
+    return it == m.end() ? FdmCfg() : it->second;
 }
 
 // Work list and tuned tile shapes of the persistent edge pass for R right-hand sides; empty
@@ -981,6 +1087,8 @@ static ddh_status edge_tune(ddh_ctx* ctx, const Work& w, int R, bool fp64) {
 static EdgeSched edge_sched(const ddh_ctx* ctx, bool fp64, int R) {
     EdgeSched es;
     const int key = edge_key(fp64, R);
+    const auto nt = ctx->edge_nt.find(key);
+    if (nt != ctx->edge_nt.end()) es.cta_threads = nt->second;
     const auto pt = ctx->edge_persist.find(key);
     if (pt == ctx->edge_persist.end() || !pt->second) return es;   // one CTA per task
     es.items = ctx->edge_items;
@@ -1016,6 +1124,7 @@ static ddh_status get_op_work(ddh_ctx* ctx, int R, bool fp64, Work& w) {
     if ((st = get_work(ctx, "mvec", sizeof(double2) * (size_t)R * std::max(1, d.n_dual), &p))) return st;
     w.mvec = (double2*)p;
     if ((st = edge_tune(ctx, w, R, fp64))) return st;
+    if ((st = fdm_tune(ctx, w, R, fp64))) return st;
     return nd_tune(ctx, w, R);
 }
 
@@ -1064,18 +1173,23 @@ static void coarse_solve_once(ddh_ctx* ctx, const double2* t, double2* x2, doubl
         return;
     }
     const auto ch = ctx->nd_chains.find(R);
-    if (ch != ctx->nd_chains.end() && ch->second == 2) {
-        // two chains over right-hand sides [0, R/2) and [R/2, R) (vectors are [R][n], so a half
-        // is a pointer offset); the second runs on stream2 between a fork and a join event
-        const int Ra = R / 2;
+    const int k = ch == ctx->nd_chains.end() ? 1 : ch->second;
+    if (k > 1) {
+        // k chains over equal shares of the right-hand sides (vectors are [R][n], so a share is
+        // a pointer offset); chains 1 .. k-1 run on side streams between a fork and join events
+        const int Rk = R / k;
         const int64_t ul = D.u_len;
         CK_VOID(cudaEventRecord(ctx->ev_fork, s));
-        CK_VOID(cudaStreamWaitEvent(ctx->stream2, ctx->ev_fork, 0));
-        nd_level_chain(ctx, D, f32nd, t + (size_t)Ra * nc, y + (size_t)Ra * nc, x2 + (size_t)Ra * nc,
-                       u + (size_t)Ra * ul, R - Ra, done, ctx->stream2);
-        nd_level_chain(ctx, D, f32nd, t, y, x2, u, Ra, done, s);
-        CK_VOID(cudaEventRecord(ctx->ev_join, ctx->stream2));
-        CK_VOID(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+        for (int c = 1; c < k; ++c) {
+            CK_VOID(cudaStreamWaitEvent(ctx->side[c - 1], ctx->ev_fork, 0));
+            const size_t o = (size_t)c * Rk;
+            nd_level_chain(ctx, D, f32nd, t + o * nc, y + o * nc, x2 + o * nc, u + o * ul, Rk, done, ctx->side[c - 1]);
+        }
+        nd_level_chain(ctx, D, f32nd, t, y, x2, u, Rk, done, s);
+        for (int c = 1; c < k; ++c) {
+            CK_VOID(cudaEventRecord(ctx->ev_join[c - 1], ctx->side[c - 1]));
+            CK_VOID(cudaStreamWaitEvent(s, ctx->ev_join[c - 1], 0));
+        }
         return;
     }
     nd_level_chain(ctx, D, f32nd, t, y, x2, u, R, done, s);
@@ -1130,12 +1244,14 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
         const EdgeSched es = edge_sched(ctx, std::is_same<T, double>::value, R);
         launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s, &es);
     }
-    else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s);
+    else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s,
+                         fdm_cfg(ctx, std::is_same<T, double>::value, R, 1));
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
     coarse_solve(ctx, w.t, w.x2, w.ctmp, R, done);
     if (ctx->edge_form && !phi_out) launch_pass2_edge<T>(d, Y, w.x2, w.xE, w.xE2, R, done, s);
-    else launch_pass2<T>(d, sinv, ctx->edge_form ? Y : nullptr, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s);
+    else launch_pass2<T>(d, sinv, ctx->edge_form ? Y : nullptr, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s,
+                         fdm_cfg(ctx, std::is_same<T, double>::value, R, 2));
     ctx->launches++;
     if (kdots) {
         launch_jump_gather_dots<T>(d, w.xE2, w.x2, *kdots, s);
@@ -1221,6 +1337,7 @@ static ddh_status ensure_krylov(ddh_ctx* ctx, KState& ks, int nd, int R, int m, 
     ok &= al(sizeof(double2) * (size_t)R * (m + 1), &p); K.h2 = (double2*)p;
     ok &= al(sizeof(double) * (size_t)R, &p); K.hn = (double*)p;
     ok &= al(sizeof(int) * (size_t)(R + 1), &p); K.cnt = (int*)p;
+    ok &= al(sizeof(double) * (size_t)R, &p); K.tolr = (double*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.w = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.vin = (double2*)p;
     ok &= al(sizeof(double2) * (size_t)R * nd, &p); K.zw = (double2*)p;
@@ -1314,7 +1431,9 @@ static void host_upper_solve(int n, int m, const std::complex<double>* Hcols, co
 
 // Restarted right-preconditioned FGMRES (CGS2, zero initial guess) on A x = b for R
 // independent right-hand sides of length nd.  Stops per RHS at ||b - A x|| <= tol ||b||
-// (Givens estimate) or after maxit iterations; x_out receives the iterates.
+// (Givens estimate) or after maxit iterations; x_out receives the iterates.  The tolerance
+// lives in device memory (one entry per RHS), so captured iteration graphs stay valid when it
+// changes (the continuation rounds of the plain solve tighten it).
 static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, const double2* bvec, double2* x_out,
                              int nd, int R, int m, double tol, int maxit, int check_every,
                              std::vector<int>& its, std::vector<double>& res, bool warm = false, bool b32 = false) {
@@ -1325,12 +1444,8 @@ static ddh_status fgmres_run(ddh_ctx* ctx, KState& ks, const KrylovOps& ops, con
     ddh_status st;
     if ((st = ensure_krylov(ctx, ks, nd, R, m, b32))) return st;
     KrylovDev& K = ks.K;
-    K.tol = tol;
-    if (ks.graph_tol != tol) {            // tol is a kernel parameter of the captured graph
-        for (auto& kv : ks.graphs) cudaGraphExecDestroy(kv.second);
-        ks.graphs.clear();
-        ks.graph_tol = tol;
-    }
+    std::vector<double> tols(R, tol);
+    CK(cudaMemcpyAsync(K.tolr, tols.data(), sizeof(double) * R, cudaMemcpyHostToDevice, ctx->stream));
     double2* r = ks.r;
     std::vector<double> h_b(R), h_n(R);
     CK(cudaMemsetAsync(ks.nrm2, 0, sizeof(double) * R, ctx->stream));
@@ -1692,6 +1807,8 @@ void ddh_default_options(ddh_options* o) {
     o->robin_modified = 0;
     o->tensor_cores = 0;
     o->inner_krylov_fp32 = 1;
+    o->edge_launch = DDH_EDGE_LAUNCH_AUTO;
+    o->nd_chains = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1708,11 +1825,17 @@ ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
         if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return DDH_ERR_CUDA; }
         ctx->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int c = 0; c < 3; ++c) {
+        ok = ok && cudaStreamCreateWithFlags(&ctx->side[c], cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&ctx->ev_join[c], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-        if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+        for (int c = 0; c < 3; ++c) {
+            if (ctx->side[c]) cudaStreamDestroy(ctx->side[c]);
+            if (ctx->ev_join[c]) cudaEventDestroy(ctx->ev_join[c]);
+        }
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         delete ctx;
         return DDH_ERR_CUDA;
@@ -1757,6 +1880,10 @@ ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (ctx->opt.check_every < 1) ctx->opt.check_every = 1;
     if (ctx->opt.coarse_form < DDH_COARSE_AUTO || ctx->opt.coarse_form > DDH_COARSE_ND_LEVELS)
         return fail(ctx, DDH_ERR_INVALID_ARG, "coarse_form must be one of the ddh_coarse_form values");
+    if (ctx->opt.edge_launch < DDH_EDGE_LAUNCH_AUTO || ctx->opt.edge_launch > DDH_EDGE_LAUNCH_PERSISTENT)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "edge_launch must be one of the ddh_edge_launch values");
+    if (ctx->opt.nd_chains != 0 && ctx->opt.nd_chains != 1 && ctx->opt.nd_chains != 2 && ctx->opt.nd_chains != 4)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "nd_chains must be 0, 1, 2 or 4");
     const auto t0 = std::chrono::steady_clock::now();
     cudaSetDevice(ctx->device);
     std::string err;
@@ -1982,8 +2109,25 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
 }
 
 ddh_status ddh_get_tuning(const ddh_ctx* ctx, int32_t R, int32_t precision, int32_t* edge_persistent,
-                          int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels, int32_t* nd_chains) {
-    if (!ctx || !edge_persistent || !tpr_by_degree || !nd_levels || !nd_chains || R <= 0) return DDH_ERR_INVALID_ARG;
+                          int32_t* edge_cta_threads, int32_t* tpr_by_degree, int32_t* nd_rb, int32_t* nd_levels,
+                          int32_t* nd_chains, int32_t* fdm_shape) {
+    if (!ctx || !edge_persistent || !edge_cta_threads || !tpr_by_degree || !nd_levels || !nd_chains || !fdm_shape ||
+        R <= 0)
+        return DDH_ERR_INVALID_ARG;
+    {
+        const bool f64 = precision == DDH_PREC_FP64;
+        const int k = edge_key(f64, R);
+        const bool tuned = ctx->fdm1.count(k) != 0;
+        const FdmCfg a = fdm_cfg(ctx, f64, R, 1), b = fdm_cfg(ctx, f64, R, 2);
+        fdm_shape[0] = tuned ? a.qb : 0;
+        fdm_shape[1] = tuned ? a.stage != 0 : -1;
+        fdm_shape[2] = tuned ? b.qb : 0;
+        fdm_shape[3] = tuned ? (b.stage != 0 && !ctx->edge_form) : -1;     // with Y pass 2 reads no S_E^-1
+    }
+    {
+        const auto nt = ctx->edge_nt.find(edge_key(precision == DDH_PREC_FP64, R));
+        *edge_cta_threads = nt == ctx->edge_nt.end() ? 0 : nt->second;
+    }
     const auto ct = ctx->nd_chains.find(R);
     *nd_chains = ct == ctx->nd_chains.end() ? 0 : ct->second;
     if (!ctx->factored) return DDH_ERR_NOT_READY;
@@ -2110,9 +2254,11 @@ void ddh_destroy(ddh_ctx* ctx) {
     cudaSetDevice(ctx->device);
     free_model(ctx);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-    cudaStreamDestroy(ctx->stream2);
+    for (int c = 0; c < 3; ++c) {
+        cudaStreamDestroy(ctx->side[c]);
+        cudaEventDestroy(ctx->ev_join[c]);
+    }
     cudaEventDestroy(ctx->ev_fork);
-    cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 

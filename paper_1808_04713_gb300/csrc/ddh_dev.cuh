@@ -29,6 +29,7 @@ template <class T> __device__ __forceinline__ void fma_r(cpx<T>& a, T s, cpx<T> 
 struct DevModel {
     int E = 0, l = 0, pmax = 0;
     int maxE1 = 0;                      // largest number of type-1 edge slots of an element
+    int maxNo = 0;                      // largest nE1 + nT of an element (edge-pass output rows)
     int* err = nullptr;                 // device error word (0 = ok), read by the host after solves
     int64_t n_local = 0;
     int nE1_tot = 0, nT_tot = 0, n_coarse = 0, n_dual = 0, n_conf = 0;

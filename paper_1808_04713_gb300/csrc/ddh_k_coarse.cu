@@ -164,6 +164,54 @@ __global__ void __launch_bounds__(128) k_gemv2r(const M* __restrict__ A, int n_o
 // complex64 copy (vectors stay complex128 in global memory and are converted at the edges).
 template <class MT> struct NDType { using T = double; };
 template <> struct NDType<float2> { using T = float; };
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+// Warp sum of V values per lane by a transposing butterfly: each of the first log2(V) rounds
+// halves the values a lane carries (it keeps one half, sends the other half to its partner and
+// adds what it receives); the remaining rounds are a plain butterfly on the one value left.
+// V - 1 + 5 - log2(V) adds per lane instead of 5 V.  On return every lane holds the full sum of
+// value index lane >> (5 - log2(V)).
+// Sum of V values per lane over each group of G consecutive lanes (xor offsets G/2, ..., 1, in
+// that order for every value, so the result does not depend on V), transposing while a lane
+// carries more than one value.  Afterwards, with g = lane & (G - 1): if V >= G, v[i] (i < V/G) is
+// the sum of value index (g << log2(V/G)) | i; else v[0] is the sum of value g >> log2(G/V).
+template <class T, int V, int G>
+__device__ __forceinline__ void group_sum_transpose(T (&v)[V]) {
+    static_assert(V >= 1 && (V & (V - 1)) == 0 && G >= 1 && G <= 32 && (G & (G - 1)) == 0, "powers of two");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = V / 2, o = G / 2; h >= 1 && o >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = (G / 2) >> ilog2(V); o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+}
+
+template <class T, int V>
+__device__ __forceinline__ T warp_sum_transpose(T (&v)[V]) {
+    static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int h = V / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 >> ilog2(V); o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
 __device__ __forceinline__ cpx<double> ld_mat(const double2* a) { const double2 v = __ldg(a); return mk<double>(v.x, v.y); }
 __device__ __forceinline__ cpx<float> ld_mat(const float2* a) { const float2 v = __ldg(a); return mk<float>(v.x, v.y); }
 // Loads of vectors written during the same launch by other CTAs (the one-launch schedule) go
@@ -212,23 +260,40 @@ __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int ro
     const MT* G = (const MT*)d.G + d.g_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (shortm) {
-        // lane = (row of 4, column slice of S, right-hand side of RB), S * RB = 8
-        constexpr int S = 8 / RB;
-        const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
+        // lane = (row of 4, column slice s of 8), all RB right-hand sides per lane: every
+        // partial sum runs over the columns j = s (mod 8) and the slices are combined in one
+        // fixed tree, so the result does not depend on RB
+        const int rl = lane >> 3, s = lane & 7;
         for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
             const int row = base + rl;
             const bool ok = row < row0 + nrows;
-            T ax = 0, ay = 0;
-            if (ok)
-                for (int j = s; j < nF; j += S) cfma(ax, ay, ld_mat(G + (int64_t)j * nB + row), nd_sm[r * sF + j]);
+            T v[2 * RB];
 #pragma unroll
-            for (int o = RB; o < 8; o <<= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                ay += __shfl_xor_sync(0xffffffffu, ay, o);
-            }
-            if (ok && s == 0 && r < nr) {
-                const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + nF + row);
-                u[(r0 + r) * ul + uo + row] = make_double2(w.x + (double)ax, w.y + (double)ay);
+            for (int i = 0; i < 2 * RB; ++i) v[i] = 0;
+            if (ok)
+                for (int j = s; j < nF; j += 8) {
+                    const cpx<T> a = ld_mat(G + (int64_t)j * nB + row);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) cfma(v[2 * r], v[2 * r + 1], a, nd_sm[r * sF + j]);
+                }
+            group_sum_transpose<T, 2 * RB, 8>(v);
+            if (RB >= 4) {
+                // value index (s << log2(2RB/8)) | i: component c of right-hand side r
+#pragma unroll
+                for (int i = 0; i < 2 * RB / 8; ++i) {
+                    const int q = (s << ilog2(2 * RB / 8)) | i, r = q >> 1, c = q & 1;
+                    if (ok && r < nr) {
+                        const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + nF + row);
+                        reinterpret_cast<double*>(u + (r0 + r) * ul + uo + row)[c] = (c ? w.y : w.x) + (double)v[i];
+                    }
+                }
+            } else {
+                constexpr int sh = 3 - ilog2(2 * RB);
+                const int q = s >> sh, r = q >> 1, c = q & 1;
+                if (ok && (s & ((1 << sh) - 1)) == 0 && r < nr) {
+                    const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + nF + row);
+                    reinterpret_cast<double*>(u + (r0 + r) * ul + uo + row)[c] = (c ? w.y : w.x) + (double)v[0];
+                }
             }
         }
         return;
@@ -243,20 +308,16 @@ __device__ __forceinline__ void nd_forward_node(const NDDev& d, int node, int ro
 #pragma unroll
             for (int r = 0; r < RB; ++r) cfma(ax[r], ay[r], a, nd_sm[r * sF + j]);
         }
+        // value 2r + c is component c (0 real, 1 imaginary) of right-hand side r
+        T v[2 * RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
-            for (int o = 16; o > 0; o >>= 1) {
-                ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
-                ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
-            }
-        if (lane < nr) {
-            // lane r writes right-hand side r (register arrays indexed by a constant only)
-            T sx = 0, sy = 0;
-#pragma unroll
-            for (int r = 0; r < RB; ++r)
-                if (r == lane) { sx = ax[r]; sy = ay[r]; }
-            const double2 w = nd_pull<CG>(u, (r0 + lane) * ul, d.src, so + nF + row);
-            u[(r0 + lane) * ul + uo + row] = make_double2(w.x + (double)sx, w.y + (double)sy);
+        for (int r = 0; r < RB; ++r) { v[2 * r] = ax[r]; v[2 * r + 1] = ay[r]; }
+        const T sum = warp_sum_transpose<T, 2 * RB>(v);
+        constexpr int sh = 5 - ilog2(2 * RB);
+        const int q = lane >> sh, r = q >> 1, c = q & 1;
+        if ((lane & ((1 << sh) - 1)) == 0 && r < nr) {
+            const double2 w = nd_pull<CG>(u, (r0 + r) * ul, d.src, so + nF + row);
+            reinterpret_cast<double*>(u + (r0 + r) * ul + uo + row)[c] = (c ? w.y : w.x) + (double)sum;
         }
     }
 }
@@ -282,20 +343,33 @@ __device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int r
     const MT* M = (const MT*)d.M + d.m_off[node];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (shortm) {
-        constexpr int S = 8 / RB;
-        const int rl = lane >> 3, s = (lane & 7) / RB, r = (lane & 7) % RB;
+        // as in the forward short rows: 8 column slices, all RB right-hand sides per lane
+        const int rl = lane >> 3, s = lane & 7;
         for (int base = row0 + warp * 4; base < row0 + nrows; base += 16) {
             const int row = base + rl;
             const bool ok = row < row0 + nrows;
-            T ax = 0, ay = 0;
-            if (ok)
-                for (int j = s; j < n; j += S) cfma(ax, ay, ld_mat(M + (int64_t)j * nF + row), nd_sm[r * sn + j]);
+            T v[2 * RB];
 #pragma unroll
-            for (int o = RB; o < 8; o <<= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            for (int i = 0; i < 2 * RB; ++i) v[i] = 0;
+            if (ok)
+                for (int j = s; j < n; j += 8) {
+                    const cpx<T> a = ld_mat(M + (int64_t)j * nF + row);
+#pragma unroll
+                    for (int r = 0; r < RB; ++r) cfma(v[2 * r], v[2 * r + 1], a, nd_sm[r * sn + j]);
+                }
+            group_sum_transpose<T, 2 * RB, 8>(v);
+            if (RB >= 4) {
+#pragma unroll
+                for (int i = 0; i < 2 * RB / 8; ++i) {
+                    const int q = (s << ilog2(2 * RB / 8)) | i, r = q >> 1, c = q & 1;
+                    if (ok && r < nr) reinterpret_cast<double*>(x + (r0 + r) * nc + f0 + row)[c] = (double)v[i];
+                }
+            } else {
+                constexpr int sh = 3 - ilog2(2 * RB);
+                const int q = s >> sh, r = q >> 1, c = q & 1;
+                if (ok && (s & ((1 << sh) - 1)) == 0 && r < nr)
+                    reinterpret_cast<double*>(x + (r0 + r) * nc + f0 + row)[c] = (double)v[0];
             }
-            if (ok && s == 0 && r < nr) x[(r0 + r) * nc + f0 + row] = make_double2((double)ax, (double)ay);
         }
         return;
     }
@@ -309,19 +383,15 @@ __device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int r
 #pragma unroll
             for (int r = 0; r < RB; ++r) cfma(ax[r], ay[r], a, nd_sm[r * sn + j]);
         }
+        // value 2r + c is component c (0 real, 1 imaginary) of right-hand side r
+        T v[2 * RB];
 #pragma unroll
-        for (int r = 0; r < RB; ++r)
-            for (int o = 16; o > 0; o >>= 1) {
-                ax[r] += __shfl_xor_sync(0xffffffffu, ax[r], o);
-                ay[r] += __shfl_xor_sync(0xffffffffu, ay[r], o);
-            }
-        if (lane < nr) {
-            T sx = 0, sy = 0;
-#pragma unroll
-            for (int r = 0; r < RB; ++r)
-                if (r == lane) { sx = ax[r]; sy = ay[r]; }
-            x[(r0 + lane) * nc + f0 + row] = make_double2((double)sx, (double)sy);
-        }
+        for (int r = 0; r < RB; ++r) { v[2 * r] = ax[r]; v[2 * r + 1] = ay[r]; }
+        const T sum = warp_sum_transpose<T, 2 * RB>(v);
+        constexpr int sh = 5 - ilog2(2 * RB);
+        const int q = lane >> sh, r = q >> 1, c = q & 1;
+        if ((lane & ((1 << sh) - 1)) == 0 && r < nr)
+            reinterpret_cast<double*>(x + (r0 + r) * nc + f0 + row)[c] = (double)sum;
     }
 }
 

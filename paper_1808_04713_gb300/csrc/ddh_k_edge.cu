@@ -14,6 +14,65 @@ namespace ddh {
 // -- two small dense products per element and right-hand side block instead of the FDM
 // chain.  Y is formed at factor time.  The interior never enters the iteration; it is
 // rebuilt by the FDM kernels in the recovery.
+// [x_E; t_T] = [S_E^-1; Y^T] r_E for one element and RB right-hand sides: output row o < nE reads
+// S_E^-1 (column-major), o >= nE reads Y (row-major nE x nT, i.e. Y^T column-major); tpr (2 or 4)
+// threads per output row.  Every output is the same fixed tree (p0 + p2) + (p1 + p3) of the four
+// partial sums p_k over the columns j = k (mod 4), each summed in increasing j, whatever tpr: with
+// 4 threads a thread holds one p_k, with 2 it holds p_part and p_(part+2).  So the launch shapes
+// the autotuner picks do not change the result.
+template <class T, int RB>
+__device__ __forceinline__ void edge_rows(const DevModel& dm, const cpx<T>* S, const cpx<T>* Ye, int nE, int nT,
+                                          const cpx<T>* rE, int vs, int cnt, int tpr, int r0, int e1o, int to,
+                                          cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out) {
+    const int no = nE + nT;
+    for (int base = 0; base < no * tpr; base += blockDim.x) {
+        const int slot = base + threadIdx.x;
+        const int o = slot / tpr, part = slot % tpr;
+        cpx<T> a0[RB], a1[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
+        if (o < no) {
+            const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
+            const int ld = o < nE ? nE : nT;
+            if (tpr == 4) {
+                for (int j = part; j < nE; j += 4) {
+                    const cpx<T> s0 = col0[(int64_t)j * ld];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
+                }
+            } else {
+                for (int j = part; j < nE; j += 4) {
+                    const cpx<T> s0 = col0[(int64_t)j * ld];
+#pragma unroll
+                    for (int q = 0; q < RB; ++q)
+                        if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
+                    if (j + 2 < nE) {
+                        const cpx<T> s1 = col0[(int64_t)(j + 2) * ld];
+#pragma unroll
+                        for (int q = 0; q < RB; ++q)
+                            if (q < cnt) fma_c(a1[q], s1, rE[q * vs + j + 2]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            cpx<T> v = a0[q] + a1[q];
+            if (tpr == 4) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, 2);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, 2);
+            }
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 1);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 1);
+            if (part == 0 && o < no && q < cnt) {
+                if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
+                else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
+            }
+        }
+    }
+}
+
 template <class T, int RB>
 __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                     const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
@@ -48,50 +107,10 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
         if (!bulk_wait_all(bar, dm.err)) return;
         S = S_s;
     }
-    // [x_E; t_T] = [S_E^-1; Y^T] r_E in one pass: output row o < nE reads S_E^-1 (column-major),
-    // o >= nE reads Y (row-major nE x nT, i.e. Y^T column-major); tpr threads per output row
-    const cpx<T>* Ye = Y + dm.pq_off[e];
-    const int no = nE + nT;
-    // every vertex and edge slot is type-1 edge or type-2, so no = 4p <= 128 (p <= 32)
-    const int tpr = no <= 64 ? 4 : 2;                           // 256 threads
-    const int chunk = (nE + tpr - 1) / tpr;
-    for (int base = 0; base < no * tpr; base += blockDim.x) {
-        const int slot = base + threadIdx.x;
-        const int o = slot / tpr, part = slot % tpr;
-        cpx<T> a0[RB], a1[RB];
-#pragma unroll
-        for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
-        if (o < no) {
-            const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
-            const int ld = o < nE ? nE : nT;
-            const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
-            int j = j0;
-            for (; j + 1 < j1; j += 2) {
-                const cpx<T> s0 = col0[(int64_t)j * ld], s1 = col0[(int64_t)(j + 1) * ld];
-#pragma unroll
-                for (int q = 0; q < RB; ++q)
-                    if (q < cnt) { fma_c(a0[q], s0, rE[q * vs + j]); fma_c(a1[q], s1, rE[q * vs + j + 1]); }
-            }
-            if (j < j1) {
-                const cpx<T> s0 = col0[(int64_t)j * ld];
-#pragma unroll
-                for (int q = 0; q < RB; ++q)
-                    if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < RB; ++q) {
-            cpx<T> v = a0[q] + a1[q];
-            for (int sh = 1; sh < tpr; sh <<= 1) {
-                v.x += __shfl_xor_sync(0xffffffffu, v.x, sh);
-                v.y += __shfl_xor_sync(0xffffffffu, v.y, sh);
-            }
-            if (part == 0 && o < no && q < cnt) {
-                if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
-                else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
-            }
-        }
-    }
+    // every vertex and edge slot is type-1 edge or type-2, so nE + nT = 4p <= 128 (p <= 32): four
+    // threads per output row when all rows fit the CTA so, else two
+    const int tpr = (nE + nT) * 4 <= (int)blockDim.x ? 4 : 2;
+    edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out);
 }
 
 // The same pass as one persistent launch over a degree-sorted work list.  Task t is (element
@@ -99,8 +118,8 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
 // the blocks of one element are adjacent, so its S_E^-1 is reused from L2.  A CTA walks tasks
 // t = blockIdx.x, blockIdx.x + gridDim.x, ...; while it computes one task, the next task's
 // S_E^-1 is already being copied into the other of two shared-memory buffers (bulk copy,
-// mbarrier per buffer).  tpr_p[p] (1, 2, 4 or 8 threads per output row) is chosen per degree by
-// the autotuner; 0 = the default (4 up to 64 output rows, else 2); tpr_force > 0 overrides it.
+// mbarrier per buffer).  tpr_p[p] (2 or 4 threads per output row) is chosen per degree by the
+// autotuner; 0 = the default (4 up to 64 output rows, else 2); tpr_force (2 or 4) overrides it.
 template <class T, int RB>
 __global__ void __launch_bounds__(256) k_pass1_edge_p(DevModel dm, const cpx<T>* __restrict__ sinv,
                                                       const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
@@ -170,48 +189,9 @@ __global__ void __launch_bounds__(256) k_pass1_edge_p(DevModel dm, const cpx<T>*
         }
         __syncthreads();
         if (s_fail) break;
-        const cpx<T>* Ye = Y + dm.pq_off[e];
-        const int no = nE + nT;
         int tpr = tpr_force > 0 ? tpr_force : (tpr_p ? (int)tpr_p[dm.p[e]] : 0);
-        if (tpr <= 0) tpr = no <= 64 ? 4 : 2;
-        const int chunk = (nE + tpr - 1) / tpr;
-        for (int base = 0; base < no * tpr; base += blockDim.x) {
-            const int slot = base + threadIdx.x;
-            const int o = slot / tpr, part = slot % tpr;
-            cpx<T> a0[RB], a1[RB];
-#pragma unroll
-            for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
-            if (o < no) {
-                const cpx<T>* col0 = o < nE ? S + o : Ye + (o - nE);
-                const int ld = o < nE ? nE : nT;
-                const int j0 = part * chunk, j1 = min(nE, j0 + chunk);
-                int j = j0;
-                for (; j + 1 < j1; j += 2) {
-                    const cpx<T> s0 = col0[(int64_t)j * ld], s1 = col0[(int64_t)(j + 1) * ld];
-#pragma unroll
-                    for (int q = 0; q < RB; ++q)
-                        if (q < cnt) { fma_c(a0[q], s0, rE[q * vs + j]); fma_c(a1[q], s1, rE[q * vs + j + 1]); }
-                }
-                if (j < j1) {
-                    const cpx<T> s0 = col0[(int64_t)j * ld];
-#pragma unroll
-                    for (int q = 0; q < RB; ++q)
-                        if (q < cnt) fma_c(a0[q], s0, rE[q * vs + j]);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < RB; ++q) {
-                cpx<T> v = a0[q] + a1[q];
-                for (int sh = 1; sh < tpr; sh <<= 1) {
-                    v.x += __shfl_xor_sync(0xffffffffu, v.x, sh);
-                    v.y += __shfl_xor_sync(0xffffffffu, v.y, sh);
-                }
-                if (part == 0 && o < no && q < cnt) {
-                    if (o < nE) xE_out[(int64_t)(r0 + q) * dm.nE1_tot + e1o + o] = v;
-                    else tT_out[(int64_t)(r0 + q) * dm.nT_tot + to + (o - nE)] = v;
-                }
-            }
-        }
+        if (tpr != 2 && tpr != 4) tpr = nE + nT <= 64 ? 4 : 2;
+        edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out);
         __syncthreads();
     }
     // copies still in flight (after a failure) land before the CTA leaves (bounded waits)
@@ -248,16 +228,25 @@ __global__ void __launch_bounds__(128) k_pass2_edge(DevModel dm, const cpx<T>* _
         uT[q][i] = u;
     }
     g.sync();
+    // one thread per row i of Y, all RB right-hand sides at once: each Y entry is read once
     const cpx<T>* Ye = Y + dm.pq_off[e];
-    for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
-        const int q = idx / nE, i = idx % nE;
+    for (int i = g.t(); i < nE; i += g.n()) {
         const cpx<T>* yr = Ye + (int64_t)i * nT;
-        cpx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
-        int t = 0;
-        for (; t + 1 < nT; t += 2) { fma_c(a0, yr[t], uT[q][t]); fma_c(a1, yr[t + 1], uT[q][t + 1]); }
-        if (t < nT) fma_c(a0, yr[t], uT[q][t]);
-        const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
-        xE_out[gi] = xE_in[gi] - (a0 + a1);
+        cpx<T> a[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) a[q] = mk<T>(0, 0);
+        for (int t = 0; t < nT; ++t) {
+            const cpx<T> y = yr[t];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                if (q < cnt) fma_c(a[q], y, uT[q][t]);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+            if (q < cnt) {
+                const int64_t gi = (int64_t)(r0 + q) * dm.nE1_tot + e1o + i;
+                xE_out[gi] = xE_in[gi] - a[q];
+            }
     }
 }
 
@@ -496,6 +485,8 @@ static void edge_p_t(const DevModel& dm, const cpx<T>* S, const cpx<T>* Yp, cons
     k_pass1_edge_p<T, RB><<<grid, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, es.items,
                                                  item0, nitems, es.tpr_p, tpr_force, so, buf, vs);
 }
+int edge_cta_threads(int maxNo) { return maxNo > 64 ? std::min(256, (2 * maxNo + 31) / 32 * 32) : 256; }
+
 template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
                        const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
@@ -517,11 +508,15 @@ void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, cons
     const int ntask = dm.E * ((R + rb - 1) / rb);
     const size_t sm = edge_smem_total<T>(rb, dm.maxE1);
     const int vs = std::max(1, dm.maxE1);
+    // CTA size: two threads per output row of the widest element when that is more than 64
+    // rows (rounded up to whole warps), else 256; the CTA takes the rows in one pass and fewer
+    // threads idle (80 rows at p = 20, l = 5: 160 threads instead of 256 with 96 idle)
+    const int nt = es && es->cta_threads > 0 ? es->cta_threads : edge_cta_threads(dm.maxNo);
     switch (rb) {
-        case 8: k_pass1_edge<T, 8><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 4: k_pass1_edge<T, 4><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 2: k_pass1_edge<T, 2><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        default: k_pass1_edge<T, 1><<<ntask, 256, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
+        case 8: k_pass1_edge<T, 8><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 4: k_pass1_edge<T, 4><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        case 2: k_pass1_edge<T, 2><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
+        default: k_pass1_edge<T, 1><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
     }
 }
 template <class T>
@@ -532,11 +527,14 @@ void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, con
     const cpx<T>* Yp = (const cpx<T>*)Y;
     const cpx<T>* xi = (const cpx<T>*)xE_in;
     cpx<T>* xo = (cpx<T>*)xE_out;
+    // one thread per edge row: 64-thread CTAs when every element has at most 64 (more CTAs
+    // resident per SM to hide the gather latency)
+    const int nt = dm.maxE1 <= 64 ? 64 : 128;
     switch (rb) {
-        case 8: k_pass2_edge<T, 8><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
-        case 4: k_pass2_edge<T, 4><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
-        case 2: k_pass2_edge<T, 2><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
-        default: k_pass2_edge<T, 1><<<ntask, 128, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
+        case 8: k_pass2_edge<T, 8><<<ntask, nt, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 4: k_pass2_edge<T, 4><<<ntask, nt, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        case 2: k_pass2_edge<T, 2><<<ntask, nt, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask); break;
+        default: k_pass2_edge<T, 1><<<ntask, nt, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
     }
 }
 template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int);
@@ -601,6 +599,9 @@ template <class T, int RB>
 static void set_edge_pass_limits(int maxE1) {
     cudaFuncSetAttribute(k_pass1_edge<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)edge_smem_total<T>(RB, maxE1));
+    // the whole unified L1/shared array as shared memory: the staged S_E^-1 limits residency
+    cudaFuncSetAttribute(k_pass1_edge<T, RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
     int buf = 0;
     size_t tot = 0;
     edge_p_layout<T>(RB, maxE1, &buf, &tot);

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
                                                const double2* __restrict__ z, double zsign,
                                                const double2* __restrict__ bt, int has_bI, int R,
                                                cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
-                                               const int* __restrict__ done, int ntask, int stage_off) {
+                                               const int* __restrict__ done, int ntask, int stage_off, int qb) {
     if (done && *done) return;
     extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
     if (bt && has_bI) {
         // r_E -= A_EI (A_II^-1 b_I) and cT = A_TI (A_II^-1 b_I) for every RHS of the block, QB
         // right-hand sides per interior transform; only the cross of A_II^-1 b_I is needed
-        const int QB = fdm_qb<T>(dm.pmax, RB), nn = n * n;
+        const int QB = qb, nn = n * n;
         const FdmBatch<T> bb = carve_batch<T>(smem + pass_elem_bytes<T>(dm.pmax, RB), dm.pmax, QB);
         for (int q0 = 0; q0 < cnt; q0 += QB) {
             const int Q = min(QB, cnt - q0);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
                                                cpx<T>* __restrict__ xE_out, int recover,
                                                const double2* __restrict__ bt, int has_bI, int R,
                                                double2* __restrict__ phi_out, const int* __restrict__ done,
-                                               int ntask, int stage_off) {
+                                               int ntask, int stage_off, int qb) {
     if (done && *done) return;
     extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
     if (!recover) return;
     // full recovery, QB right-hand sides per interior transform: frame = [x1_E; u_T] (read through
     // the slot map), x1_I = A_II^-1 (b_I - A_IF frame)
-    const int QB = fdm_qb<T>(dm.pmax, RB), nn = n * n;
+    const int QB = qb, nn = n * n;
     const FdmBatch<T> bb = carve_batch<T>(smem + pass_elem_bytes<T>(dm.pmax, RB), dm.pmax, QB);
     for (int i = g.t(); i < N * N; i += g.n()) bb.fidx[i] = -1;
     g.sync();
@@ -437,47 +437,62 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
 }
 
 // ------------------------------------------------------------------ launch wrappers
+// shared-memory layout of one FDM pass launch: batch size, staging offset (0 = none), bytes
+template <class T>
+static void fdm_shape(const DevModel& dm, int rb, const FdmCfg& c, bool needS, int* qb, int* so, size_t* sm) {
+    const int qmax = fdm_qb<T>(dm.pmax, rb);
+    *qb = c.qb > 0 ? std::min(c.qb, qmax) : qmax;
+    const size_t base = pass_elem_bytes<T>(dm.pmax, rb) + fdm_batch_bytes<T>(dm.pmax, *qb);
+    const size_t sb = 128 + (((size_t)dm.maxE1 * dm.maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+    const bool stage = needS && c.stage != 0 && dm.maxE1 > 0 && base + sb <= 200 * 1024;
+    *so = stage ? (int)base : 0;
+    *sm = stage ? base + sb : base;
+}
+
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign, const double2* bt,
-                  int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st) {
+                  int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st, const FdmCfg& cfg) {
     const int rb = rhs_block(R);
-    const int so = pass_stage_off<T>(dm.pmax, rb, dm.maxE1);
+    int qb, so;
+    size_t sm;
+    fdm_shape<T>(dm, rb, cfg, true, &qb, &so, &sm);
     const int ntask = dm.E * ((R + rb - 1) / rb);
     const dim3 g(ntask);
-    const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     switch (rb) {
-        case 8: k_pass1<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 4: k_pass1<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        case 2: k_pass1<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so); break;
-        default: k_pass1<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so);
+        case 8: k_pass1<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, qb); break;
+        case 4: k_pass1<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, qb); break;
+        case 2: k_pass1<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, qb); break;
+        default: k_pass1<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, z, zsign, bt, has_bI, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, qb);
     }
 }
 // shared memory of the edge-operator pass 1: r_E and x_E blocks, then (when it fits) the
 // staged S_E^-1 behind an mbarrier
 template <class T>
 void launch_pass2(const DevModel& dm, const void* sinv, const void* Y, const double2* x2, const void* xE_in, void* xE_out,
-                  int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st) {
+                  int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st,
+                  const FdmCfg& cfg) {
     const int rb = rhs_block(R);
-    const int so = Y ? 0 : pass_stage_off<T>(dm.pmax, rb, dm.maxE1);     // with Y, S_E^-1 is not read
+    int qb, so;
+    size_t sm;
+    fdm_shape<T>(dm, rb, cfg, Y == nullptr, &qb, &so, &sm);      // with Y, S_E^-1 is not read
     const int ntask = dm.E * ((R + rb - 1) / rb);
     const dim3 g(ntask);
-    const size_t sm = pass_smem_total<T>(dm.pmax, rb, dm.maxE1);
     const cpx<T>* S = (const cpx<T>*)sinv;
     const cpx<T>* xi = (const cpx<T>*)xE_in;
     cpx<T>* xo = (cpx<T>*)xE_out;
     switch (rb) {
-        case 8: k_pass2<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 4: k_pass2<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        case 2: k_pass2<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so); break;
-        default: k_pass2<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so);
+        case 8: k_pass2<T, 8><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so, qb); break;
+        case 4: k_pass2<T, 4><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so, qb); break;
+        case 2: k_pass2<T, 2><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so, qb); break;
+        default: k_pass2<T, 1><<<g, kFdmThreads, sm, st>>>(dm, S, (const cpx<T>*)Y, x2, xi, xo, recover, bt, has_bI, R, phi, done, ntask, so, qb);
     }
 }
 // dynamic shared-memory limits of one pass in precision T, for every RHS block size
 template <class T>
 void set_pass1_limits(int pmax, int maxE1) {
-    const int b1 = (int)pass_smem_total<T>(pmax, 1, maxE1), b2 = (int)pass_smem_total<T>(pmax, 2, maxE1);
-    const int b4 = (int)pass_smem_total<T>(pmax, 4, maxE1), b8 = (int)pass_smem_total<T>(pmax, 8, maxE1);
+    const int b1 = (int)pass_smem_max<T>(pmax, 1, maxE1), b2 = (int)pass_smem_max<T>(pmax, 2, maxE1);
+    const int b4 = (int)pass_smem_max<T>(pmax, 4, maxE1), b8 = (int)pass_smem_max<T>(pmax, 8, maxE1);
     cudaFuncSetAttribute(k_pass1<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
     cudaFuncSetAttribute(k_pass1<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b2);
     cudaFuncSetAttribute(k_pass1<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b4);
@@ -485,8 +500,8 @@ void set_pass1_limits(int pmax, int maxE1) {
 }
 template <class T>
 void set_pass2_limits(int pmax, int maxE1) {
-    const int b1 = (int)pass_smem_total<T>(pmax, 1, maxE1), b2 = (int)pass_smem_total<T>(pmax, 2, maxE1);
-    const int b4 = (int)pass_smem_total<T>(pmax, 4, maxE1), b8 = (int)pass_smem_total<T>(pmax, 8, maxE1);
+    const int b1 = (int)pass_smem_max<T>(pmax, 1, maxE1), b2 = (int)pass_smem_max<T>(pmax, 2, maxE1);
+    const int b4 = (int)pass_smem_max<T>(pmax, 4, maxE1), b8 = (int)pass_smem_max<T>(pmax, 8, maxE1);
     cudaFuncSetAttribute(k_pass2<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
     cudaFuncSetAttribute(k_pass2<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b2);
     cudaFuncSetAttribute(k_pass2<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b4);

@@ -3,7 +3,7 @@
 
 namespace ddh {
 
-template void launch_pass1<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t);
+template void launch_pass1<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, int, void*, void*, int, const int*, cudaStream_t, const FdmCfg&);
 template void set_pass1_limits<double>(int, int);
 
 }  // namespace ddh

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) k_cgs_final(KrylovDev K) {
         const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y) / K.bnorm[r];
         K.resid[r] = res;
         K.iters[r] = j + 1;
-        if (res <= K.tol || hn_s == 0.0) K.rdone[r] = 1;
+        if (res <= K.tolr[r] || hn_s == 0.0) K.rdone[r] = 1;
     }
     __syncthreads();
     // columns past a right-hand side's convergence are never read back

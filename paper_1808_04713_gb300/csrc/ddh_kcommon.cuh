@@ -113,6 +113,18 @@ inline int pass_stage_off(int pmax, int rb, int maxE1) {
     const size_t st = 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
     return (maxE1 > 0 && base + st <= 200 * 1024) ? (int)base : 0;
 }
+// the most shared memory any FDM pass shape can take: every batch size from 1 to the largest,
+// with S_E^-1 staged wherever it then fits (the bound the kernels' limit is set to)
+template <class T>
+inline size_t pass_smem_max(int pmax, int rb, int maxE1) {
+    const size_t sb = 128 + (((size_t)maxE1 * maxE1 * sizeof(cpx<T>) + 127) & ~(size_t)127);
+    size_t m = 0;
+    for (int q = 1; q <= fdm_qb<T>(pmax, rb); ++q) {
+        const size_t base = pass_elem_bytes<T>(pmax, rb) + fdm_batch_bytes<T>(pmax, q);
+        m = std::max(m, (maxE1 > 0 && base + sb <= 200 * 1024) ? base + sb : base);
+    }
+    return m;
+}
 template <class T>
 inline size_t pass_smem_total(int pmax, int rb, int maxE1) {
     const int off = pass_stage_off<T>(pmax, rb, maxE1);

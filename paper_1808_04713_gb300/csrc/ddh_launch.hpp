@@ -19,19 +19,29 @@ struct KrylovDev {
     double* resid; int* ctl; int* rdone; int* iters; double2* partial; double2* hcol; double2* w;
     double2* vin; double2* zw;
     double2* h2; double* hn; int* cnt;   // second CGS projection, norm estimate, chunk counters
-    int nd, m, R, nchunk, chunk; double tol;
+    double* tolr;                        // per-RHS relative tolerance (device, read at every column)
+    int nd, m, R, nchunk, chunk;
 };
 
+// Shape of one FDM pass launch: right-hand sides per batched interior transform (0 = as many
+// as fit 48 KB of shared memory, and never more) and whether S_E^-1 is staged in shared memory
+// by a bulk copy (-1 = when it fits, 0 = read from global memory)
+struct FdmCfg {
+    int qb = 0;
+    int stage = -1;
+};
 // FDM-form passes; Y (edge operators, or null) replaces the cross pipelines that only feed
 // type-1 edge and type-2 values, leaving one full FDM per RHS for the interior terms
 template <class T>
 void launch_pass1(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign, const double2* bt,
-                  int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st);
+                  int has_bI, void* xE, void* tT, int R, const int* done, cudaStream_t st,
+                  const FdmCfg& cfg = FdmCfg());
 // Work list of the persistent edge pass: elements by degree, descending, and the tuned threads
 // per output row of each degree (index p; 0 = default)
 struct EdgeSched {
     const int* items = nullptr;
     const signed char* tpr_p = nullptr;
+    int cta_threads = 0;        // one-CTA-per-task form: CTA size (0 = the size rule of the launcher)
 };
 // Krylov-loop passes with the explicit edge operators Y = [A11^-1 A_1T]_E (no FDM; pass 1
 // requires a load without interior components, pass 2 no recovery).  With es (and es->items)
@@ -42,6 +52,8 @@ template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
                        const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
                        const EdgeSched* es = nullptr, int item0 = 0, int nitems = -1, int tpr_force = 0);
+// default CTA size of the one-CTA-per-task edge pass for elements of at most maxNo output rows
+int edge_cta_threads(int maxNo);
 template <class T>
 void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, const void* xE_in, void* xE_out, int R,
                        const int* done, cudaStream_t st);
@@ -52,7 +64,10 @@ void launch_coarse_assemble(const DevModel& dm, const void* tT, const double2* b
                             double2* t, int R, const int* done, cudaStream_t st);
 template <class T>
 void launch_pass2(const DevModel& dm, const void* sinv, const void* Y, const double2* x2, const void* xE_in, void* xE_out,
-                  int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st);
+                  int recover, const double2* bt, int has_bI, double2* phi, int R, const int* done, cudaStream_t st,
+                  const FdmCfg& cfg = FdmCfg());
+// the largest right-hand-side batch of an FDM pass in precision fp64 / complex64 for block rb
+int fdm_qb_max(int pmax, int rb, bool fp64);
 template <class T>
 void launch_jump_gather(const DevModel& dm, const void* xE, const double2* x2, double2* w, int R, const int* done,
                         cudaStream_t st);

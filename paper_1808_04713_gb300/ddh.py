@@ -20,6 +20,7 @@ PREC_FP64, PREC_MIXED_FP32 = 0, 1
 PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
 LOCAL_EDGE, LOCAL_FDM = 0, 1
 COARSE_AUTO, COARSE_DENSE, COARSE_ND, COARSE_ND_LEVELS = 0, 1, 2, 3
+EDGE_LAUNCH_AUTO, EDGE_LAUNCH_PER_TASK, EDGE_LAUNCH_PERSISTENT = 0, 1, 2
 
 
 class DDHError(RuntimeError):
@@ -34,7 +35,8 @@ class Options(C.Structure):
                 ("inner_iters", C.c_int32), ("check_every", C.c_int32), ("use_graph", C.c_int32),
                 ("coarse_fp32", C.c_int32), ("local_form", C.c_int32),
                 ("inner_tol", C.c_double), ("coarse_form", C.c_int32), ("robin_modified", C.c_int32),
-                ("tensor_cores", C.c_int32), ("inner_krylov_fp32", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("inner_krylov_fp32", C.c_int32), ("edge_launch", C.c_int32),
+                ("nd_chains", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -69,7 +71,7 @@ _SIGS = {
     "ddh_primal_residual_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_apply_dual_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
     "ddh_get_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                 C.c_void_p]),
+                                 C.c_void_p, C.c_void_p, C.c_void_p]),
     "ddh_kernel_launches": (C.c_int64, [C.c_void_p]),
     "ddh_profile_op": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "ddh_last_error": (C.c_char_p, [C.c_void_p]),
@@ -258,16 +260,21 @@ class DDH:
         """Autotuner choices for R right-hand sides: the launch form of the edge pass (1
         persistent, 0 one CTA per task, -1 untuned), its threads per output row by degree, the
         right-hand-side block of each nested-dissection level launch and the number of level
-        chains (2 = two half-R chains on forked streams)."""
+        chains (1, 2 or 4, over equal right-hand-side shares on forked streams)."""
         tpr = np.zeros(33, np.int32)
         nd = np.zeros(128, np.int32)
         L = C.c_int32()
         ep = C.c_int32()
+        ent = C.c_int32()
         ch = C.c_int32()
-        self._check(self.lib.ddh_get_tuning(self.h, int(R), int(precision), C.byref(ep), tpr.ctypes.data,
-                                            nd.ctypes.data, C.byref(L), C.byref(ch)))
-        return {"edge_persistent": int(ep.value), "tpr_by_degree": {int(p): int(t) for p, t in enumerate(tpr) if t},
+        fs = np.zeros(4, np.int32)
+        self._check(self.lib.ddh_get_tuning(self.h, int(R), int(precision), C.byref(ep), C.byref(ent),
+                                            tpr.ctypes.data, nd.ctypes.data, C.byref(L), C.byref(ch), fs.ctypes.data))
+        return {"edge_persistent": int(ep.value), "edge_cta_threads": int(ent.value),
+                "tpr_by_degree": {int(p): int(t) for p, t in enumerate(tpr) if t},
                 "nd_chains": int(ch.value),
+                "fdm_pass1": {"batch": int(fs[0]), "staged": int(fs[1])},
+                "fdm_pass2": {"batch": int(fs[2]), "staged": int(fs[3])},
                 "nd_rb_forward": nd[:L.value].tolist(), "nd_rb_backward": nd[L.value:2 * L.value].tolist()}
 
     def profile_op(self, R: int, precision: int = PREC_FP64, reps: int = 20) -> np.ndarray:

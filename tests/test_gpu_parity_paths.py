@@ -8,7 +8,8 @@
   edge), p ~ U{8..24}, eps = 4 in the disk, the element k h of the full workload, 16 right-hand
   sides, in both precisions;
 * wide element rows (p = 20: two threads per output row of the edge pass and one per row of the
-  FDM-form S_E^-1 product; p = 32: S_E^-1 too large to stage in shared memory);
+  FDM-form S_E^-1 product; p = 24 in FP64: S_E^-1 staged only with the smaller interior batches
+  the FDM-pass autotuner tries; p = 32: S_E^-1 too large to stage in shared memory);
 * the two operators of the dual iteration applied once: F nu (eq. complicated_schur_system) and
   the Dirichlet preconditioner P^-1 v (eqs. general_preconditioner, weight_matrix).
 
@@ -102,8 +103,7 @@ def test_nested_dissection_on_a_deep_tree(R, form):
 @pytest.mark.parametrize("R", [1, 8])
 def test_nested_dissection_forms_agree_at_full_size(R):
     """lens_48 (21217 coarse unknowns, 2491 fronts): the one-launch and per-level coarse solves
-    apply the same factor (the per-level form with tuned right-hand-side blocks, which changes
-    the order of the partial sums), so the solutions agree to the solve tolerance."""
+    apply the same factor, so the solutions agree to the solve tolerance."""
     w = _with_rhs(W.lens_48(), R)
     out = {}
     for form in (ddh.COARSE_ND, ddh.COARSE_ND_LEVELS):
@@ -114,6 +114,63 @@ def test_nested_dissection_forms_agree_at_full_size(R):
     a, b = out[ddh.COARSE_ND], out[ddh.COARSE_ND_LEVELS]
     assert np.linalg.norm(a[0] - b[0]) <= 1e-9 * np.linalg.norm(b[0])
     assert abs(max(a[1]) - max(b[1])) <= 1 and max(a[2]) <= 1e-10 and max(b[2]) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["uniform4_mixed_p", "multilevel"])
+@pytest.mark.parametrize("chains", [1, 2, 4])
+def test_nested_dissection_chains_match_oracle(name, chains):
+    """The per-level solve split into 1, 2 or 4 chains over equal shares of 8 right-hand sides
+    (forked streams, each chain with the level tuning of its share) solves the same systems."""
+    w = _with_rhs(ND_SMALL[name](), 8)
+    s = _solver(w, tol=1e-12, coarse_form=ddh.COARSE_ND_LEVELS, nd_chains=chains)
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-12)
+    assert s.get_tuning(8, ddh.PREC_FP64)["nd_chains"] == chains
+    ref = dd.DDSolver(dd.problem_from_workload(w), l=s.info().l).solve(tol=1e-12)
+    got = u.cpu().numpy()
+    for r in range(8):
+        assert _rel(got[r], ref["phi_N"][r]) <= 1e-10, (name, chains, r)
+    s.close()
+
+
+@pytest.mark.parametrize("launch", [ddh.EDGE_LAUNCH_PER_TASK, ddh.EDGE_LAUNCH_PERSISTENT])
+@pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
+def test_edge_pass_launch_forms_match_oracle(launch, prec):
+    """Both launch forms of the Krylov-loop edge pass (one CTA per task; one persistent launch
+    over the degree-sorted element list with tuned threads per row) on a mixed-degree hanging
+    mesh with 8 right-hand sides."""
+    w = _with_rhs(ND_SMALL["hanging_corner"](), 8)
+    s = _solver(w, tol=1e-12, precision=prec, edge_launch=launch)
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-12 if prec == ddh.PREC_FP64 else 1e-10)
+    assert s.get_tuning(8, prec)["edge_persistent"] == (1 if launch == ddh.EDGE_LAUNCH_PERSISTENT else 0)
+    got = u.cpu().numpy()
+    if prec == ddh.PREC_FP64:
+        ref = dd.DDSolver(dd.problem_from_workload(w), l=s.info().l).solve(tol=1e-12)["phi_N"]
+        bound = 1e-10
+    else:
+        ref = dd.Conforming(dd.problem_from_workload(w)).solve_direct()
+        bound = 1e-8
+    for r in range(8):
+        assert _rel(got[r], ref[r]) <= bound, (launch, prec, r)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
+def test_tuned_launch_shapes_do_not_change_the_bits(prec):
+    """Every shape an autotuner picks (edge-pass launch form and threads per row, coarse-solve
+    chains and right-hand sides per CTA) leaves each sum in a fixed order: solves pinned to
+    different shapes agree bit for bit, so the tuners' timing noise cannot change iteration
+    counts."""
+    w = _with_rhs(ND_SMALL["hanging_corner"](), 8)
+    outs = []
+    for opts in ({}, {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "nd_chains": 1},
+                 {"edge_launch": ddh.EDGE_LAUNCH_PERSISTENT, "nd_chains": 2}, {"nd_chains": 4}):
+        s = _solver(w, tol=1e-10, precision=prec, coarse_form=ddh.COARSE_ND_LEVELS, **opts)
+        u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
+        outs.append((u.cpu(), [x.iterations for x in st], [x.inner_iterations for x in st]))
+        s.close()
+    for u, its, inner in outs[1:]:
+        assert torch.equal(u, outs[0][0])
+        assert its == outs[0][1] and inner == outs[0][2]
 
 
 # ---------------------------------------------------------------- reduced batching workload
@@ -149,7 +206,7 @@ def test_reduced_disk_batch_mixed(disk_reduced):
 
 
 # ---------------------------------------------------------------- wide element rows
-@pytest.mark.parametrize("p", [20, 32])
+@pytest.mark.parametrize("p", [20, 24, 32])
 @pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
 @pytest.mark.parametrize("form", [ddh.LOCAL_EDGE, ddh.LOCAL_FDM])
 def test_wide_rows_match_oracle(p, prec, form):
