@@ -140,6 +140,9 @@ typedef struct {
                               1, 2 or 4 chains over equal shares of the right-hand sides on forked
                               streams; 1, 2 or 4 = that many (fewer when R is not a multiple with
                               at least 2 right-hand sides per chain) */
+    int32_t inner_passes_fp64; /* mixed precision: 1 = the RHS pass and the recovery of each inner
+                              solve (the two passes that solve the element interiors by the FDM)
+                              run in FP64, the Krylov loop in complex64; 0 = all complex64 */
 } ddh_options;
 
 typedef struct {

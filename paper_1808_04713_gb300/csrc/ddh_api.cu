@@ -1238,7 +1238,7 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     cudaStream_t s = ctx->stream;
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
     const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
-    if (ctx->edge_form && !(bt && has_bI) && !bt && std::is_same<T, float>::value && ctx->tc_W)
+    if (ctx->edge_form && !bt && std::is_same<T, float>::value && ctx->tc_W)
         launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, zsign, w.xE, w.tT, R, done, s, ctx->tc_maxT);
     else if (ctx->edge_form && !(bt && has_bI)) {
         const EdgeSched es = edge_sched(ctx, std::is_same<T, double>::value, R);
@@ -1599,7 +1599,14 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
     // g = C^ A^-1 b^
     // (the interior FDM terms of the load are skipped when the load has no interior part)
     const int has_bI = interior ? 1 : 0;
-    apply_op<T>(ctx, w, nullptr, 0.0, bt, has_bI, (double2*)g, nullptr, R, nullptr);
+    // the RHS pass and the recovery solve the element interiors through the FDM; in complex64
+    // its rounding is amplified by cond(A_II) (thousands at p = 20), so the mixed form can run
+    // these two passes in FP64 (inner_passes_fp64); the Krylov loop stays complex64
+    const bool p64 = std::is_same<T, float>::value && ctx->opt.inner_passes_fp64 != 0;
+    Work w64;
+    if (p64 && (st = get_op_work(ctx, R, true, w64))) return st;
+    if (p64) apply_op<double>(ctx, w64, nullptr, 0.0, bt, has_bI, (double2*)g, nullptr, R, nullptr);
+    else apply_op<T>(ctx, w, nullptr, 0.0, bt, has_bI, (double2*)g, nullptr, R, nullptr);
     // the inner solves of the mixed form keep their Krylov basis in complex64
     const bool b32 = std::is_same<T, float>::value && ctx->opt.inner_krylov_fp32 != 0;
     if ((st = ensure_krylov(ctx, ctx->kin, d.n_dual, R, restart, b32))) return st;
@@ -1618,7 +1625,8 @@ static ddh_status dd_solve_tilde(ddh_ctx* ctx, const double2* bt, double2* phit,
         for (int i = 0; i < R; ++i) its[i] += its_c[i];
         res = res_c;
         // recovery: A^ phi_p = b^ - C^T nu
-        apply_op<T>(ctx, w, (const double2*)nu, -1.0, bt, has_bI, nullptr, phit, R, nullptr);
+        if (p64) apply_op<double>(ctx, w64, (const double2*)nu, -1.0, bt, has_bI, nullptr, phit, R, nullptr);
+        else apply_op<T>(ctx, w, (const double2*)nu, -1.0, bt, has_bI, nullptr, phit, R, nullptr);
         if (primal_tol <= 0.0 || d.n_dual == 0) break;
         std::vector<double> pr;
         if ((st = primal_residual_dev(ctx, bt, phit, R, pr))) return st;
@@ -1809,6 +1817,7 @@ void ddh_default_options(ddh_options* o) {
     o->inner_krylov_fp32 = 1;
     o->edge_launch = DDH_EDGE_LAUNCH_AUTO;
     o->nd_chains = 0;
+    o->inner_passes_fp64 = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {

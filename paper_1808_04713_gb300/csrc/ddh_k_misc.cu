@@ -105,13 +105,21 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
     extern __shared__ __align__(128) char smem[];
     const int e = blockIdx.x, r = blockIdx.y;
     const int p = dm.p[e], N = p + 1;
-    const CtaGroup g;
-    ElemSmem<double> s = carve<double>(smem, dm.pmax, 0);
     const int NP = dm.pmax + 1;
-    cpx<double>* T1 = s.vec;                 // [N][N], index c + N b
-    cpx<double>* T2 = s.vec + NP * NP;
-    cpx<double>* S1 = s.vec + 2 * NP * NP;   // [2][N]: sum_c Mt[a][c] Phi[c][b'] for b' = 0, 1
-    load_tables<double>(g, dm, e, s);
+    // only what the matvec reads: the tile, two products, the side sums and the 1-D mass table
+    struct {
+        cpx<double>* tile;
+        double* Mt;
+    } s;
+    s.tile = reinterpret_cast<cpx<double>*>(smem);   // [N][N], index c + N b
+    cpx<double>* T1 = s.tile + NP * NP;
+    cpx<double>* T2 = T1 + NP * NP;
+    cpx<double>* S1 = T2 + NP * NP;                  // [2][N]: sum_c Mt[a][c] Phi[c][b'] for b' = 0, 1
+    s.Mt = reinterpret_cast<double*>(S1 + 2 * NP);
+    {
+        const double* Mt = dm.Mt_all + dm.tab_Mt[dm.ptab[e]];
+        for (int i = threadIdx.x; i < N * N; i += blockDim.x) s.Mt[i] = Mt[i];
+    }
     const int64_t base = (int64_t)r * dm.n_local + dm.off[e];
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) { const double2 v = phi[base + i]; s.tile[i] = mk<double>(v.x, v.y); }
     __syncthreads();
@@ -356,7 +364,10 @@ void launch_interior_nz(const DevModel& dm, const double2* bt, int* flag, int R,
 void launch_basis(const DevModel& dm, const double2* x, double2* y, int conj_in, int R, cudaStream_t st) {
     k_basis<<<dim3(dm.E, R), 128, 0, st>>>(dm, x, y, conj_in);
 }
-static size_t elem_matvec_smem(int pmax) { return elem_smem_bytes<double>(pmax, 2 * (pmax + 1) * (pmax + 1) + 2 * (pmax + 1)); }
+static size_t elem_matvec_smem(int pmax) {
+    const size_t NP = pmax + 1;
+    return sizeof(cpx<double>) * (3 * NP * NP + 2 * NP) + sizeof(double) * NP * NP;
+}
 void launch_elem_matvec(const DevModel& dm, const double2* phi, const double2* b, double2* out, int R, cudaStream_t st) {
     const size_t sm = elem_matvec_smem(dm.pmax);
     k_elem_matvec<<<dim3(dm.E, R), 128, sm, st>>>(dm, phi, b, out);

@@ -178,6 +178,21 @@ def test_plain_path_meets_primal_yardstick_lens():
     s.close()
 
 
+@pytest.mark.parametrize("name", ["uniform4_mixed_p", "hanging_mixed_p", "hanging_corner"])
+def test_fp64_interior_passes_meet_the_yardstick(name):
+    """The mixed form with the RHS pass and the recovery in FP64 (inner_passes_fp64): the FP64
+    primal residual reaches 1e-10 and the solution matches the oracle to 1e-8."""
+    w = SMALL[name]()
+    s = _solver(w, tol=1e-10, precision=ddh.PREC_MIXED_FP32, inner_passes_fp64=1)
+    u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
+    ref = dd.Conforming(dd.problem_from_workload(w)).solve_direct()
+    got = u.cpu().numpy()
+    for r in range(got.shape[0]):
+        assert st[r].primal_residual <= 1e-10
+        assert np.linalg.norm(got[r] - ref[r]) / np.linalg.norm(ref[r]) <= 1e-8
+    s.close()
+
+
 @pytest.mark.parametrize("name", ["uniform4_mixed_p", "hanging_corner", "multilevel"])
 @pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
 def test_local_forms_agree(name, prec):
