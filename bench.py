@@ -40,6 +40,9 @@ CPU_SAMPLE_BLOCK = 16           # the oracle times the 16 x 16-element corner of
 # x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25; cuBLAS DGEMM measured 1.10 on this GPU)
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 70.0         # FP32 SIMT FMA throughput timed on this GPU
+# DRAM bytes of one coarse solve of the headline workload (8 RHS in two chains of 4) from an ncu
+# capture of its 52 level launches (cold cache per launch; profiles/nd_coarse_random_eps_64.md)
+ND_TRAFFIC_BYTES_2CHAINS = 290.1e6
 
 
 def _dist():
@@ -344,6 +347,10 @@ def run_ours(args):
     comp = s.profile_op(R, ddh.PREC_MIXED_FP32, reps=10)
     roof = roofline(comp, info, R, 20, False, "coarse solve (nested dissection, FP64: k_nd_forward/backward levels)")
     tuning = s.get_tuning(R, ddh.PREC_MIXED_FP32)
+    if tuning.get("nd_chains") == 2 and "nested dissection" in roof["kernel"]:
+        roof["traffic"] = ND_TRAFFIC_BYTES_2CHAINS
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 52 level launches of one "
+                                  "coarse solve (two chains of 4 RHS), cold cache per launch")
     clocks = clk.summary()
     s.close()
     del u, b
