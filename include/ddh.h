@@ -143,6 +143,10 @@ typedef struct {
     int32_t inner_passes_fp64; /* mixed precision: 1 = the RHS pass and the recovery of each inner
                               solve (the two passes that solve the element interiors by the FDM)
                               run in FP64, the Krylov loop in complex64; 0 = all complex64 */
+    int32_t split_pass1;   /* 1: inside the Krylov loop, pass 1's t_T rows run first and its x_E rows
+                              on a forked stream beside the coarse solve (same result bits; measured
+                              slower, the x_E rows compete with the coarse solve); 0 (default) = one
+                              pass-1 launch */
 } ddh_options;
 
 typedef struct {

@@ -101,6 +101,8 @@ struct ddh_ctx {
     std::map<int, int> nd_chains;                  // per R: level chains (1, 2 or 4) over equal RHS shares
     cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // side streams of the forked coarse solve
     cudaEvent_t ev_fork = nullptr, ev_join[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t side_p1 = nullptr;                // x_E rows of pass 1 beside the coarse solve
+    cudaEvent_t ev_p1_fork = nullptr, ev_p1_join = nullptr;
     NDSched nd_sched;                              // one-launch schedule of the same items
     bool nd_levels = false;                        // one launch per tree level instead
     bool coarse32 = false;                         // current inner solves use the complex64 copy
@@ -1238,17 +1240,33 @@ static void apply_op(ddh_ctx* ctx, const Work& w, const double2* z, double zsign
     cudaStream_t s = ctx->stream;
     const void* sinv = std::is_same<T, double>::value ? ctx->sinv64 : ctx->sinv32;
     const void* Y = std::is_same<T, double>::value ? ctx->pq64 : ctx->pq32;
+    // With split_pass1, inside the Krylov loop (one-CTA edge form) pass 1 is split: the t_T rows,
+    // which the coarse assembly needs, on the context stream; the x_E rows, needed only by pass 2,
+    // on a forked stream beside the coarse solve.  Each output row is computed the same way
+    // either way.  (Measured slower: the x_E rows compete with the coarse solve's critical path.)
+    bool split = false;
     if (ctx->edge_form && !bt && std::is_same<T, float>::value && ctx->tc_W)
         launch_pass1_tc(d, ctx->tc_W, ctx->tc_off, ctx->tc_items, d.E, z, zsign, w.xE, w.tT, R, done, s, ctx->tc_maxT);
     else if (ctx->edge_form && !(bt && has_bI)) {
         const EdgeSched es = edge_sched(ctx, std::is_same<T, double>::value, R);
-        launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s, &es);
+        split = ctx->opt.split_pass1 != 0 && !bt && !es.items && ctx->side_p1;
+        if (split) {
+            cudaEventRecord(ctx->ev_p1_fork, s);
+            cudaStreamWaitEvent(ctx->side_p1, ctx->ev_p1_fork, 0);
+            launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, ctx->side_p1, &es, 0, -1, 0, 1);
+            cudaEventRecord(ctx->ev_p1_join, ctx->side_p1);
+            launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s, &es, 0, -1, 0, 2);
+            ctx->launches++;
+        } else {
+            launch_pass1_edge<T>(d, sinv, Y, z, zsign, bt, w.xE, w.tT, R, done, s, &es);
+        }
     }
     else launch_pass1<T>(d, sinv, ctx->edge_form ? Y : nullptr, z, zsign, bt, has_bI, w.xE, w.tT, R, done, s,
                          fdm_cfg(ctx, std::is_same<T, double>::value, R, 1));
     launch_coarse_assemble<T>(d, w.tT, bt, z, zsign, w.t, R, done, s);
     ctx->launches += 2;
     coarse_solve(ctx, w.t, w.x2, w.ctmp, R, done);
+    if (split) cudaStreamWaitEvent(s, ctx->ev_p1_join, 0);
     if (ctx->edge_form && !phi_out) launch_pass2_edge<T>(d, Y, w.x2, w.xE, w.xE2, R, done, s);
     else launch_pass2<T>(d, sinv, ctx->edge_form ? Y : nullptr, w.x2, w.xE, w.xE2, phi_out ? 1 : 0, bt, has_bI, phi_out, R, done, s,
                          fdm_cfg(ctx, std::is_same<T, double>::value, R, 2));
@@ -1818,6 +1836,7 @@ void ddh_default_options(ddh_options* o) {
     o->edge_launch = DDH_EDGE_LAUNCH_AUTO;
     o->nd_chains = 0;
     o->inner_passes_fp64 = 0;
+    o->split_pass1 = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -1835,6 +1854,9 @@ ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
         ctx->own_stream = true;
     }
     bool ok = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&ctx->side_p1, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_p1_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&ctx->ev_p1_join, cudaEventDisableTiming) == cudaSuccess;
     for (int c = 0; c < 3; ++c) {
         ok = ok && cudaStreamCreateWithFlags(&ctx->side[c], cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&ctx->ev_join[c], cudaEventDisableTiming) == cudaSuccess;
@@ -1846,6 +1868,9 @@ ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
             if (ctx->ev_join[c]) cudaEventDestroy(ctx->ev_join[c]);
         }
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->side_p1) cudaStreamDestroy(ctx->side_p1);
+        if (ctx->ev_p1_fork) cudaEventDestroy(ctx->ev_p1_fork);
+        if (ctx->ev_p1_join) cudaEventDestroy(ctx->ev_p1_join);
         delete ctx;
         return DDH_ERR_CUDA;
     }
@@ -2268,6 +2293,9 @@ void ddh_destroy(ddh_ctx* ctx) {
         cudaEventDestroy(ctx->ev_join[c]);
     }
     cudaEventDestroy(ctx->ev_fork);
+    cudaStreamDestroy(ctx->side_p1);
+    cudaEventDestroy(ctx->ev_p1_fork);
+    cudaEventDestroy(ctx->ev_p1_join);
     delete ctx;
 }
 

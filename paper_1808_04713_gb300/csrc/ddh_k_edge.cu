@@ -20,14 +20,16 @@ namespace ddh {
 // partial sums p_k over the columns j = k (mod 4), each summed in increasing j, whatever tpr: with
 // 4 threads a thread holds one p_k, with 2 it holds p_part and p_(part+2).  So the launch shapes
 // the autotuner picks do not change the result.
+// Output rows [o_lo, o_hi) only (x_E rows are o < nE, t_T rows o >= nE).
 template <class T, int RB>
 __device__ __forceinline__ void edge_rows(const DevModel& dm, const cpx<T>* S, const cpx<T>* Ye, int nE, int nT,
                                           const cpx<T>* rE, int vs, int cnt, int tpr, int r0, int e1o, int to,
-                                          cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out) {
-    const int no = nE + nT;
-    for (int base = 0; base < no * tpr; base += blockDim.x) {
+                                          cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out, int o_lo,
+                                          int o_hi) {
+    const int no = o_hi;
+    for (int base = 0; base < (o_hi - o_lo) * tpr; base += blockDim.x) {
         const int slot = base + threadIdx.x;
-        const int o = slot / tpr, part = slot % tpr;
+        const int o = o_lo + slot / tpr, part = slot % tpr;
         cpx<T> a0[RB], a1[RB];
 #pragma unroll
         for (int q = 0; q < RB; ++q) { a0[q] = mk<T>(0, 0); a1[q] = mk<T>(0, 0); }
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
                                                     const cpx<T>* __restrict__ Y, const double2* __restrict__ z,
                                                     double zsign, const double2* __restrict__ bt, int R,
                                                     cpx<T>* __restrict__ xE_out, cpx<T>* __restrict__ tT_out,
-                                                    const int* __restrict__ done, int ntask, int stage_off, int vs) {
+                                                    const int* __restrict__ done, int ntask, int stage_off, int vs,
+                                                    int rows) {
     if (done && *done) return;
     extern __shared__ __align__(128) char smem[];
     const CtaGroup g;
@@ -110,7 +113,9 @@ __global__ void __launch_bounds__(256) k_pass1_edge(DevModel dm, const cpx<T>* _
     // every vertex and edge slot is type-1 edge or type-2, so nE + nT = 4p <= 128 (p <= 32): four
     // threads per output row when all rows fit the CTA so, else two
     const int tpr = (nE + nT) * 4 <= (int)blockDim.x ? 4 : 2;
-    edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out);
+    // rows: 0 all output rows, 1 the x_E rows only, 2 the t_T rows only (no S_E^-1 read)
+    const int o_lo = rows == 2 ? nE : 0, o_hi = rows == 1 ? nE : nE + nT;
+    edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out, o_lo, o_hi);
 }
 
 // The same pass as one persistent launch over a degree-sorted work list.  Task t is (element
@@ -191,7 +196,8 @@ __global__ void __launch_bounds__(256) k_pass1_edge_p(DevModel dm, const cpx<T>*
         if (s_fail) break;
         int tpr = tpr_force > 0 ? tpr_force : (tpr_p ? (int)tpr_p[dm.p[e]] : 0);
         if (tpr != 2 && tpr != 4) tpr = nE + nT <= 64 ? 4 : 2;
-        edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out);
+        edge_rows<T, RB>(dm, S, Y + dm.pq_off[e], nE, nT, rE, vs, cnt, tpr, r0, e1o, to, xE_out, tT_out, 0,
+                         nE + nT);
         __syncthreads();
     }
     // copies still in flight (after a failure) land before the CTA leaves (bounded waits)
@@ -490,11 +496,11 @@ int edge_cta_threads(int maxNo) { return maxNo > 64 ? std::min(256, (2 * maxNo +
 template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
                        const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
-                       const EdgeSched* es, int item0, int nitems, int tpr_force) {
+                       const EdgeSched* es, int item0, int nitems, int tpr_force, int rows) {
     const int rb = rhs_block(R);
     const cpx<T>* S = (const cpx<T>*)sinv;
     const cpx<T>* Yp = (const cpx<T>*)Y;
-    if (es && es->items) {
+    if (es && es->items && rows == 0) {
         if (nitems < 0) nitems = dm.E;
         switch (rb) {
             case 8: edge_p_t<T, 8>(dm, S, Yp, z, zsign, bt, xE, tT, R, done, *es, item0, nitems, tpr_force, st); break;
@@ -504,19 +510,20 @@ void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, cons
         }
         return;
     }
-    const int so = edge_stage_off<T>(rb, dm.maxE1);
+    // the t_T rows alone read no S_E^-1: no staging
+    const int so = rows == 2 ? 0 : edge_stage_off<T>(rb, dm.maxE1);
     const int ntask = dm.E * ((R + rb - 1) / rb);
-    const size_t sm = edge_smem_total<T>(rb, dm.maxE1);
+    const size_t sm = rows == 2 ? edge_vec_bytes<T>(rb, dm.maxE1) : edge_smem_total<T>(rb, dm.maxE1);
     const int vs = std::max(1, dm.maxE1);
     // CTA size: two threads per output row of the widest element when that is more than 64
     // rows (rounded up to whole warps), else 256; the CTA takes the rows in one pass and fewer
     // threads idle (80 rows at p = 20, l = 5: 160 threads instead of 256 with 96 idle)
     const int nt = es && es->cta_threads > 0 ? es->cta_threads : edge_cta_threads(dm.maxNo);
     switch (rb) {
-        case 8: k_pass1_edge<T, 8><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 4: k_pass1_edge<T, 4><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        case 2: k_pass1_edge<T, 2><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs); break;
-        default: k_pass1_edge<T, 1><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs);
+        case 8: k_pass1_edge<T, 8><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs, rows); break;
+        case 4: k_pass1_edge<T, 4><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs, rows); break;
+        case 2: k_pass1_edge<T, 2><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs, rows); break;
+        default: k_pass1_edge<T, 1><<<ntask, nt, sm, st>>>(dm, S, Yp, z, zsign, bt, R, (cpx<T>*)xE, (cpx<T>*)tT, done, ntask, so, vs, rows);
     }
 }
 template <class T>
@@ -537,8 +544,8 @@ void launch_pass2_edge(const DevModel& dm, const void* Y, const double2* x2, con
         default: k_pass2_edge<T, 1><<<ntask, nt, 0, st>>>(dm, Yp, x2, xi, xo, R, done, ntask);
     }
 }
-template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int);
-template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int);
+template void launch_pass1_edge<double>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int, int);
+template void launch_pass1_edge<float>(const DevModel&, const void*, const void*, const double2*, double, const double2*, void*, void*, int, const int*, cudaStream_t, const EdgeSched*, int, int, int, int);
 template void launch_pass2_edge<double>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
 template void launch_pass2_edge<float>(const DevModel&, const void*, const double2*, const void*, void*, int, const int*, cudaStream_t);
 template <class T>

@@ -47,11 +47,13 @@ struct EdgeSched {
 // requires a load without interior components, pass 2 no recovery).  With es (and es->items)
 // pass 1 is one persistent launch over items[item0 .. item0 + nitems) (nitems < 0: all
 // elements) with the S_E^-1 copy of the next task in flight; tpr_force > 0 overrides the
-// per-degree threads per output row (autotuning)
+// per-degree threads per output row (autotuning).  rows (one-CTA form only): 0 all output rows,
+// 1 only x_E = S_E^-1 r_E, 2 only t_T = Y^T r_E (the result bits of each row do not depend on it)
 template <class T>
 void launch_pass1_edge(const DevModel& dm, const void* sinv, const void* Y, const double2* z, double zsign,
                        const double2* bt, void* xE, void* tT, int R, const int* done, cudaStream_t st,
-                       const EdgeSched* es = nullptr, int item0 = 0, int nitems = -1, int tpr_force = 0);
+                       const EdgeSched* es = nullptr, int item0 = 0, int nitems = -1, int tpr_force = 0,
+                       int rows = 0);
 // default CTA size of the one-CTA-per-task edge pass for elements of at most maxNo output rows
 int edge_cta_threads(int maxNo);
 template <class T>

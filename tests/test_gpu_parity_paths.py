@@ -157,13 +157,15 @@ def test_edge_pass_launch_forms_match_oracle(launch, prec):
 @pytest.mark.parametrize("prec", [ddh.PREC_FP64, ddh.PREC_MIXED_FP32])
 def test_tuned_launch_shapes_do_not_change_the_bits(prec):
     """Every shape an autotuner picks (edge-pass launch form and threads per row, coarse-solve
-    chains and right-hand sides per CTA) leaves each sum in a fixed order: solves pinned to
+    chains and right-hand sides per CTA), and the split of pass 1 into its t_T rows and its x_E
+    rows on a forked stream, leave each sum in a fixed order: solves pinned to
     different shapes agree bit for bit, so the tuners' timing noise cannot change iteration
     counts."""
     w = _with_rhs(ND_SMALL["hanging_corner"](), 8)
     outs = []
     for opts in ({}, {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "nd_chains": 1},
-                 {"edge_launch": ddh.EDGE_LAUNCH_PERSISTENT, "nd_chains": 2}, {"nd_chains": 4}):
+                 {"edge_launch": ddh.EDGE_LAUNCH_PERSISTENT, "nd_chains": 2}, {"nd_chains": 4},
+                 {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "split_pass1": 0}):
         s = _solver(w, tol=1e-10, precision=prec, coarse_form=ddh.COARSE_ND_LEVELS, **opts)
         u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
         outs.append((u.cpu(), [x.iterations for x in st], [x.inner_iterations for x in st]))
