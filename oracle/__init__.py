@@ -17,6 +17,9 @@ Modules
   dd           Section 2.3: partial-nullspace dual-primal solve, block inversion with the
                coarse matrix K, Dirichlet preconditioner, FGMRES, recovery.
   adjoint      the adjoint (conjugate) solve and permittivity gradient.
+  poisson      Section 3.1: the Poisson test with zero Dirichlet data and rho jumps, the
+               Dirichlet preconditioner with diagonal scaling, PCG and the spectrum of
+               P^-1 F (pinned to the printed Table 2).
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``; see the
 docstrings for the pin of each part.
