@@ -147,6 +147,10 @@ typedef struct {
                               on a forked stream beside the coarse solve (same result bits; measured
                               slower, the x_E rows compete with the coarse solve); 0 (default) = one
                               pass-1 launch */
+    int32_t nd_pdl;        /* 1: each per-level nested-dissection launch after the first of a chain is
+                              a programmatic dependent launch of the one before it (it waits for that
+                              level before touching memory; only CTA scheduling overlaps; same result
+                              bits; measured slower); 0 (default) = plain stream order */
 } ddh_options;
 
 typedef struct {

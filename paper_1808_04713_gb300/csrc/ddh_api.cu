@@ -1213,16 +1213,22 @@ static void nd_level_chain(ddh_ctx* ctx, const NDDev& D, bool f32nd, const doubl
                            u, R, done, s);
         ctx->launches++;
     }
+    // every level launch after the first of the chain is a programmatic dependent of the one
+    // before it (nd_pdl): its CTAs are scheduled while the previous level drains
+    bool prev_nd = subs;
+    const bool pdl = ctx->opt.nd_pdl != 0;
     for (int lv = cut - 1; lv >= 0; --lv) {
         if (!ctx->nd_fwd_n[lv]) continue;
         launch_nd_forward(D, f32nd, ctx->nd_items + ctx->nd_fwd_off[lv], ctx->nd_fwd_n[lv], ctx->nd_fwd_rows[lv], t, y, u,
-                          R, done, s, rbs ? (*rbs)[lv] : 0);
+                          R, done, s, rbs ? (*rbs)[lv] : 0, pdl && prev_nd);
+        prev_nd = true;
         ctx->launches++;
     }
     for (int lv = 0; lv < cut; ++lv) {
         if (!ctx->nd_bwd_n[lv]) continue;
         launch_nd_backward(D, f32nd, ctx->nd_items + ctx->nd_bwd_off[lv], ctx->nd_bwd_n[lv], ctx->nd_bwd_rows[lv], y, x2,
-                           R, done, s, rbs ? (*rbs)[L + lv] : 0);
+                           R, done, s, rbs ? (*rbs)[L + lv] : 0, pdl && prev_nd);
+        prev_nd = true;
         ctx->launches++;
     }
     if (subs) {
@@ -1837,6 +1843,7 @@ void ddh_default_options(ddh_options* o) {
     o->nd_chains = 0;
     o->inner_passes_fp64 = 0;
     o->split_pass1 = 0;
+    o->nd_pdl = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {

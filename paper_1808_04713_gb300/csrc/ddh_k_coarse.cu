@@ -2,6 +2,7 @@
 // small coarse systems, the nested-dissection multifrontal solve, and the CSR residual of
 // the refinement step.
 #include "ddh_kcommon.cuh"
+#include <utility>
 
 namespace ddh {
 
@@ -395,12 +396,22 @@ __device__ __forceinline__ void nd_backward_node(const NDDev& d, int node, int r
     }
 }
 
+// Programmatic dependent launch between consecutive level launches: a CTA first waits until
+// the previous launch in the stream has completed and its writes are visible (a no-op when
+// this launch was not made dependent), then lets the next launch be scheduled, so that its
+// CTAs are resident when this one ends.  No memory is touched before the wait.
+__device__ __forceinline__ void nd_pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // forward level: one item per CTA
 template <class MT, int RB>
 __global__ void __launch_bounds__(128) k_nd_forward(NDDev d, const int4* __restrict__ items,
                                                     const double2* __restrict__ t, double2* __restrict__ y,
                                                     double2* __restrict__ u, int R, const int* __restrict__ done) {
     using T = typename NDType<MT>::T;
+    nd_pdl_enter();
     if (done && *done) return;
     extern __shared__ __align__(16) char nd_raw[];
     const int4 it = items[blockIdx.x];
@@ -415,6 +426,7 @@ __global__ void __launch_bounds__(128) k_nd_backward(NDDev d, const int4* __rest
                                                      const double2* __restrict__ y, double2* __restrict__ x, int R,
                                                      const int* __restrict__ done) {
     using T = typename NDType<MT>::T;
+    nd_pdl_enter();
     if (done && *done) return;
     extern __shared__ __align__(16) char nd_raw[];
     const int4 it = items[blockIdx.x];
@@ -592,26 +604,41 @@ void nd_set_smem_limits() {
     nd_attr<double2, 1>(); nd_attr<double2, 2>(); nd_attr<double2, 4>(); nd_attr<double2, 8>();
     nd_attr<float2, 1>(); nd_attr<float2, 2>(); nd_attr<float2, 4>(); nd_attr<float2, 8>();
 }
+// launch with (pdl) or without the programmatic-stream-serialization attribute
+template <typename... Exp, typename... Act>
+static void nd_launch(void (*k)(Exp...), dim3 g, size_t sm, cudaStream_t st, bool pdl, Act&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, std::forward<Act>(args)...);
+}
 template <class MT, int RB>
 static void nd_fwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* t, double2* y,
-                     double2* u, int R, const int* done, cudaStream_t st) {
+                     double2* u, int R, const int* done, cudaStream_t st, bool pdl) {
     const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(MT));
-    k_nd_forward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, t, y, u, R, done);
+    nd_launch(k_nd_forward<MT, RB>, dim3(nitems, (R + RB - 1) / RB), sm, st, pdl, d, items, t, y, u, R, done);
 }
 template <class MT, int RB>
 static void nd_bwd_t(const NDDev& d, const int4* items, int nitems, int smem_rows, const double2* y, double2* x,
-                     int R, const int* done, cudaStream_t st) {
+                     int R, const int* done, cudaStream_t st, bool pdl) {
     const size_t sm = std::max<size_t>(16, (size_t)(smem_rows | 1) * RB * sizeof(MT));
-    k_nd_backward<MT, RB><<<dim3(nitems, (R + RB - 1) / RB), 128, sm, st>>>(d, items, y, x, R, done);
+    nd_launch(k_nd_backward<MT, RB>, dim3(nitems, (R + RB - 1) / RB), sm, st, pdl, d, items, y, x, R, done);
 }
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
-                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want) {
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want, bool pdl) {
     if (nitems <= 0) return;
     const int rb_max = nd_rhs_block(smem_rows, R);
     const int rb = rb_want > 0 && rb_want <= rb_max ? rb_want : rb_max;
 #define ND_F(RBV)                                                                             \
-    if (f32) nd_fwd_t<float2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);        \
-    else nd_fwd_t<double2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st);
+    if (f32) nd_fwd_t<float2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st, pdl);   \
+    else nd_fwd_t<double2, RBV>(d, items, nitems, smem_rows, t, y, u, R, done, st, pdl);
     switch (rb) {
         case 8: ND_F(8) break;
         case 4: ND_F(4) break;
@@ -621,13 +648,13 @@ void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, 
 #undef ND_F
 }
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
-                        double2* x, int R, const int* done, cudaStream_t st, int rb_want) {
+                        double2* x, int R, const int* done, cudaStream_t st, int rb_want, bool pdl) {
     if (nitems <= 0) return;
     const int rb_max = nd_rhs_block(smem_rows, R);
     const int rb = rb_want > 0 && rb_want <= rb_max ? rb_want : rb_max;
 #define ND_B(RBV)                                                                          \
-    if (f32) nd_bwd_t<float2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);        \
-    else nd_bwd_t<double2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st);
+    if (f32) nd_bwd_t<float2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st, pdl);   \
+    else nd_bwd_t<double2, RBV>(d, items, nitems, smem_rows, y, x, R, done, st, pdl);
     switch (rb) {
         case 8: ND_B(8) break;
         case 4: ND_B(4) break;

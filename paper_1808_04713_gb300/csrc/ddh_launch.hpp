@@ -107,10 +107,13 @@ struct NDDev {
 constexpr int kNDShortRow = 128;
 // rb_want: right-hand sides per CTA (1, 2, 4 or 8; 0 or larger than nd_rhs_block allows: the
 // largest allowed).  Smaller blocks put more CTAs on a level of few, large fronts.
+// pdl: launch as a programmatic dependent of the previous launch in the stream (the kernel waits
+// for it before touching memory; only the scheduling of its CTAs overlaps)
 void launch_nd_forward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* t,
-                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want = 0);
+                       double2* y, double2* u, int R, const int* done, cudaStream_t st, int rb_want = 0,
+                       bool pdl = false);
 void launch_nd_backward(const NDDev& d, bool f32, const int4* items, int nitems, int smem_rows, const double2* y,
-                        double2* x, int R, const int* done, cudaStream_t st, int rb_want = 0);
+                        double2* x, int R, const int* done, cudaStream_t st, int rb_want = 0, bool pdl = false);
 // largest right-hand-side block whose staged vectors fit in shared memory (and below 2 R)
 int nd_rhs_block(int smem_rows, int R);
 // the levels below a cut in one launch: CTA b walks the subtree nodes

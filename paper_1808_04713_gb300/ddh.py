@@ -36,7 +36,8 @@ class Options(C.Structure):
                 ("coarse_fp32", C.c_int32), ("local_form", C.c_int32),
                 ("inner_tol", C.c_double), ("coarse_form", C.c_int32), ("robin_modified", C.c_int32),
                 ("tensor_cores", C.c_int32), ("inner_krylov_fp32", C.c_int32), ("edge_launch", C.c_int32),
-                ("nd_chains", C.c_int32), ("inner_passes_fp64", C.c_int32), ("split_pass1", C.c_int32)]
+                ("nd_chains", C.c_int32), ("inner_passes_fp64", C.c_int32), ("split_pass1", C.c_int32),
+                ("nd_pdl", C.c_int32)]
 
 
 class Info(C.Structure):

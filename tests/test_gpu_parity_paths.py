@@ -165,7 +165,7 @@ def test_tuned_launch_shapes_do_not_change_the_bits(prec):
     outs = []
     for opts in ({}, {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "nd_chains": 1},
                  {"edge_launch": ddh.EDGE_LAUNCH_PERSISTENT, "nd_chains": 2}, {"nd_chains": 4},
-                 {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "split_pass1": 0}):
+                 {"edge_launch": ddh.EDGE_LAUNCH_PER_TASK, "split_pass1": 1, "nd_pdl": 0}):
         s = _solver(w, tol=1e-10, precision=prec, coarse_form=ddh.COARSE_ND_LEVELS, **opts)
         u, st = s.solve(s.rhs_planewave(w.thetas), tol=1e-10)
         outs.append((u.cpu(), [x.iterations for x in st], [x.inner_iterations for x in st]))
