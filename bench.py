@@ -330,6 +330,11 @@ def run_ours(args):
     bh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
     uh = torch.empty(b.shape, dtype=b.dtype, pin_memory=True)
     bh.copy_(b.cpu())
+    # one untimed call first, like the device-timed warm-up: it allocates the device staging
+    # buffers (which also re-captures the iteration graphs); every timed call still copies the
+    # loads in and the solution out
+    st_ = s.lib.ddh_solve_host(s.h, bh.data_ptr(), uh.data_ptr(), R, TOL, None)
+    assert st_ == 0, s.lib.ddh_last_error(s.h)
     e2e_t = []
     for _ in range(max(1, args.steps)):
         with torch.cuda.stream(stream):
