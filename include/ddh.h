@@ -197,6 +197,27 @@ ddh_status ddh_set_mesh(ddh_ctx* ctx, int32_t base_n, const int32_t* leaves,
 /* Wavenumber k > 0 and relative permittivity eps_r[e] > 0 per element (host pointer). */
 ddh_status ddh_set_coefficients(ddh_ctx* ctx, double k, const double* eps_r);
 
+/* Poisson mode (Sec. 3.1, Table 2 test problem): -div(rho grad phi) = f on the mesh's square with
+ * zero Dirichlet data on the whole boundary, rho[e] > 0 per element (host pointer, n_elem
+ * entries; piecewise constant).  Replaces ddh_set_coefficients (a later ddh_set_coefficients
+ * returns the context to the Helmholtz problem).  The Dirichlet data enter as constraints
+ * (Sec. 2.2.1): Algorithm 1 discards the boundary vertices and the edge moments 2..l of every
+ * boundary side, and the moments above l of a boundary side become single-sided dual rows.
+ * ddh_factor then builds the same pieces with the element operators rho_e (K (x) M + M (x) K),
+ * and the Dirichlet preconditioner takes the diagonal scaling of Sec. 2.3.3 (W^(j) with
+ * diag(A_EE)^-1).  In this mode ddh_solve runs preconditioned conjugate gradients on the dual
+ * problem in FP64 (options precision and tensor_cores are ignored; tol is the relative residual
+ * reduction of PCG), ddh_apply_dual_operator applies this F and scaled P^-1, and
+ * ddh_pcg_spectrum reports the Lanczos estimates of the extreme eigenvalues of P^-1 F.
+ * ddh_rhs_planewave, ddh_grad_eps and ddh_grad_k return DDH_ERR_INVALID_ARG.  Meshes with hanging
+ * edges are rejected (DDH_ERR_INVALID_ARG). */
+ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho);
+
+/* Poisson mode: the smallest and largest eigenvalue of the Lanczos matrix built from the PCG
+ * coefficients of right-hand side r of the last ddh_solve (Ritz values of P^-1 F, Sec. 3.1 reads
+ * lambda_max this way).  DDH_ERR_NOT_READY before a Poisson solve or for r out of range. */
+ddh_status ddh_pcg_spectrum(const ddh_ctx* ctx, int32_t r, double* lambda_min, double* lambda_max);
+
 /* Build every table and factor: per-element edge Schur complements of A11 through the
  * fast-diagonalisation solver (Sec. 2.2.1 fast solver; Sec. 2.3.3 block inversion), the
  * coarse matrix K = A22 - A12^T A11^-1 A12 and its nested-dissection factor, the preconditioner
@@ -348,7 +369,8 @@ ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);
  * factor is built also when the device would use the dense K^-1 made from it);
  * seconds_out[5]: classification and factorisation wall time, the relative residual
  * ||K x - t||/||t|| of one coarse solve with a seeded random t, max_e ||S_E S_E^-1 - I||_max, and
- * the minimum relative resonance gap of the interior blocks; l_out: l in use. */
+ * the minimum relative resonance gap of the interior blocks; l_out: l in use.  k = 0 selects
+ * the Poisson mode of ddh_set_poisson with eps_r read as rho. */
 ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem,
                            double k, const double* eps_r, int32_t l_override, int64_t* sizes_out,
                            double* seconds_out, int32_t* l_out);

@@ -17,9 +17,13 @@ entries on the interpolatory-basis trace slots, the same rows up to a constant):
   W^(j) = [I 0; -(A_ii)^-1 A_ei^T 0] diag(diag(A_ee)^-1, I) over the edge (e) and interior (i)
   unknowns of A11 (W2 = 0; the mesh is conforming, so C2 = 0);
 * PCG on F nu = g, F = C^ A^-1 C^T, with P^-1 (Sec. 2.3.3 Poisson paragraph), and the extreme
-  eigenvalues of P^-1 F by a dense eigensolve (small cases).
+  eigenvalues of P^-1 F by a dense eigensolve (small cases);
+* the recovered field phi = Z A^-1 (b^ - C^T nu) in the N basis;
+* Lanczos estimates of the extreme eigenvalues from the PCG coefficients.
 
-Parity pinned against the paper's Table 2 in tests/test_oracle_poisson.py.
+Parity pinned against the paper's Table 2 in tests/test_oracle_poisson.py, and the recovered
+field against the exact solution sin(pi x) sin(pi y) of a manufactured problem (rho = 1) and
+against the all-primal split (l = p, no dual rows) for piecewise rho.
 """
 from __future__ import annotations
 
@@ -208,9 +212,23 @@ class Solver:
         x1, _ = self.Ahat_solve(bh[:self.dd.n1], bh[self.dd.n1:])
         return self.C1 @ x1
 
-    def pcg(self, g, tol=1e-10, maxit=500):
+    def solve(self, b_N, tol=1e-12):
+        """phi (N basis, element-local) of the Poisson problem with load b_N: PCG on F nu = g,
+        then the recovery A^ phi^ = b^ - C^T nu (Sec. 2.3.3) and phi = Z phi^ back in the N basis
+        (B (x) B is involutory).  Returns (phi_N, iterations)."""
+        dd = self.dd
+        bh = dd.Z.T @ (dd.B @ b_N)
+        if dd.nd:
+            nu, its = self.pcg(self.rhs(b_N), tol=tol)
+        else:
+            nu, its = np.zeros(0), 0
+        x1, x2 = self.Ahat_solve(bh[:dd.n1] - self.C1.T @ nu, bh[dd.n1:])
+        return dd.B @ (dd.Z @ np.concatenate([x1, x2])), its
+
+    def pcg(self, g, tol=1e-10, maxit=500, coeffs=None):
         """Preconditioned conjugate gradients on F nu = g from nu = 0; iterations until
-        ||g - F nu|| <= tol ||g||."""
+        ||g - F nu|| <= tol ||g||.  With a list `coeffs`, appends (alpha_j, beta_j) of every
+        iteration (beta of the last one is None)."""
         nu = np.zeros_like(g)
         r = g.copy()
         z = self.apply_P(r)
@@ -223,9 +241,31 @@ class Solver:
             nu += a * d
             r -= a * Fd
             if np.linalg.norm(r) <= tol * g0:
+                if coeffs is not None:
+                    coeffs.append((a, None))
                 return nu, it
             z = self.apply_P(r)
             rz_new = r @ z
+            if coeffs is not None:
+                coeffs.append((a, rz_new / rz))
             d = z + (rz_new / rz) * d
             rz = rz_new
         return nu, maxit
+
+
+def lanczos_extremes(coeffs):
+    """Extreme eigenvalues of the Lanczos matrix of k CG steps (the CG-Lanczos relation, e.g.
+    Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.7.3): T_00 = 1/alpha_0,
+    T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j-1} = sqrt(beta_{j-1})/alpha_{j-1}; its
+    eigenvalues are Ritz values of P^-1 F (Sec. 3.1 reads lambda_max by Lanczos)."""
+    k = len(coeffs)
+    T = np.zeros((k, k))
+    for j in range(k):
+        a = coeffs[j][0]
+        T[j, j] = 1.0 / a
+        if j:
+            ap, bp = coeffs[j - 1]
+            T[j, j] += bp / ap
+            T[j, j - 1] = T[j - 1, j] = np.sqrt(bp) / ap
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[0]), float(ev[-1])

@@ -120,6 +120,8 @@ struct ddh_ctx {
     // Krylov solvers: dual interface problem (plain solve / inner preconditioner) and the
     // FP64 outer refinement on the conforming primal system (mixed precision)
     KState kin, kout;
+    // Poisson mode: extreme Ritz values of P^-1 F from the PCG coefficients of the last solve
+    std::vector<double> pcg_lmin, pcg_lmax;
 };
 
 // accessors for translation units that do not see the context definition
@@ -245,13 +247,13 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     int pmax = 0;
     std::vector<int> p(E), e1o(E), ne1(E), to(E), nt(E), ptab(E);
     std::vector<int64_t> off(E), so(E);
-    std::vector<double> c(E), gam(4 * E), geo(3 * E);
+    std::vector<double> c(E), ks(E), gam(4 * E), geo(3 * E);
     std::vector<int> bmask(E, 0);
     for (int e = 0; e < E; ++e) {
         const Elem& El = m.el[e];
         pmax = std::max(pmax, El.p);
         p[e] = El.p; e1o[e] = El.e1_off; ne1[e] = El.nE1; to[e] = El.t_off; nt[e] = El.nT;
-        ptab[e] = El.ptab; off[e] = El.off; so[e] = El.sinv_off; c[e] = El.c;
+        ptab[e] = El.ptab; off[e] = El.off; so[e] = El.sinv_off; c[e] = El.c; ks[e] = El.rho;
         for (int s = 0; s < 4; ++s) gam[4 * e + s] = El.gam[s].imag();
         for (int s = 0; s < 4; ++s) bmask[e] |= El.boundary[s] ? (1 << s) : 0;
         geo[3 * e] = El.x0; geo[3 * e + 1] = El.y0; geo[3 * e + 2] = El.h;
@@ -270,11 +272,12 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, so, &d.sinv_off))) return st;
     if ((st = upload(ctx, ptab, &d.ptab))) return st;
     if ((st = upload(ctx, c, &d.c))) return st;
+    if ((st = upload(ctx, ks, &d.ks))) return st;
     if ((st = upload(ctx, gam, &d.gam))) return st;
     if ((st = upload(ctx, bmask, &d.bmask))) return st;
     if ((st = upload(ctx, geo, &d.geo))) return st;
     {
-        // 1 / (mu_a + mu_b + c_e mu_a mu_b): the divide of the element fast solver
+        // 1 / (rho_e (mu_a + mu_b + c_e mu_a mu_b)): the divide of the element fast solver
         std::vector<int64_t> doff(E);
         std::vector<double> dv;
         for (int e = 0; e < E; ++e) {
@@ -283,7 +286,7 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             const int n = El.p - 1;
             doff[e] = (int64_t)dv.size();
             for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) dv.push_back(1.0 / (mu[a] + mu[b] + El.c * mu[a] * mu[b]));
+                for (int b = 0; b < n; ++b) dv.push_back(1.0 / (mu[a] + mu[b] + El.c * mu[a] * mu[b]) / El.rho);
         }
         if ((st = upload(ctx, dv, &d.dinv_all))) return st;
         if ((st = upload(ctx, doff, &d.dinv_off))) return st;
@@ -366,6 +369,31 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, m.row_c, &d.row_c))) return st;
     if ((st = upload(ctx, m.row_f, &d.row_f))) return st;
     if ((st = upload(ctx, m.row_hblock, &d.row_hb))) return st;
+    if (m.dirichlet) {
+        // diagonal scaling of the Dirichlet preconditioner (Sec. 2.3.3, Poisson): w = 1/diag(A_EE)
+        // per type-1 edge slot, rho_e w for the output side of rho_e S^Lap, and per dual row the
+        // inverse of (C W C^T)_rr = sum of w over the row's slots
+        std::vector<double> win(m.e1_slot.size()), wout(m.e1_slot.size()), rdi(m.n_dual, 0.0);
+        for (int e = 0; e < E; ++e) {
+            const Elem& El = m.el[e];
+            const int N = El.p + 1;
+            for (int i = 0; i < El.nE1; ++i) {
+                const int slot = m.e1_slot[El.e1_off + i];
+                const double dg = elem_entry(m, El, slot % N, slot / N, slot % N, slot / N, false).real();
+                win[El.e1_off + i] = 1.0 / dg;
+                wout[El.e1_off + i] = El.rho / dg;
+            }
+        }
+        for (int64_t r = 0; r < m.n_dual; ++r) {
+            double sw = 0;
+            if (m.row_c[r] >= 0) sw += win[m.row_c[r]];
+            if (m.row_f[r] >= 0) sw += win[m.row_f[r]];
+            rdi[r] = 1.0 / sw;
+        }
+        if ((st = upload(ctx, win, &d.e1_win))) return st;
+        if ((st = upload(ctx, wout, &d.e1_wout))) return st;
+        if ((st = upload(ctx, rdi, &d.row_dinv))) return st;
+    }
     if ((st = upload(ctx, m.c2_ptr, &d.c2_ptr))) return st;
     std::vector<int> c2col(m.c2_col.size());
     for (size_t i = 0; i < c2col.size(); ++i) c2col[i] = newidx[m.c2_col[i]];
@@ -1757,6 +1785,147 @@ static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
     return conv ? DDH_OK : fail(ctx, DDH_ERR_NO_CONVERGENCE, "tolerance not reached within maxit");
 }
 
+// Extreme eigenvalues of the symmetric tridiagonal Lanczos matrix of k CG steps (Saad,
+// Iterative Methods for Sparse Linear Systems, Sec. 6.7.3): T_00 = 1/a_0,
+// T_jj = 1/a_j + b_{j-1}/a_{j-1}, T_j,j-1 = sqrt(b_{j-1})/a_{j-1}; by Sturm-sequence bisection.
+static void lanczos_extremes(const double* a, const double* b, int k, double& lmin, double& lmax) {
+    lmin = lmax = 0.0;
+    if (k <= 0 || !(a[0] > 0.0)) return;
+    std::vector<double> dg(k), of(k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        dg[j] = 1.0 / a[j] + (j > 0 ? b[j - 1] / a[j - 1] : 0.0);
+        if (j > 0) of[j] = std::sqrt(std::max(0.0, b[j - 1])) / a[j - 1];
+    }
+    double lo = 1e300, hi = -1e300;          // Gershgorin interval
+    for (int j = 0; j < k; ++j) {
+        const double rad = std::fabs(of[j]) + (j + 1 < k ? std::fabs(of[j + 1]) : 0.0);
+        lo = std::min(lo, dg[j] - rad);
+        hi = std::max(hi, dg[j] + rad);
+    }
+    // number of eigenvalues below x (pivots of the LDL^T factorisation of T - x I)
+    auto below = [&](double x) {
+        int c = 0;
+        double q = 1.0;
+        for (int j = 0; j < k; ++j) {
+            q = dg[j] - x - (j > 0 ? of[j] * of[j] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0) ++c;
+        }
+        return c;
+    };
+    auto kth = [&](int target) {           // smallest x with below(x) >= target
+        double l = lo, h = hi;
+        for (int it = 0; it < 200 && h - l > 1e-15 * std::max(1.0, std::fabs(h)); ++it) {
+            const double m = 0.5 * (l + h);
+            if (below(m) >= target) h = m; else l = m;
+        }
+        return 0.5 * (l + h);
+    };
+    lmin = kth(1);
+    lmax = kth(k);
+}
+
+// Poisson mode (Sec. 3.1): RHS pass, PCG on F nu = g with the diagonally scaled Dirichlet
+// preconditioner (Sec. 2.3.3), recovery; FP64 element kernels throughout.  PCG stops when
+// ||g - F nu|| <= tol ||g|| (recursively updated residual).
+static ddh_status solve_pcg(ddh_ctx* ctx, const double2* b_dev, double2* u_dev, int R, double tol, ddh_rhs_stats* stats) {
+    const DevModel& d = ctx->dm;
+    cudaStream_t st = ctx->stream;
+    ddh_status sts;
+    void *bt, *phit;
+    if ((sts = get_work(ctx, "bt", sizeof(double2) * (size_t)R * d.n_local, &bt))) return sts;
+    if ((sts = get_work(ctx, "phit", sizeof(double2) * (size_t)R * d.n_local, &phit))) return sts;
+    launch_basis(d, b_dev, (double2*)bt, 0, R, st);
+    ctx->launches++;
+    ctx->refine_active = true;
+    struct Off { ddh_ctx* c; ~Off() { c->refine_active = false; } } off_guard{ctx};
+    Work w;
+    if ((sts = get_op_work(ctx, R, true, w))) return sts;
+    const int maxit = std::max(1, ctx->opt.maxit);
+    const int64_t nd = d.n_dual;
+    const size_t vb = sizeof(double2) * (size_t)R * std::max<int64_t>(1, nd);
+    void *g, *nu, *rv, *z, *dv, *Fd, *part, *sc, *ah, *bh;
+    if ((sts = get_work(ctx, "pcg_g", vb, &g))) return sts;
+    if ((sts = get_work(ctx, "pcg_nu", vb, &nu))) return sts;
+    if ((sts = get_work(ctx, "pcg_r", vb, &rv))) return sts;
+    if ((sts = get_work(ctx, "pcg_z", vb, &z))) return sts;
+    if ((sts = get_work(ctx, "pcg_d", vb, &dv))) return sts;
+    if ((sts = get_work(ctx, "pcg_Fd", vb, &Fd))) return sts;
+    if ((sts = get_work(ctx, "pcg_part", sizeof(double) * (size_t)R * kPcgBlocks, &part))) return sts;
+    if ((sts = get_work(ctx, "pcg_sc", sizeof(double) * 8 * (size_t)R, &sc))) return sts;
+    if ((sts = get_work(ctx, "pcg_ah", sizeof(double) * (size_t)R * maxit, &ah))) return sts;
+    if ((sts = get_work(ctx, "pcg_bh", sizeof(double) * (size_t)R * maxit, &bh))) return sts;
+    double2 *G = (double2*)g, *NU = (double2*)nu, *RV = (double2*)rv, *Z = (double2*)z, *D = (double2*)dv,
+            *FD = (double2*)Fd;
+    double *PART = (double*)part, *SC = (double*)sc, *AH = (double*)ah, *BH = (double*)bh;
+    const double tol2 = tol * tol;
+    std::vector<int> its(R, 0);
+    std::vector<double> res(R, 0.0), pr;
+    std::vector<double> hsc(8 * (size_t)R, 0.0);
+    // g = C^ A^-1 b^ (interior loads included)
+    apply_op<double>(ctx, w, nullptr, 0.0, (const double2*)bt, 1, G, nullptr, R, nullptr);
+    CK(cudaMemsetAsync(SC, 0, sizeof(double) * 8 * (size_t)R, st));
+    CK(cudaMemsetAsync(AH, 0, sizeof(double) * (size_t)R * maxit, st));
+    CK(cudaMemsetAsync(BH, 0, sizeof(double) * (size_t)R * maxit, st));
+    int done_all = 0;
+    if (nd > 0) {
+        CK(cudaMemsetAsync(NU, 0, vb, st));
+        CK(cudaMemcpyAsync(RV, G, vb, cudaMemcpyDeviceToDevice, st));
+        launch_dual_dot(RV, RV, nd, PART, R, st);
+        launch_pcg_scalar(PART, SC, 0, 0, tol2, AH, BH, maxit, R, st);
+        apply_prec<double>(ctx, w, RV, Z, R, nullptr);
+        launch_dual_dot(RV, Z, nd, PART, R, st);
+        launch_pcg_scalar(PART, SC, 1, 0, tol2, AH, BH, maxit, R, st);
+        CK(cudaMemcpyAsync(D, Z, vb, cudaMemcpyDeviceToDevice, st));
+        ctx->launches += 4;
+        int it = 0;
+        for (; it < maxit; ++it) {
+            apply_op<double>(ctx, w, D, 1.0, nullptr, 0, FD, nullptr, R, nullptr);   // F d
+            launch_dual_dot(D, FD, nd, PART, R, st);
+            launch_pcg_scalar(PART, SC, 2, it, tol2, AH, BH, maxit, R, st);
+            launch_pcg_xr(NU, RV, D, FD, SC, nd, PART, R, st);
+            launch_pcg_scalar(PART, SC, 3, it, tol2, AH, BH, maxit, R, st);
+            ctx->launches += 4;
+            CK(cudaMemcpyAsync(hsc.data(), SC, sizeof(double) * 8 * (size_t)R, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            done_all = 1;
+            for (int r = 0; r < R; ++r) done_all &= hsc[8 * r + 4] != 0.0;
+            if (done_all) break;
+            apply_prec<double>(ctx, w, RV, Z, R, nullptr);
+            launch_dual_dot(RV, Z, nd, PART, R, st);
+            launch_pcg_scalar(PART, SC, 4, it, tol2, AH, BH, maxit, R, st);
+            launch_pcg_d(D, Z, SC, nd, R, st);
+            ctx->launches += 3;
+        }
+        CK(cudaMemcpyAsync(hsc.data(), SC, sizeof(double) * 8 * (size_t)R, cudaMemcpyDeviceToHost, st));
+        std::vector<double> ha((size_t)R * maxit), hb((size_t)R * maxit);
+        CK(cudaMemcpyAsync(ha.data(), AH, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hb.data(), BH, sizeof(double) * hb.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        ctx->pcg_lmin.assign(R, 0.0);
+        ctx->pcg_lmax.assign(R, 0.0);
+        for (int r = 0; r < R; ++r) {
+            const bool dn = hsc[8 * r + 4] != 0.0;
+            its[r] = dn ? (int)hsc[8 * r + 5] : maxit;
+            res[r] = hsc[8 * r + 3] > 0 ? std::sqrt(hsc[8 * r + 6] / hsc[8 * r + 3]) : 0.0;
+            lanczos_extremes(ha.data() + (size_t)r * maxit, hb.data() + (size_t)r * maxit, its[r], ctx->pcg_lmin[r],
+                             ctx->pcg_lmax[r]);
+        }
+        // recovery: A^ phi = b^ - C^T nu
+        apply_op<double>(ctx, w, NU, -1.0, (const double2*)bt, 1, nullptr, (double2*)phit, R, nullptr);
+    } else {
+        apply_op<double>(ctx, w, nullptr, 0.0, (const double2*)bt, 1, nullptr, (double2*)phit, R, nullptr);
+        ctx->pcg_lmin.assign(R, 0.0);
+        ctx->pcg_lmax.assign(R, 0.0);
+        done_all = 1;
+    }
+    launch_basis(d, (const double2*)phit, u_dev, 0, R, st);
+    ctx->launches++;
+    CK(cudaGetLastError());
+    if ((sts = finish_stats(ctx, (const double2*)bt, (const double2*)phit, R, its, {}, res, stats))) return sts;
+    return done_all ? DDH_OK : fail(ctx, DDH_ERR_NO_CONVERGENCE, "PCG tolerance not reached within maxit");
+}
+
 // mixed precision: FP64 FGMRES on the conforming primal system A_c u = b_c (residuals,
 // Arnoldi, Hessenberg least squares in FP64); preconditioner = one dual-primal solve with
 // complex64 element kernels and a fixed number of dual FGMRES iterations (coarse solve FP64),
@@ -1911,6 +2080,25 @@ ddh_status ddh_set_coefficients(ddh_ctx* ctx, double k, const double* eps) {
     return DDH_OK;
 }
 
+ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->have_mesh) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh first");
+    if (!rho) return fail(ctx, DDH_ERR_INVALID_ARG, "rho must be non-null");
+    std::string err;
+    if (!set_poisson(ctx->m, rho, err)) return fail(ctx, DDH_ERR_INVALID_ARG, err);
+    ctx->have_coef = true;
+    ctx->factored = false;
+    return DDH_OK;
+}
+
+ddh_status ddh_pcg_spectrum(const ddh_ctx* ctx, int32_t r, double* lambda_min, double* lambda_max) {
+    if (!ctx || !lambda_min || !lambda_max) return DDH_ERR_INVALID_ARG;
+    if (!ctx->m.dirichlet || r < 0 || r >= (int32_t)ctx->pcg_lmax.size()) return DDH_ERR_NOT_READY;
+    *lambda_min = ctx->pcg_lmin[r];
+    *lambda_max = ctx->pcg_lmax[r];
+    return DDH_OK;
+}
+
 ddh_status ddh_factor(ddh_ctx* ctx, const ddh_options* opt) {
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->have_mesh || !ctx->have_coef) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh and coefficients first");
@@ -1983,6 +2171,7 @@ ddh_status ddh_rhs_planewave(ddh_ctx* ctx, const double* theta, int32_t R, void*
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!theta || R <= 0 || !b_dev) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
     void* th;
     void* bt;
     ddh_status st;
@@ -2005,6 +2194,7 @@ ddh_status ddh_solve(ddh_ctx* ctx, const void* b_dev, void* u_dev, int32_t R, do
     if (((uintptr_t)b_dev | (uintptr_t)u_dev) & 15) return fail(ctx, DDH_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     if (tol <= 0) tol = ctx->opt.tol;
     cudaSetDevice(ctx->device);
+    if (ctx->m.dirichlet) return solve_pcg(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
     if (ctx->opt.precision == DDH_PREC_MIXED_FP32)
         return solve_mixed(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
     return solve_plain(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
@@ -2056,6 +2246,7 @@ ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, in
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !grad_eps_dev || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
     void *ut, *lt;
     ddh_status st;
     const size_t bytes = sizeof(double2) * (size_t)R * ctx->dm.n_local;
@@ -2075,6 +2266,7 @@ ddh_status ddh_grad_k(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, cons
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !theta || !grad_k_host || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
     void *ut, *lt, *db, *pe, *th;
     ddh_status st;
     const DevModel& d = ctx->dm;
@@ -2308,11 +2500,15 @@ void ddh_destroy(ddh_ctx* ctx) {
 
 ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem, double k,
                            const double* eps, int32_t l_override, int64_t* sizes, double* secs, int32_t* l_out) {
-    if (!leaves || !p || !eps || !sizes || !secs || n_elem <= 0 || !(k > 0)) return DDH_ERR_INVALID_ARG;
+    if (!leaves || !p || !eps || !sizes || !secs || n_elem <= 0 || !(k >= 0)) return DDH_ERR_INVALID_ARG;
     Model m;
     std::string err;
     if (!build_model(m, base_n, leaves, p, n_elem, err)) return DDH_ERR_INVALID_ARG;
-    set_coefficients(m, k, eps);
+    if (k == 0.0) {
+        if (!set_poisson(m, eps, err)) return DDH_ERR_INVALID_ARG;
+    } else {
+        set_coefficients(m, k, eps);
+    }
     const int l = l_override > 0 ? l_override : dispersion_l(m);
     auto t0 = std::chrono::steady_clock::now();
     if (!classify(m, l, err)) return DDH_ERR_INVALID_ARG;

@@ -44,10 +44,12 @@ struct DevModel {
     const int64_t* pq_off = nullptr;    // start of Y = [A11^-1 A_1T]_E (nE x nT, row-major)
     const int* ptab = nullptr;
     const double* c = nullptr;          // -k^2 eps (h/2)^2
+    const double* ks = nullptr;         // element coefficient: A_e = ks_e (K(x)M + M(x)K + c_e M(x)M + Robin);
+                                        // rho in the Poisson mode (c_e = 0, no Robin), else 1
     const double* gam = nullptr;        // [E][4] imaginary part of gamma_eff (real part 0)
     const int* bmask = nullptr;         // [E] bit s set when side s lies on the domain boundary
     const double* geo = nullptr;        // [E][3] x0, y0, h
-    const double* dinv_all = nullptr;   // per element n^2: 1 / (mu_a + mu_b + c_e mu_a mu_b)
+    const double* dinv_all = nullptr;   // per element n^2: 1 / (ks_e (mu_a + mu_b + c_e mu_a mu_b))
     const int64_t* dinv_off = nullptr;
     // per degree table t
     const int* tab_p = nullptr;
@@ -66,6 +68,11 @@ struct DevModel {
     const int* e1_row = nullptr;
     const double* e1_sign = nullptr;
     const int* e1_eall = nullptr;
+    // Poisson mode (diagonally scaled Dirichlet preconditioner, Sec. 2.3.3): per E1 slot
+    // w = 1 / diag(A_EE) and rho_e w, per dual row 1 / (C W C^T)_rr; null otherwise
+    const double* e1_win = nullptr;
+    const double* e1_wout = nullptr;
+    const double* row_dinv = nullptr;
     // T slots and slaving (CSR over coarse dofs)
     const int* t_slot = nullptr;
     const int* t_ptr = nullptr;

@@ -107,7 +107,7 @@ cd elem_entry(const Model& m, const Elem& E, int a, int b, int c, int d, bool st
     if (a == 0 && c == 0) v += E.gam[1] * Mbd;
     if (b == 1 && d == 1) v += E.gam[2] * Mac;
     if (b == 0 && d == 0) v += E.gam[3] * Mac;
-    return v;
+    return E.rho * v;
 }
 
 // Complex Gauss-Jordan inverse with partial pivoting on the augmented system [A | I]
@@ -189,15 +189,15 @@ static void cross_slots(int p, std::vector<int>& X) {
             if (a <= 3 || b <= 3) X.push_back(a + N * b);
 }
 
-// G = A_II^-1 restricted to the cross (row-major |X| x |X|) for FDM parameter c
-static void cross_green(const PTable& T, double c, const std::vector<int>& X, std::vector<double>& G,
+// G = A_II^-1 restricted to the cross (row-major |X| x |X|) for A_II = rho (K (x) M + M (x) K + c M (x) M)
+static void cross_green(const PTable& T, double rho, double c, const std::vector<int>& X, std::vector<double>& G,
                         double* gap) {
     const int n = T.n, N = T.p + 1, nx = (int)X.size();
     std::vector<double> Dinv((size_t)n * n);
     double dmin = 1e300, dmax = 0;
     for (int al = 0; al < n; ++al)
         for (int be = 0; be < n; ++be) {
-            const double D = T.mu[al] + T.mu[be] + c * T.mu[al] * T.mu[be];
+            const double D = rho * (T.mu[al] + T.mu[be] + c * T.mu[al] * T.mu[be]);
             dmin = std::min(dmin, std::fabs(D));
             dmax = std::max(dmax, std::fabs(D));
             Dinv[(size_t)al * n + be] = 1.0 / D;
@@ -286,7 +286,7 @@ static void build_slap_tables(Model& m) {
         Elem E;
         E.p = p; E.ptab = m.ptab_of_p[p];
         std::vector<double> G;
-        cross_green(T, 0.0, X, G, nullptr);
+        cross_green(T, 1.0, 0.0, X, G, nullptr);
         const int nx = (int)X.size();
         std::vector<cd> AEE, AEX, AXE;
         auto f = [&](int a, int b, int c, int d) { return elem_entry(m, E, a, b, c, d, true); };
@@ -324,7 +324,7 @@ bool factor(Model& m, int nthreads, std::string& err) {
         cross_slots(El.p, X);
         const int nE = El.nE1, nT = El.nT, nX = (int)X.size();
         std::vector<double> Gr;
-        cross_green(T, El.c, X, Gr, &ef[e].gap);
+        cross_green(T, El.rho, El.c, X, Gr, &ef[e].gap);
         std::vector<cd> G(Gr.begin(), Gr.end());
         auto f = [&](int a, int b, int c, int d) { return elem_entry(m, El, a, b, c, d, false); };
         std::vector<cd> AEE, AEX, AXE, AET, AXT, ATE, ATX, ATT;
@@ -442,7 +442,7 @@ bool factor(Model& m, int nthreads, std::string& err) {
             cross_slots(El.p, X);
             const int nE = El.nE1, nT = El.nT, nX = (int)X.size();
             std::vector<double> Gr;
-            cross_green(T, 0.0, X, Gr, nullptr);
+            cross_green(T, 1.0, 0.0, X, Gr, nullptr);
             std::vector<cd> G(Gr.begin(), Gr.end());
             auto f = [&](int a, int b, int c, int d) { return elem_entry(m, El, a, b, c, d, true); };
             std::vector<cd> AEX, AXE, AET, AXT, ATE, ATX, ATT, SE((size_t)nE * nE), Sinv;

@@ -39,6 +39,7 @@ struct Elem {
     int p = 0, n = 0, lev = 0, i = 0, j = 0;
     int64_t X0 = 0, X1 = 0, Y0 = 0, Y1 = 0;       // integer box (finest units)
     double h = 0, x0 = 0, y0 = 0, eps = 1, c = 0;
+    double rho = 1;                                // stiffness coefficient (Poisson mode, Sec. 3.1)
     cd gam[4];                                     // Robin gamma_eff per side (set_robin)
     bool boundary[4] = {false, false, false, false};
     int64_t off = 0;                               // start in local vectors
@@ -64,6 +65,10 @@ struct Model {
     std::vector<Elem> el;
     double k = 0;
     int l = 0;
+    // Poisson mode (Sec. 3.1): -div(rho grad phi) = f with zero Dirichlet data on the whole
+    // boundary; the boundary vertices and the moments 2..l of a boundary side are discarded,
+    // its moments above l become single-sided dual rows (Sec. 2.2.1 Dirichlet constraints)
+    bool dirichlet = false;
     std::unordered_map<uint64_t, int> leaf_of;    // (level, i, j) key -> element
     // tables
     std::vector<PTable> tabs;
@@ -81,7 +86,8 @@ struct Model {
     std::vector<double> t_w;
     // dual rows
     int64_t n_dual = 0;
-    std::vector<int32_t> row_c, row_f;            // E1 global index (c may be -1)
+    std::vector<int32_t> row_c, row_f;            // E1 global index (c -1 on hanging rows, f -1 on
+                                                  // the single-sided rows of a Dirichlet side)
     std::vector<int32_t> row_hblock;              // -1 conforming, else hanging block id
     std::vector<int32_t> c2_ptr, c2_col;          // C2 CSR by dual row
     std::vector<double> c2_w;
@@ -128,6 +134,9 @@ bool build_model(Model& m, int base_n, const int32_t* leaves, const int32_t* p, 
 // element containing (x, y) in [0,1]^2 and the canonical coordinates (u1, u2) in [-1,1]^2
 int locate_point(const Model& m, double x, double y, double& u1, double& u2);
 void set_coefficients(Model& m, double k, const double* eps);
+// Poisson mode: k = 0, eps = 1, rho[e] > 0 per element, zero Dirichlet data on the boundary
+// (no Robin terms); the mesh must be conforming (returns false with err otherwise)
+bool set_poisson(Model& m, const double* rho, std::string& err);
 // Robin coefficients per element side: gamma_eff = -i k h/2 on the boundary of the domain;
 // with `modified` (the Robin-modified local problems of Sec. 2.3.4) also +- i k h/2 on each
 // conforming interior side shared with an element of the opposite sign of the weak
@@ -150,7 +159,9 @@ bool host_invert(int n, const std::vector<cd>& A, std::vector<cd>& inv, double& 
 void host_gemm(int M, int K, int N, const cd* A, const cd* B, cd* C, bool subtract, int nthreads);
 
 // entry of the element operator (interpolatory basis) for element e:
-// A[(a,b),(c,d)] = Kt[a,c] Mt[b,d] + Mt[a,c] Kt[b,d] + c_e Mt[a,c] Mt[b,d] + Robin.
+// A[(a,b),(c,d)] = rho_e (Kt[a,c] Mt[b,d] + Mt[a,c] Kt[b,d] + c_e Mt[a,c] Mt[b,d] + Robin)
+// (rho_e = 1 for Helmholtz; c_e = 0 and no Robin term in the Poisson mode; stiff_only: the
+// unscaled stiffness part alone).
 cd elem_entry(const Model& m, const Elem& e, int a, int b, int c, int d, bool stiff_only);
 
 }  // namespace ddh

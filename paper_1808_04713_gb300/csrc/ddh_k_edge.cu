@@ -291,7 +291,8 @@ __global__ void k_coarse_assemble(DevModel dm, const cpx<T>* __restrict__ tT, co
 }
 
 // ------------------------------------------------------------------ jump gather (C^ x)
-// w[row] = x1_E[c] - x1_E[f] + sum_k C2[row][k] x2[k]
+// w[row] = x1_E[c] - x1_E[f] + sum_k C2[row][k] x2[k] (c absent on hanging rows, f on the
+// single-sided rows of a Dirichlet side)
 template <class T>
 __global__ void k_jump_gather(DevModel dm, const cpx<T>* __restrict__ xE, const double2* __restrict__ x2,
                               double2* __restrict__ w, const int* __restrict__ done) {
@@ -302,7 +303,7 @@ __global__ void k_jump_gather(DevModel dm, const cpx<T>* __restrict__ xE, const 
     double sx = 0, sy = 0;
     const int c = dm.row_c[row], f = dm.row_f[row];
     if (c >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + c]; sx += (double)v.x; sy += (double)v.y; }
-    { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
+    if (f >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
     for (int a = dm.c2_ptr[row]; a < dm.c2_ptr[row + 1]; ++a) {
         const double2 v = x2[(int64_t)r * dm.n_coarse + dm.c2_col[a]];
         sx += dm.c2_w[a] * v.x;
@@ -312,7 +313,8 @@ __global__ void k_jump_gather(DevModel dm, const cpx<T>* __restrict__ xE, const 
 }
 
 // ------------------------------------------------------------------ preconditioner
-// y = D^-1 x, D = C1_E C1_E^T + C2 C2^T: 1/2 on conforming rows, dense blocks on hanging edges
+// y = D^-1 x, D = C1_E C1_E^T + C2 C2^T: 1/2 on conforming rows, dense blocks on hanging edges;
+// in the Poisson mode D = C1 W C1^T (diagonal, one weight per row)
 __global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __restrict__ y, int lumped,
                        const int* __restrict__ done) {
     if (done && *done) return;
@@ -320,6 +322,12 @@ __global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __re
     const int r = blockIdx.y;
     if (row >= dm.n_dual) return;
     const int64_t ro = (int64_t)r * dm.n_dual;
+    if (dm.row_dinv) {
+        const double2 v = x[ro + row];
+        const double w = dm.row_dinv[row];
+        y[ro + row] = make_double2(w * v.x, w * v.y);
+        return;
+    }
     const int hb = dm.row_hb[row];
     if (hb < 0) {
         const double2 v = x[ro + row];
@@ -345,7 +353,8 @@ __global__ void k_dinv(DevModel dm, const double2* __restrict__ x, double2* __re
 // degree pattern and L1/L2-resident); tpr adjacent threads share an output row
 template <class T, int RB>
 __device__ __forceinline__ void pre_apply(const double* __restrict__ S, int nE, int cnt, const cpx<T>* in,
-                                          cpx<T>* __restrict__ out, int64_t ostride) {
+                                          cpx<T>* __restrict__ out, int64_t ostride,
+                                          const double* __restrict__ wout = nullptr) {
     const int tpr = nE <= 32 ? 4 : (nE <= 64 ? 2 : 1);
     const int chunk = (nE + tpr - 1) / tpr;
     for (int base = 0; base < nE * tpr; base += blockDim.x) {
@@ -369,7 +378,7 @@ __device__ __forceinline__ void pre_apply(const double* __restrict__ S, int nE, 
                 acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, o);
                 acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, o);
             }
-            if (part == 0 && i < nE && q < cnt) out[(int64_t)q * ostride + i] = acc[q];
+            if (part == 0 && i < nE && q < cnt) out[(int64_t)q * ostride + i] = wout ? (T)wout[i] * acc[q] : acc[q];
         }
     }
 }
@@ -387,11 +396,16 @@ __global__ void __launch_bounds__(128) k_pre_elem(DevModel dm, const double2* __
         const int q = idx / nE, i = idx % nE;
         const int row = dm.e1_row[e1o + i];
         cpx<T> val = mk<T>(0, 0);
-        if (row >= 0) val = (T)dm.e1_sign[e1o + i] * ld<T>(v, (int64_t)(r0 + q) * dm.n_dual + row);
+        if (row >= 0) {
+            const double w = dm.e1_win ? dm.e1_sign[e1o + i] * dm.e1_win[e1o + i] : dm.e1_sign[e1o + i];
+            val = (T)w * ld<T>(v, (int64_t)(r0 + q) * dm.n_dual + row);
+        }
         in[q * nE + i] = val;
     }
     __syncthreads();
-    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot);
+    // Poisson mode: out = (rho_e w) .* (S^Lap (w .* C1^T v)), the diagonally scaled W^T A W
+    pre_apply<T, RB>(dm.pre_all + dm.pre_off[e], nE, cnt, in, outE + (int64_t)r0 * dm.nE1_tot + e1o, dm.nE1_tot,
+                     dm.e1_wout ? dm.e1_wout + e1o : nullptr);
 }
 
 // Conforming meshes (no hanging rows: D = 2 I, no C2 K C2^T term), fused with the Krylov
@@ -435,7 +449,7 @@ __global__ void k_pre_rows_kry(DevModel dm, KrylovDev K, const cpx<T>* __restric
     double sx = 0, sy = 0;
     const int c = dm.row_c[row], f = dm.row_f[row];
     if (c >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + c]; sx += (double)a.x; sy += (double)a.y; }
-    { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
+    if (f >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
     const double2 z = make_double2(0.5 * sx, 0.5 * sy);
     K.zw[(int64_t)r * K.nd + row] = z;
     K.Zb[((int64_t)r * K.m + jj) * K.nd + row] = z;
@@ -452,7 +466,7 @@ __global__ void k_pre_rows(DevModel dm, const cpx<T>* __restrict__ outE, const d
     double sx = 0, sy = 0;
     const int c = dm.row_c[row], f = dm.row_f[row];
     if (c >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + c]; sx += (double)a.x; sy += (double)a.y; }
-    { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
+    if (f >= 0) { const cpx<T> a = outE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)a.x; sy -= (double)a.y; }
     if (!lumped)
         for (int a = dm.mh_ptr[row]; a < dm.mh_ptr[row + 1]; ++a) {
             const double2 vv = v[(int64_t)r * dm.n_dual + dm.mh_col[a]];

@@ -148,7 +148,8 @@ struct FrameTile {
 };
 
 // Interior coupling of the frame values (cross_coupling for QB right-hand sides at once):
-// rrow[q] / rcol[q] = sign * (interior rows / columns 0, 1 of A_IF Phi_F)
+// rrow[q] / rcol[q] = sign * (interior rows / columns 0, 1 of A_IF Phi_F); callers fold the
+// element coefficient ks into sign
 template <class T, class G>
 __device__ inline void cross_coupling_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int p, T ce, T sign,
                                         const cpx<T>* xe, const cpx<T>* ut, int stride, int Q) {
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
     load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const int64_t off = dm.off[e];
-    const T ce = (T)dm.c[e];
+    const T ce = (T)dm.c[e], ks = (T)dm.ks[e];
     T gam[4];
     elem_gam<T>(dm, e, gam);
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
                 const int q = idx / (nE + nT), i = idx % (nE + nT);
                 const CrossTile<T> X{bb.rrow + (size_t)q * 2 * n, bb.rcol + (size_t)q * 2 * n, n};
                 const int slot = i < nE ? dm.e1_slot[e1o + i] : dm.t_slot[to + i - nE];
-                const cpx<T> v = apply_A_entry_f<T>(X, s.Mt, p, ce, gam, slot % N, slot / N, false);
+                const cpx<T> v = apply_A_entry_f<T>(X, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
                 if (i < nE) rE[(q0 + q) * stride + i] -= v;
                 else if (Y) cT[(q0 + q) * stride + (i - nE)] = v;
             }
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
         for (int i = g.t(); i < nE; i += g.n()) s.tile[dm.e1_slot[e1o + i]] = xE[q * stride + i];
         g.sync();
         // y_I = A_II^-1 (b_I - A_IE x_E) on the cross: the coupling part first ...
-        cross_coupling<T>(g, s, p, ce, (T)-1);
+        cross_coupling<T>(g, s, p, ce, -ks);
         spec_from_cross<T>(g, s, n, false);
         spec_divide<T>(g, s, n);
         cross_from_spec<T>(g, s, n);
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
         }
         for (int i = g.t(); i < nT; i += g.n()) {
             const int slot = dm.t_slot[to + i];
-            tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+            tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
         }
         g.sync();
     }
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
     cpx<T>* uT = s.vec + 2 * RB * stride;     // [RB][4N]
     load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
-    const T ce = (T)dm.c[e];
+    const T ce = (T)dm.c[e], ks = (T)dm.ks[e];
     T gam[4];
     elem_gam<T>(dm, e, gam);
     for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
@@ -376,14 +377,14 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
         for (int i = g.t(); i < nT; i += g.n()) s.tile[dm.t_slot[to + i]] = uT[q * stride + i];
         g.sync();
         // w_I = A_II^-1 (A_IT u_T) on the cross; r'_E = A_ET u_T - A_EI w_I
-        cross_coupling<T>(g, s, p, ce, (T)1);
+        cross_coupling<T>(g, s, p, ce, ks);
         spec_from_cross<T>(g, s, n, false);
         spec_divide<T>(g, s, n);
         cross_from_spec<T>(g, s, n);
         cross_to_tile<T>(g, s, p, (T)-1);
         for (int i = g.t(); i < nE; i += g.n()) {
             const int slot = dm.e1_slot[e1o + i];
-            rE[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ce, gam, slot % N, slot / N, false);
+            rE[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
         }
         g.sync();
     }
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
     g.sync();
     for (int q0 = 0; q0 < cnt; q0 += QB) {
         const int Q = min(QB, cnt - q0);
-        cross_coupling_b<T>(g, s, bb, p, ce, (T)-1, sE + q0 * stride, uT + q0 * stride, stride, Q);
+        cross_coupling_b<T>(g, s, bb, p, ce, -ks, sE + q0 * stride, uT + q0 * stride, stride, Q);
         for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
             const int q = idx / nn, r = idx % nn, a = r / n, b = r % n;
             cpx<T> v = mk<T>(0, 0);

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(128) k_jump_gather_dots(DevModel dm, const cpx
         double sx = 0, sy = 0;
         const int c = dm.row_c[row], f = dm.row_f[row];
         if (c >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + c]; sx += (double)v.x; sy += (double)v.y; }
-        { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
+        if (f >= 0) { const cpx<T> v = xE[(int64_t)r * dm.nE1_tot + f]; sx -= (double)v.x; sy -= (double)v.y; }
         for (int a = dm.c2_ptr[row]; a < dm.c2_ptr[row + 1]; ++a) {
             const double2 v = x2[(int64_t)r * dm.n_coarse + dm.c2_col[a]];
             sx += dm.c2_w[a] * v.x;
@@ -417,6 +417,103 @@ __global__ void k_norm2_sum(const double* __restrict__ part, int nb, double* __r
     if (lane == 0) out[r] = s;
 }
 
+// ------------------------------------------------------------------ PCG (Poisson mode, FP64)
+// Preconditioned conjugate gradients on F nu = g (Sec. 2.3.3, Poisson paragraph) with every
+// scalar kept on the device, per right-hand side r: sc[8 r + .] = rz, alpha, beta, ||g||^2,
+// done, iterations, ||r||^2.  Dot products in two fixed-order stages (64 partial sums per
+// right-hand side, then one warp adds them), so the iterates are the same on every run.
+
+// part[r][blk] = partial sums of Re(conj(a_r) . b_r)
+__global__ void k_dual_dot(const double2* __restrict__ a, const double2* __restrict__ b, int64_t n,
+                           double* __restrict__ part) {
+    const int r = blockIdx.y;
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 u = a[(int64_t)r * n + i], v = b[(int64_t)r * n + i];
+        s += u.x * v.x + u.y * v.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[(int64_t)r * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// adds the partial sums of one dot product per right-hand side and updates the scalars:
+//   mode 0: ||g||^2 (also ||r||^2; done when g = 0)   mode 1: rz = (r, z)
+//   mode 2: alpha = rz / (d, F d)                        mode 3: ||r||^2, done when <= tol2 ||g||^2
+//   mode 4: beta = (r, z)_new / rz, rz updated
+// alpha_hist / beta_hist [R][maxit]: the coefficients of iteration `it` (Lanczos matrix)
+__global__ void k_pcg_scalar(const double* __restrict__ part, int nb, double* __restrict__ sc, int mode, int it,
+                             double tol2, double* __restrict__ alpha_hist, double* __restrict__ beta_hist, int maxit) {
+    const int r = blockIdx.x, lane = threadIdx.x;
+    double s = 0;
+    for (int i = lane; i < nb; i += 32) s += part[(int64_t)r * nb + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane) return;
+    double* c = sc + 8 * r;
+    const bool done = c[4] != 0.0;
+    switch (mode) {
+        case 0: c[3] = s; c[6] = s; if (s == 0.0) { c[4] = 1.0; c[5] = 0.0; } break;
+        case 1: c[0] = s; break;
+        case 2:
+            c[1] = (done || s == 0.0) ? 0.0 : c[0] / s;
+            if (!done && it < maxit) alpha_hist[(int64_t)r * maxit + it] = c[1];
+            break;
+        case 3:
+            c[6] = s;
+            if (!done && s <= tol2 * c[3]) { c[4] = 1.0; c[5] = it + 1; }
+            break;
+        default:
+            c[2] = (done || c[0] == 0.0) ? 0.0 : s / c[0];
+            if (!done) { c[0] = s; if (it < maxit) beta_hist[(int64_t)r * maxit + it] = c[2]; }
+    }
+}
+
+// nu += alpha d, r -= alpha F d, with the partial sums of ||r||^2 (the same 64 x 256 split as
+// k_dual_dot)
+__global__ void k_pcg_xr(double2* __restrict__ nu, double2* __restrict__ rv, const double2* __restrict__ d,
+                         const double2* __restrict__ Fd, const double* __restrict__ sc, int64_t n,
+                         double* __restrict__ part) {
+    const int r = blockIdx.y;
+    const double al = sc[8 * r + 1];
+    double s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)r * n + i;
+        const double2 dv = d[q], fv = Fd[q];
+        double2 x = nu[q], y = rv[q];
+        x.x += al * dv.x; x.y += al * dv.y;
+        y.x -= al * fv.x; y.y -= al * fv.y;
+        nu[q] = x;
+        rv[q] = y;
+        s += y.x * y.x + y.y * y.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        part[(int64_t)r * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// d = z + beta d
+__global__ void k_pcg_d(double2* __restrict__ d, const double2* __restrict__ z, const double* __restrict__ sc, int64_t n) {
+    const int r = blockIdx.y;
+    const double be = sc[8 * r + 2];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)r * n + i;
+        const double2 zv = z[q], dv = d[q];
+        d[q] = make_double2(zv.x + be * dv.x, zv.y + be * dv.y);
+    }
+}
+
 // ------------------------------------------------------------------ launch wrappers
 template <class B>
 static void iter_tail(const KrylovDev& K, cudaStream_t st, bool skip_first) {
@@ -451,6 +548,20 @@ void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R,
     k_norm2_sum<<<R, 32, 0, st>>>(part, 64, out);
 }
 
+void launch_dual_dot(const double2* a, const double2* b, int64_t n, double* part, int R, cudaStream_t st) {
+    k_dual_dot<<<dim3(kPcgBlocks, R), 256, 0, st>>>(a, b, n, part);
+}
+void launch_pcg_scalar(const double* part, double* sc, int mode, int it, double tol2, double* ah, double* bh,
+                       int maxit, int R, cudaStream_t st) {
+    k_pcg_scalar<<<R, 32, 0, st>>>(part, kPcgBlocks, sc, mode, it, tol2, ah, bh, maxit);
+}
+void launch_pcg_xr(double2* nu, double2* r, const double2* d, const double2* Fd, const double* sc, int64_t n,
+                   double* part, int R, cudaStream_t st) {
+    k_pcg_xr<<<dim3(kPcgBlocks, R), 256, 0, st>>>(nu, r, d, Fd, sc, n, part);
+}
+void launch_pcg_d(double2* d, const double2* z, const double* sc, int64_t n, int R, cudaStream_t st) {
+    k_pcg_d<<<dim3(kPcgBlocks, R), 256, 0, st>>>(d, z, sc, n);
+}
 
 void set_krylov_limits() {
     cudaFuncSetAttribute(k_cgs_first<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4096 * (int)sizeof(double2));

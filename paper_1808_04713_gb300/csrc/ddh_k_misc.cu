@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
     __syncthreads();
     double gam[4];
     elem_gam<double>(dm, e, gam);
-    const double ce = dm.c[e];
+    const double ce = dm.c[e], ks = dm.ks[e];
     for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
         const int c = idx % N, bb = idx / N;
         int cd[6];
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
         if (bb == 0 && gam[3] != 0.0) rob += gam[3] * S1[a + N * 0];
         v.x -= rob.y;
         v.y += rob.x;
+        v = ks * v;                      // element coefficient (1 for Helmholtz: exact)
         double2 o = make_double2(-v.x, -v.y);
         if (b) { const double2 bv = b[base + idx]; o.x += bv.x; o.y += bv.y; }
         out[base + idx] = o;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(128) k_grad_elem(DevModel dm, const double2* _
         for (int i = g.t(); i < N * N; i += g.n()) { const double2 v = ut[base + i]; s.tile[i] = mk<double>(v.x, v.y); }
         g.sync();
         for (int idx = g.t(); idx < N * N; idx += g.n()) {
-            const cpx<double> au = apply_A_entry<double>(s.tile, s.Mt, p, ce, gam, idx % N, idx / N, false, true);
+            const cpx<double> au = apply_A_entry<double>(s.tile, s.Mt, p, 1.0, ce, gam, idx % N, idx / N, false, true);
             const double2 l = lt[base + idx];
             acc += l.x * au.x - l.y * au.y;          // Re(l * au)
         }

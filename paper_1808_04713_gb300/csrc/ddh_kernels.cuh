@@ -149,10 +149,12 @@ __device__ __forceinline__ T kt(int a, int c) {
     return a == c ? (T)1 : (T)0;
 }
 
-// (A Phi)[a][b] with Phi read through `tile(c, d)`; gam[s] = imaginary part of gamma_eff on
-// side s (0 if none).
+// (A Phi)[a][b] with Phi read through `tile(c, d)`, A = ks (K (x) M + M (x) K + ce M (x) M + Robin);
+// gam[s] = imaginary part of gamma_eff on side s (0 if none), ks the element's coefficient
+// (rho of the Poisson mode, where ce = 0 and there is no Robin term; 1 for Helmholtz, where
+// the product by ks is exact and leaves every bit as without it).
 template <class T, class F>
-__device__ inline cpx<T> apply_A_entry_f(const F& tile, const T* Mt, int p, T ce, const T* gam,
+__device__ inline cpx<T> apply_A_entry_f(const F& tile, const T* Mt, int p, T ks, T ce, const T* gam,
                                           int a, int b, bool stiff_only, bool no_stiff = false) {
     const int N = p + 1;
     int ca[6], cb[6];
@@ -180,7 +182,7 @@ __device__ inline cpx<T> apply_A_entry_f(const F& tile, const T* Mt, int p, T ce
         acc.y += rob.x;
     }
     (void)N;
-    return acc;
+    return ks * acc;
 }
 
 template <class T>
@@ -192,14 +194,15 @@ struct TileRef {
 
 // (A Phi)[a][b] from the tile (N x N, column-major)
 template <class T>
-__device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ce, const T* gam,
+__device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ks, T ce, const T* gam,
                                         int a, int b, bool stiff_only, bool no_stiff = false) {
-    return apply_A_entry_f<T>(TileRef<T>{tile, p + 1}, Mt, p, ce, gam, a, b, stiff_only, no_stiff);
+    return apply_A_entry_f<T>(TileRef<T>{tile, p + 1}, Mt, p, ks, ce, gam, a, b, stiff_only, no_stiff);
 }
 
 // Interior coupling of the frame values: coupling = Mt_BV X + Y Mt_VB with
 // X = Phi_VB (I + c M_b) + c Phi_VV Mt_VB (2 x n),  Y = (I + c M_b) Phi_BV (n x 2).
-// Writes sign * coupling into rrow (interior rows 0,1) and rcol (interior cols 0,1).
+// Writes sign * coupling into rrow (interior rows 0,1) and rcol (interior cols 0,1); callers
+// fold the element coefficient ks into sign.
 template <class T, class G>
 __device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T ce, T sign) {
     const int N = p + 1, n = p - 1;

@@ -184,6 +184,15 @@ void launch_axpby(const double2* x, double a, const double2* y, double b, double
 void launch_scale_f32(const double2* x, double a, float2* out, int64_t n, cudaStream_t st);
 // out[r] = ||x_r||^2 (deterministic; part: R x 64 doubles of scratch)
 void launch_norm2(const double2* x, int64_t n, double* out, double* part, int R, cudaStream_t st);
+// PCG of the Poisson mode: partial sums per right-hand side (kPcgBlocks of them), scalar update
+// (modes of k_pcg_scalar), nu/r update with ||r||^2 partial sums, and d = z + beta d
+constexpr int kPcgBlocks = 64;
+void launch_dual_dot(const double2* a, const double2* b, int64_t n, double* part, int R, cudaStream_t st);
+void launch_pcg_scalar(const double* part, double* sc, int mode, int it, double tol2, double* ah, double* bh,
+                       int maxit, int R, cudaStream_t st);
+void launch_pcg_xr(double2* nu, double2* r, const double2* d, const double2* Fd, const double* sc, int64_t n,
+                   double* part, int R, cudaStream_t st);
+void launch_pcg_d(double2* d, const double2* z, const double* sc, int64_t n, int R, cudaStream_t st);
 void launch_conf_scatter(const DevModel& dm, const double2* x, double2* out, int R, cudaStream_t st);
 void launch_conf_gather_vec(const DevModel& dm, const double2* x, double2* out, double sign, int R, cudaStream_t st);
 void launch_inject(const DevModel& dm, const double2* rc, double2* b, int R, cudaStream_t st);

@@ -174,9 +174,11 @@ int locate_point(const Model& m, double x, double y, double& u1, double& u2) {
 
 void set_coefficients(Model& m, double k, const double* eps) {
     m.k = k;
+    m.dirichlet = false;
     for (size_t e = 0; e < m.el.size(); ++e) {
         Elem& E = m.el[e];
         E.eps = eps[e];
+        E.rho = 1.0;
         E.c = -k * k * E.eps * (0.5 * E.h) * (0.5 * E.h);
         for (int s = 0; s < 4; ++s) {
             const auto& se = m.side_edge[4 * e + s];
@@ -184,6 +186,26 @@ void set_coefficients(Model& m, double k, const double* eps) {
         }
     }
     set_robin(m, false);
+}
+
+bool set_poisson(Model& m, const double* rho, std::string& err) {
+    for (const auto& ed : m.edges)
+        if (ed.kind == 2) { err = "Poisson mode needs a conforming mesh (no hanging edges)"; return false; }
+    for (size_t e = 0; e < m.el.size(); ++e)
+        if (!(rho[e] > 0.0) || !std::isfinite(rho[e])) { err = "rho must be positive and finite"; return false; }
+    m.k = 0.0;
+    m.dirichlet = true;
+    for (size_t e = 0; e < m.el.size(); ++e) {
+        Elem& E = m.el[e];
+        E.eps = 1.0;
+        E.rho = rho[e];
+        E.c = 0.0;
+        for (int s = 0; s < 4; ++s) {
+            E.boundary[s] = m.edges[m.side_edge[4 * e + s].first].kind == 0;
+            E.gam[s] = cd(0.0, 0.0);
+        }
+    }
+    return true;
 }
 
 int set_robin(Model& m, bool modified) {
@@ -256,6 +278,12 @@ struct Slaver {
 
     explicit Slaver(Model& mm, int l) : m(mm), lcut(l) {}
 
+    bool on_dirichlet(int64_t X, int64_t Y) const {
+        if (!m.dirichlet) return false;
+        const int64_t top = (int64_t)m.base_n << m.maxlev;
+        return X == 0 || Y == 0 || X == top || Y == top;
+    }
+
     const std::vector<double>& Lt(int n, double a, double b) {
         auto key = std::make_tuple(n, a, b);
         auto it = Lcache.find(key);
@@ -279,6 +307,8 @@ struct Slaver {
         auto vt = vert.find(pt_key(X, Y));
         if (vt != vert.end()) {
             out.push_back({vt->second, 1.0});
+        } else if (on_dirichlet(X, Y)) {
+            // a vertex on a Dirichlet boundary is discarded: zero, no coarse unknown
         } else {
             const int sides[2] = {a == 0 ? 1 : 0, b == 0 ? 3 : 2};
             bool done = false;
@@ -322,7 +352,11 @@ struct Slaver {
     }
 };
 
-int edge_top(const MasterEdge& ed, int lcut) { return ed.kind == 2 ? ed.degree : std::min(lcut, ed.degree); }
+// highest primal moment of an edge (a Dirichlet side keeps none: its moments 2..l are discarded)
+int edge_top(const Model& m, const MasterEdge& ed, int lcut) {
+    if (ed.kind == 0 && m.dirichlet) return 1;
+    return ed.kind == 2 ? ed.degree : std::min(lcut, ed.degree);
+}
 
 // Number the coarse dofs and compute the slot expressions for constraint count lcut.
 // Fills, per element, the list of type-1 edge slots and the expression of every other
@@ -354,7 +388,7 @@ int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* X2, std::vector<in
         for (int b = 0; b < 2; ++b)
             for (int a = 0; a < 2; ++a) {
                 const uint64_t key = pt_key(xs[a], ys[b]);
-                if (hanging.count(key) || sl.vert.count(key)) continue;
+                if (hanging.count(key) || sl.vert.count(key) || sl.on_dirichlet(xs[a], ys[b])) continue;
                 sl.vert[key] = nd++;
                 if (X2) X2->push_back(2 * xs[a]);
                 if (Y2) Y2->push_back(2 * ys[b]);
@@ -365,7 +399,7 @@ int number_coarse(Model& m, Slaver& sl, std::vector<int64_t>* X2, std::vector<in
     for (size_t ei = 0; ei < m.edges.size(); ++ei) {
         const MasterEdge& ed = m.edges[ei];
         sl.edof[ei].assign(ed.degree + 1, -1);
-        for (int k = 2; k <= edge_top(ed, sl.lcut); ++k) {
+        for (int k = 2; k <= edge_top(m, ed, sl.lcut); ++k) {
             sl.edof[ei][k] = nd++;
             if (X2) X2->push_back(ed.X2);
             if (Y2) Y2->push_back(ed.Y2);
@@ -405,6 +439,8 @@ bool classify(Model& m, int l, std::string& err) {
                     const int slot = side_slot(El.p, s, mm);
                     if (ed.kind == 2 && se.second == 1) {
                         push_T(slot, {{sl.edof[se.first][mm], 1.0}});
+                    } else if (mm <= l && ed.kind == 0 && m.dirichlet) {
+                        // discarded moment of a Dirichlet side: in neither slot list (zero)
                     } else if (mm <= l) {
                         if (ed.kind == 2) push_T(slot, sl.slaved(se.first, e, s, mm));
                         else push_T(slot, {{sl.edof[se.first][mm], 1.0}});
@@ -427,7 +463,21 @@ bool classify(Model& m, int l, std::string& err) {
         auto e1_index = [&](int e, int s, int mm) { return e1_first[4 * e + s] + (mm - (l + 1)); };
         for (size_t ei = 0; ei < m.edges.size(); ++ei) {
             const MasterEdge& ed = m.edges[ei];
-            if (ed.kind == 0 || ed.degree <= l) continue;
+            if (ed.degree <= l) continue;
+            if (ed.kind == 0) {
+                // Dirichlet side: single-sided rows t[m] = 0 for m > l on the element's slots
+                if (!m.dirichlet) continue;
+                for (int mm = l + 1; mm <= ed.degree; ++mm) {
+                    const int r = (int)m.row_f.size();
+                    const int ci = e1_index(ed.elem, ed.side, mm);
+                    m.row_c.push_back(ci);
+                    m.row_f.push_back(-1);
+                    m.e1_row[ci] = r; m.e1_sign[ci] = 1.0;
+                    m.row_hblock.push_back(-1);
+                    m.c2_ptr.push_back((int32_t)m.c2_col.size());
+                }
+                continue;
+            }
             const int r0 = (int)m.row_f.size();
             for (auto& sub : ed.subs) {
                 const int n = std::max(m.el[ed.elem].p, m.el[sub.elem].p);
@@ -518,6 +568,7 @@ bool classify(Model& m, int l, std::string& err) {
                 for (int mm = 2; mm <= std::min(El.p, ed.degree); ++mm) {
                     const int slot = side_slot(El.p, s, mm);
                     if (ed.kind == 2 && se.second == 2) ex[slot] = sc.slaved(se.first, e, s, mm);
+                    else if (ed.kind == 0 && m.dirichlet) ex[slot].clear();     // zero Dirichlet data
                     else ex[slot] = {{sc.edof[se.first][mm], 1.0}};
                 }
             }

@@ -58,6 +58,8 @@ _SIGS = {
     "ddh_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
     "ddh_set_mesh": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
     "ddh_set_coefficients": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
+    "ddh_set_poisson": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ddh_pcg_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ddh_factor": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
     "ddh_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
     "ddh_elem_offsets": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -160,6 +162,17 @@ class DDH:
     def set_coefficients(self, k: float, eps):
         e = np.ascontiguousarray(eps, dtype=np.float64)
         self._check(self.lib.ddh_set_coefficients(self.h, float(k), e.ctypes.data))
+
+    def set_poisson(self, rho):
+        """Poisson mode: -div(rho grad phi) = f, zero Dirichlet data, rho per element."""
+        r = np.ascontiguousarray(rho, dtype=np.float64)
+        self._check(self.lib.ddh_set_poisson(self.h, r.ctypes.data))
+
+    def pcg_spectrum(self, r: int = 0):
+        """(lambda_min, lambda_max) Lanczos estimates of P^-1 F from the last Poisson solve."""
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.ddh_pcg_spectrum(self.h, int(r), C.byref(lo), C.byref(hi)))
+        return lo.value, hi.value
 
     def factor(self, **opts) -> int:
         o = default_options(**opts)

@@ -56,3 +56,25 @@ def test_host_factor_l_override(ddh, l):
     assert l_used == l
     assert (sizes["n_dual"], sizes["n_coarse"]) == (S.nd, S.n2)
     assert secs[2] <= 1e-12
+
+
+@pytest.mark.parametrize("n,p,l", [(1, 3, 1), (1, 4, 3), (2, 3, 2), (2, 8, 2), (1, 16, 4)])
+def test_host_factor_poisson_split_matches_oracle(ddh, n, p, l):
+    """Poisson mode (k = 0, rho_ij = 10^((i - j)/4), zero Dirichlet data): the library's
+    Dirichlet split (discarded boundary vertices and moments 2..l of boundary sides, single-sided
+    dual rows above l) has the oracle's sizes, and its factor passes the self-checks."""
+    from oracle import poisson as P
+    m = 2 ** n
+    leaves = P.uniform_leaves(m)
+    rho = P.rho_table2(m)
+    sizes, secs, l_used = ddh.host_factor(m, leaves, np.full(m * m, p), 0.0, rho, l_override=l)
+    D = P.build(n, p, l)
+    interior = m * m * (p - 1) ** 2
+    assert l_used == l
+    assert sizes["n_dual"] == D.nd
+    assert sizes["n_coarse"] == D.n2
+    assert sizes["n_e1"] + interior == D.n1
+    # conforming unknowns: interior vertices, interior edge bubbles, element interiors
+    assert sizes["n_conforming"] == (m - 1) ** 2 + 2 * m * (m - 1) * (p - 1) + interior
+    assert secs[2] <= 1e-12, secs
+    assert secs[3] <= 1e-10, secs

@@ -76,3 +76,73 @@ def test_planted_mistakes_move_the_printed_values():
     s2.CWC = C1 @ W @ C1.T
     s2.mid = C1 @ W.T @ A11 @ W @ C1.T
     assert abs(s2.eigs()[1] - 1.26) > 0.05
+
+
+def _volume_load(dd_mesh_n, p, f):
+    """b_N of a volume load f on the 2^n x 2^n squares of [0, 1]^2 (Gauss-Legendre quadrature)."""
+    from oracle import element as el
+    m = 2 ** dd_mesh_n
+    h = 1.0 / m
+    out = []
+    for e in range(m * m):
+        i, j = e % m, e // m
+        out.append(el.volume_load_N(p, f, i * h, j * h, h))
+    return np.concatenate(out).real
+
+
+def _field(phi_N, n, p, x, y):
+    from oracle import element as el
+    m = 2 ** n
+    h = 1.0 / m
+    N2 = (p + 1) ** 2
+    i = np.minimum((x / h).astype(int), m - 1)
+    j = np.minimum((y / h).astype(int), m - 1)
+    out = np.empty(x.shape)
+    for q in range(x.size):
+        e = i[q] + m * j[q]
+        u1 = 2 * (x[q] - i[q] * h) / h - 1
+        u2 = 2 * (y[q] - j[q] * h) / h - 1
+        out[q] = el.evaluate_N(p, phi_N[e * N2:(e + 1) * N2], np.array([u1]), np.array([u2])).real[0]
+    return out
+
+
+def test_recovered_field_converges_to_the_manufactured_solution():
+    """rho = 1, f = 2 pi^2 sin(pi x) sin(pi y) on [0, 1]^2 with zero Dirichlet data: the exact
+    solution is sin(pi x) sin(pi y), and the DD field converges to it spectrally in p."""
+    f = lambda x, y: 2 * np.pi ** 2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+    rng = np.random.default_rng(3)
+    x, y = rng.uniform(0, 1, 40), rng.uniform(0, 1, 40)
+    ex = np.sin(np.pi * x) * np.sin(np.pi * y)
+    errs = []
+    for p in (4, 6, 8):
+        s = P.Solver(P.build(1, p, 2, rho=np.ones(4)))
+        phi, _ = s.solve(_volume_load(1, p, f))
+        errs.append(np.max(np.abs(_field(phi, 1, p, x, y) - ex)))
+    assert all(a / b > 20 for a, b in zip(errs[:-1], errs[1:])), errs
+    assert errs[-1] < 1e-5, errs
+
+
+def test_dual_solution_equals_the_all_primal_split():
+    """Piecewise rho of Table 2: the field recovered from the PCG dual solution (l = 1) equals
+    the one of the split with every edge moment primal (l = p: no dual rows, one direct solve)."""
+    p, n = 5, 1
+    b = np.random.default_rng(11).uniform(0, 1, (2 ** n) ** 2 * (p + 1) ** 2)
+    phi1, its = P.Solver(P.build(n, p, 1)).solve(b, tol=1e-13)
+    phip, _ = P.Solver(P.build(n, p, p)).solve(b)
+    assert its > 1
+    assert np.max(np.abs(phi1 - phip)) <= 1e-10 * np.max(np.abs(phip))
+
+
+@pytest.mark.parametrize("n,p,l", [(1, 16, 1), (2, 4, 1), (1, 8, 2)])
+def test_lanczos_ritz_values_bracket_by_the_dense_spectrum(n, p, l):
+    """The Lanczos matrix of the PCG run has Ritz values of P^-1 F: its extremes lie inside the
+    dense spectrum, and after the run they reach lambda_max (relative 1e-6 in these cases, where
+    the largest eigenvalue is well separated)."""
+    s = P.Solver(P.build(n, p, l))
+    lo, hi = s.eigs()
+    b = np.random.default_rng(7).uniform(0.0, 1.0, size=s.dd.B.shape[0])
+    c = []
+    s.pcg(s.rhs(b), coeffs=c)
+    llo, lhi = P.lanczos_extremes(c)
+    assert lo - 1e-9 <= llo <= lhi <= hi + 1e-9
+    assert abs(lhi - hi) <= 1e-6 * hi, (lhi, hi)
