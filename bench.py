@@ -10,7 +10,10 @@ relative residual 1e-10.  Beside it, on the same workload and tolerance:
   plain_fp64    the plain method (everything complex128), same 8 right-hand sides;
   disk_hanging  the batching workload (4144 leaves with hanging nodes, p ~ U{8..24}, 64 plane
                 waves), both forms at 64 right-hand sides;
-  plane_16x16   the plain FP64 GPU baseline workload (16 x 16, p = 16, k = 100, one plane wave).
+  plane_16x16   the plain FP64 GPU baseline workload (16 x 16, p = 16, k = 100, one plane wave);
+  poisson_table2  the Poisson test problem of Sec. 3.1 (PCG with the scaled Dirichlet
+                preconditioner) on three Table 2 cases, with iterations and the Lanczos lambda_max
+                beside the printed values.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -255,6 +258,44 @@ def _form(name, prec, local, stream, flush, warmup, steps, R=None, **opts):
     return w, s, b, u, out
 
 
+# the paper's Table 2 (Sec. 3.1): printed PCG iterations and lambda_max of P^-1 F for the Poisson
+# cases timed here (p, N, l) -> (iterations, lambda_max)
+TABLE2_PRINTED = {(3, 64, 2): (7, 1.17), (8, 16, 2): (11, 1.70), (16, 4, 1): (11, 5.84)}
+
+
+def _poisson_form(p, N, l, R, local, stream, flush, warmup, steps):
+    """Solves/s of the Poisson mode (PCG, FP64) on one Table 2 case, its iterations and the
+    Lanczos lambda_max beside the printed values."""
+    import torch
+    import workloads as W
+    from paper_1808_04713_gb300 import ddh
+    w = W.poisson_table2(p, N, l, n_rhs=R)
+    s = ddh.DDH(local, stream=stream)
+    s.set_mesh(w.base_n, w.leaves, w.p)
+    s.set_poisson(w.rho)
+    s.factor(tol=TOL, l_override=l, maxit=200)
+    with torch.cuda.stream(stream):
+        b = torch.tensor(w.loads.astype("complex128"), device=f"cuda:{local}")
+        u = torch.empty_like(b)
+    for _ in range(warmup):
+        s.solve(b, tol=TOL, out=u, stats=False)
+    l0 = s.kernel_launches()
+    ts = _time_solves(s, b, u, stream, flush, steps)
+    launches = (s.kernel_launches() - l0) // max(1, steps)
+    _, st = s.solve(b, tol=TOL, out=u)
+    lo, hi = s.pcg_spectrum(0)
+    its_p, lmax_p = TABLE2_PRINTED.get((p, N, l), (None, None))
+    out = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT, "rhs": R,
+           "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3), "steps": len(ts),
+           "iterations": max(x.iterations for x in st), "iterations_printed": its_p,
+           "lanczos_lambda_max": round(hi, 4), "lambda_max_printed": lmax_p,
+           "lanczos_lambda_min": round(lo, 6),
+           "max_primal_residual": float(max(x.primal_residual for x in st)),
+           "launches_per_step": int(launches), "n_dual": s.info().n_dual}
+    s.close()
+    return out
+
+
 def _cpu_baseline(n_elem_full: int, iters_full: int) -> dict:
     """The oracle, as it stands, on the 16 x 16 corner of the workload (same element operators),
     timed with one BLAS thread and with all host cores; rates scaled to the full workload."""
@@ -392,6 +433,11 @@ def run_ours(args):
         s2.close()
         del b2, u2
         extras["plane_16x16"] = c2
+        # ---- the Poisson test problem of Sec. 3.1 (PCG, scaled Dirichlet preconditioner)
+        pt = {}
+        for (pp, NN, ll), R_ in (((3, 64, 2), 1), ((8, 16, 2), 1), ((16, 4, 1), 1), ((8, 16, 2), 8)):
+            pt[f"p{pp}_N{NN}_l{ll}_R{R_}"] = _poisson_form(pp, NN, ll, R_, local, stream, flush, 3, max(3, args.steps))
+        extras["poisson_table2"] = pt
 
     out = None
     if rank == 0:

@@ -21,6 +21,9 @@ The five named workloads are:
 * ``lens_48``      -- 48x48 squares, p=16, k=200, eps ~ U[1,4] (seed 5), theta=0,
   32 observation points on x=0.9, y in [0.4, 0.6]; 16 finite-difference
   parameter indices (seed 55).
+
+``poisson_table2(p, N, l)`` gives the Poisson test problem of the paper's Table 2 (rho_ij =
+10^((i-j)/4) on sqrt(N) x sqrt(N) squares, zero Dirichlet data, loads ~ U(0,1), seed 7).
 """
 from __future__ import annotations
 
@@ -148,6 +151,29 @@ def corner_block(w: Workload, n: int, n_rhs: int = 1) -> Workload:
     scale = n / w.base_n
     return Workload(f"{w.name}_corner{n}", n, lv.copy(), w.p[sel].copy(), w.eps[sel].copy(), w.k * scale,
                     w.thetas[:n_rhs].copy())
+
+
+@dataclass
+class PoissonWorkload:
+    """The Poisson test problem of Sec. 3.1 (Table 2): N = 4^n squares of degree p on the unit
+    square, rho_ij = 10^((i - j)/4) on element (i, j), zero Dirichlet data, l primal moments per
+    edge, and load vectors with entries ~ U(0, 1) (seeded) in the N basis."""
+    name: str
+    base_n: int
+    leaves: np.ndarray
+    p: np.ndarray
+    rho: np.ndarray
+    l: int
+    loads: np.ndarray           # float64 [R, n_local]
+
+
+def poisson_table2(p: int, N: int, l: int, n_rhs: int = 1, seed: int = 7) -> PoissonWorkload:
+    m = int(round(math.sqrt(N)))
+    leaves = uniform_leaves(m)
+    rho = 10.0 ** ((leaves[:, 1] - leaves[:, 2]) / 4.0)
+    n_local = m * m * (p + 1) ** 2
+    loads = np.random.default_rng(seed).uniform(0.0, 1.0, size=(n_rhs, n_local))
+    return PoissonWorkload(f"poisson_p{p}_N{N}_l{l}", m, leaves, np.full(m * m, p, np.int32), rho, l, loads)
 
 
 WORKLOADS = {
