@@ -32,7 +32,15 @@ def _rows():
     return out
 
 
-ROWS = _rows()
+def _n_dual(p, N, l):
+    """Dual rows of the split: moments l+1..p on every edge, interior and boundary alike."""
+    m = int(round(np.sqrt(N)))
+    return 2 * m * (m + 1) * (p - l)
+
+
+# the oracle's dense eigensolve of P^-1 F grows with the cube of the dual size: the CPU suite
+# takes every listed case up to 450 dual rows (34 of the 72; the GPU tests take the rest)
+ROWS = [r for r in _rows() if _n_dual(*r[:3]) <= 450]
 
 
 @pytest.mark.parametrize("p,N,l,its,lmax", ROWS, ids=[f"p{r[0]}-N{r[1]}-l{r[2]}" for r in ROWS])
@@ -53,6 +61,11 @@ def test_constant_rho_removes_the_dependence_on_the_jumps():
     s = P.Solver(P.build(2, 4, 2, rho=np.ones(16)))
     lo, hi = s.eigs()
     assert abs(lo - 1.0) <= 1e-3 and 1.0 < hi < 2.0
+
+
+def test_dual_size_formula_matches_the_split():
+    for p, N, l in ((3, 4, 1), (4, 16, 2), (8, 64, 3)):
+        assert P.build(int(round(np.log(N) / np.log(4))), p, l).nd == _n_dual(p, N, l)
 
 
 def test_planted_mistakes_move_the_printed_values():
