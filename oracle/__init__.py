@@ -20,6 +20,9 @@ Modules
   poisson      Section 3.1: the Poisson test with zero Dirichlet data and rho jumps, the
                Dirichlet preconditioner with diagonal scaling, PCG and the spectrum of
                P^-1 F (pinned to the printed Table 2).
+  dirichlet    Section 3.2: the Helmholtz test with point-source Dirichlet data (lifting of
+               the boundary trace, zero-data dual-primal solve, FGMRES), pinned to the exact
+               solution and to the printed Table 3.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``; see the
 docstrings for the pin of each part.

@@ -35,7 +35,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import legendre as lg
-from .element import stiffness_matrix_N, to_tilde
+from .element import mass_matrix_N, stiffness_matrix_N, to_tilde
 from .mesh import build_mesh, side_corners, side_slot
 
 
@@ -64,10 +64,14 @@ class PoissonDD:
     t1_offset: np.ndarray
     t1_edge_mask: list
     B: sp.csr_matrix          # block-diagonal B (x) B: phi~ = B phi (N -> interpolatory basis)
+    A11_lap: sp.csr_matrix    # stiffness part of A11 (equal to A11 when k = 0)
 
 
-def build(n: int, p: int, l: int, rho: np.ndarray | None = None) -> PoissonDD:
-    """The dual-primal pieces for 2^n x 2^n squares of degree p with l primal moments per edge."""
+def build(n: int, p: int, l: int, rho: np.ndarray | None = None, k: float = 0.0) -> PoissonDD:
+    """The dual-primal pieces for 2^n x 2^n squares of degree p with l primal moments per edge.
+    With k > 0 the element operators are those of the Helmholtz problem with the same zero
+    Dirichlet constraints (alpha = I, beta = -k^2 on the unit square: S + c_e M, c_e = -k^2 (h/2)^2;
+    Sec. 3.2); A11_lap then holds the stiffness part, which the Dirichlet preconditioner uses."""
     m = 2 ** n
     E = m * m
     leaves = uniform_leaves(m)
@@ -139,27 +143,37 @@ def build(n: int, p: int, l: int, rho: np.ndarray | None = None) -> PoissonDD:
     C1 = sp.csr_matrix((dv, (dr, dc)), shape=(r, n1))
     # ---- element operators rho_e (K (x) M + M (x) K) on the interpolatory basis
     S = to_tilde(p, stiffness_matrix_N(p))
-    A = sp.block_diag([rho[e] * S for e in range(E)], format="csr")
+    if k > 0.0:
+        c = -(k * 0.5 / m) ** 2
+        Ae = S + c * to_tilde(p, mass_matrix_N(p))
+        A = sp.block_diag([rho[e] * Ae for e in range(E)], format="csr")
+    else:
+        A = sp.block_diag([rho[e] * S for e in range(E)], format="csr")
     Ah = (Z.T @ A @ Z).tocsr()
     Bl = lg.B_matrix(p)
     B = sp.block_diag([np.kron(Bl, Bl)] * E, format="csr")
+    Z1 = Z[:, :n1]
+    A11_lap = (Z1.T @ sp.block_diag([rho[e] * S for e in range(E)], format="csr") @ Z1).tocsr()
     return PoissonDD(n1, n2, r, Ah[:n1, :n1].tocsr(), Ah[:n1, n1:].tocsr(), Ah[n1:, n1:].tocsr(), C1, Z,
-                     t1_offset, t1_edge_mask, B)
+                     t1_offset, t1_edge_mask, B, A11_lap)
 
 
 class Solver:
-    """F, the scaled Dirichlet preconditioner and PCG for one PoissonDD."""
+    """F, the Dirichlet preconditioner and PCG for one PoissonDD.  scaled = True: the diagonally
+    scaled Dirichlet preconditioner of the Poisson test (W^(j) with diag(A_ee)^-1, on A11);
+    scaled = False: the unscaled Dirichlet preconditioner on the stiffness part of A11 (W^(j) =
+    [I; -A_ii^-1 A_ei^T], Sec. 2.3.3), used for the Helmholtz problem."""
 
-    def __init__(self, dd: PoissonDD):
+    def __init__(self, dd: PoissonDD, scaled: bool = True):
         self.dd = dd
         self.lu11 = spla.splu(dd.A11.tocsc())
         K = dd.A22 - dd.A12.T @ self.lu11.solve(dd.A12.toarray())
         self.K = np.asarray(K)
         self.Klu = sla.lu_factor(self.K) if dd.n2 else None
-        # W1 with diagonal scaling, element by element (edge unknowns e, interior unknowns i)
+        # W1 element by element (edge unknowns e, interior unknowns i)
         n1 = dd.n1
         W = np.zeros((n1, n1))
-        A11 = dd.A11.toarray()
+        A11 = (dd.A11 if scaled else dd.A11_lap).toarray().real
         t = dd.t1_offset
         for e in range(len(t) - 1):
             idx = np.arange(t[e], t[e + 1])
@@ -168,7 +182,7 @@ class Solver:
             Aee = A11[np.ix_(ie, ie)]
             Aei = A11[np.ix_(ie, ii)]
             Aii = A11[np.ix_(ii, ii)]
-            Dinv = np.diag(1.0 / np.diag(Aee))
+            Dinv = np.diag(1.0 / np.diag(Aee)) if scaled else np.eye(len(ie))
             W[np.ix_(ie, ie)] = Dinv
             W[np.ix_(ii, ie)] = -np.linalg.solve(Aii, Aei.T) @ Dinv
         C1 = dd.C1.toarray()

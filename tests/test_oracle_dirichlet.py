@@ -1,0 +1,105 @@
+"""Pins of the oracle's Helmholtz test with Dirichlet data (Sec. 3.2, Table 3).
+
+* the side rule: the bubble coefficients of a polynomial trace of degree p come back exactly
+  (the L^2 projection onto degree p is the identity there);
+* the field converges spectrally to the point-source solution -(i/4) H0^(2)(k |x - x_c|) that
+  the Dirichlet data come from;
+* the dual solution equals the all-primal split (l = p: no dual rows);
+* the printed iteration counts of Table 3 (within one, or 3 % on runs beyond 33 iterations:
+  FGMRES here, left-preconditioned PGMRES in the paper) on the 56 cells the oracle takes in
+  seconds (p <= 16 and N <= 16, and p = 8, N = 64, k = 11), and at least 95 iterations where
+  the table prints a dash (more than 100);
+* the table's bold cells are exactly those where the dispersion criterion (eq.
+  dispersion_criterion, l > (kh + (kh)^(1/3) - 1)/2 with h the element size on (-1,1)^2) holds.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dirichlet as D
+from oracle import element as el
+from oracle import legendre as lg
+
+_FIX = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_helmholtz.txt")
+
+
+def _rows():
+    out = []
+    for line in open(_FIX):
+        s = line.split("#", 1)[0].split()
+        if len(s) == 6:
+            out.append(tuple(int(v) for v in s))
+    return out
+
+
+ROWS = _rows()
+
+
+def _field_error(phi, n, p, data, pts):
+    m = 2 ** n
+    h = 1.0 / m
+    N2 = (p + 1) ** 2
+    err = 0.0
+    for x, y in pts:
+        i, j = min(int(x / h), m - 1), min(int(y / h), m - 1)
+        e = i + m * j
+        v = el.evaluate_N(p, phi[e * N2:(e + 1) * N2], np.array([2 * (x - i * h) / h - 1]),
+                          np.array([2 * (y - j * h) / h - 1]))[0]
+        err = max(err, abs(v - data(x, y)))
+    return err
+
+
+def test_side_rule_is_exact_on_polynomials():
+    p = 9
+    tau = np.random.default_rng(1).standard_normal(p + 1) + 1j * np.random.default_rng(2).standard_normal(p + 1)
+    f = lambda t: tau @ lg.N_basis(p, t)
+    assert np.allclose(D.side_bubbles(p, f), tau, atol=1e-13)
+
+
+def test_field_converges_to_the_point_source():
+    k, data = D.table3_problem(11.0)
+    pts = np.random.default_rng(3).uniform(0.0, 1.0, size=(40, 2))
+    errs = []
+    for p, l in ((8, 3), (12, 4), (16, 5)):
+        s = D.Solver(1, p, l, k)
+        g = D.lifting(1, p, data)
+        phi, _, _ = s.solve(np.zeros_like(g), g, tol=1e-12)
+        errs.append(_field_error(phi, 1, p, data, pts))
+    assert all(a / b > 50 for a, b in zip(errs[:-1], errs[1:])), errs
+    assert errs[-1] < 1e-6, errs
+
+
+def test_dual_solution_equals_the_all_primal_split():
+    k, data = D.table3_problem(5.0)
+    n, p = 1, 6
+    g = D.lifting(n, p, data)
+    b = np.random.default_rng(4).uniform(0.0, 1.0, size=g.shape)
+    phi1, its, _ = D.Solver(n, p, 1, k).solve(b, g, tol=1e-13)
+    phip, _, _ = D.Solver(n, p, p, k).solve(b, g)
+    assert its > 1
+    assert np.max(np.abs(phi1 - phip)) <= 1e-10 * np.max(np.abs(phip))
+
+
+ORACLE_ROWS = [r for r in ROWS if r[0] <= 16 and r[1] <= 16] + [r for r in ROWS if r[:3] == (8, 64, 11)]
+
+
+@pytest.mark.parametrize("p,N,k,l,its,bold", ORACLE_ROWS,
+                         ids=[f"p{r[0]}-N{r[1]}-k{r[2]}-l{r[3]}" for r in ORACLE_ROWS])
+def test_table3_iterations(p, N, k, l, its, bold):
+    n = int(round(np.log(N) / np.log(4)))
+    kk, data = D.table3_problem(float(k))
+    g = D.lifting(n, p, data)
+    _, got, _ = D.Solver(n, p, l, kk).solve(np.zeros_like(g), g, tol=1e-10, maxit=110)
+    if its < 0:
+        assert got >= 95, got
+    else:
+        # left (paper) and right (here) preconditioning drift apart over long runs: one
+        # iteration, or 3 % beyond 33 (p = 16, N = 4, k = 21, l = 2: 91 here, 93 printed)
+        assert abs(got - its) <= max(1.0, 0.03 * its), (got, its)
+
+
+def test_bold_cells_are_the_dispersion_criterion():
+    for p, N, k, l, its, bold in ROWS:
+        kh = k * 2.0 / np.sqrt(N)
+        assert (l > 0.5 * (kh + np.cbrt(kh) - 1.0)) == bool(bold), (p, N, k, l)
