@@ -151,6 +151,9 @@ typedef struct {
                               a programmatic dependent launch of the one before it (it waits for that
                               level before touching memory; only CTA scheduling overlaps; same result
                               bits; measured slower); 0 (default) = plain stream order */
+    int32_t dual_stop;     /* 1: a plain FP64 solve stops when the dual residual ||g - F nu|| / ||g|| of
+                              its FGMRES reaches tol (the paper's criterion, Sec. 3); 0 (default) =
+                              it continues with warm restarts until the FP64 primal residual does */
 } ddh_options;
 
 typedef struct {
@@ -218,6 +221,37 @@ ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho);
  * lambda_max this way).  DDH_ERR_NOT_READY before a Poisson solve or for r out of range. */
 ddh_status ddh_pcg_spectrum(const ddh_ctx* ctx, int32_t r, double* lambda_min, double* lambda_max);
 
+/* Boundary condition of the Helmholtz problem set by ddh_set_coefficients: DDH_BOUNDARY_IMPEDANCE
+ * (the default: Robin data g = du/dn - i k u on every boundary side) or DDH_BOUNDARY_DIRICHLET
+ * (phi given on the whole boundary; Sec. 2.2.1 Dirichlet constraints, the test of Sec. 3.2 /
+ * Table 3).  Dirichlet sides carry no Robin term; Algorithm 1 discards their boundary vertices and
+ * moments 2..l, and their moments above l are single-sided dual rows; the Dirichlet preconditioner
+ * divides those rows by 1 (C C^T).  Inhomogeneous data enter through ddh_solve_dirichlet.  Meshes
+ * with hanging edges are rejected with DDH_ERR_INVALID_ARG.  Call after ddh_set_coefficients and
+ * before ddh_factor. */
+typedef enum { DDH_BOUNDARY_IMPEDANCE = 0, DDH_BOUNDARY_DIRICHLET = 1 } ddh_boundary;
+ddh_status ddh_set_boundary(ddh_ctx* ctx, int32_t kind);
+
+/* Dirichlet data of R point sources, phi = -(i/4) H0^(2)(k |x - x_c|) (Sec. 3.2: x_c = (-2, 1) on
+ * (-1,1)^2, i.e. (-1/2, 1) on the unit square with k doubled), as a lifting g: the element-local
+ * field (N basis, device complex128 [R][n_local]) that is zero except on the boundary trace slots,
+ * where it holds the data's value at every boundary vertex and, on every boundary side, the bubble
+ * coefficients m = 2..p of the data's L^2 projection onto degree p (tau = S^-T q with q the
+ * orthonormal-Legendre moments by Gauss-Legendre quadrature of p + 40 nodes).  This is the reading
+ * of the constraint rows C_i phi = d_i, d_i = sqrt(2) S^-T p_i (Sec. 2.2.1) in which each boundary
+ * vertex keeps one constraint (its point value) and each side its bubble rows.  src: host [2R]
+ * (x_c, y_c) per right-hand side, unit-square coordinates; k is the context's wavenumber.  Needs
+ * DDH_BOUNDARY_DIRICHLET and a factored context. */
+ddh_status ddh_dirichlet_point_source(ddh_ctx* ctx, const double* src, int32_t R, void* g_dev);
+
+/* Solve with Dirichlet data: phi = g + phi_0, where g is a conforming lifting of the data (only its
+ * boundary trace matters for phi; e.g. from ddh_dirichlet_point_source) and phi_0 solves the
+ * problem with zero Dirichlet data and load b - A g (ddh_solve, in the factor's precision).  b_dev,
+ * g_dev, u_dev: device complex128 [R][n_local] (N basis).  Stats as ddh_solve (the primal residual
+ * is that of phi).  Needs a Dirichlet boundary (DDH_BOUNDARY_DIRICHLET or the Poisson mode). */
+ddh_status ddh_solve_dirichlet(ddh_ctx* ctx, const void* b_dev, const void* g_dev, void* u_dev, int32_t R,
+                               double tol, ddh_rhs_stats* stats);
+
 /* Build every table and factor: per-element edge Schur complements of A11 through the
  * fast-diagonalisation solver (Sec. 2.2.1 fast solver; Sec. 2.3.3 block inversion), the
  * coarse matrix K = A22 - A12^T A11^-1 A12 and its nested-dissection factor, the preconditioner
@@ -232,7 +266,8 @@ ddh_status ddh_elem_offsets(const ddh_ctx* ctx, int64_t* offsets_host);
 
 /* Load vectors b (Sec. 2.2.1, r_i terms) of R plane-wave problems: g = du/dn - i k u of
  * u = exp(i k (x cos theta + y sin theta)) on every boundary side.  theta: host [R];
- * b_dev: device complex128 [R][n_local] written (N basis). */
+ * b_dev: device complex128 [R][n_local] written (N basis).  DDH_ERR_INVALID_ARG with a Dirichlet
+ * boundary (DDH_BOUNDARY_DIRICHLET or the Poisson mode). */
 ddh_status ddh_rhs_planewave(ddh_ctx* ctx, const double* theta, int32_t R, void* b_dev);
 
 /* Solve A-phi = b subject to the continuity constraints for R right-hand sides.

@@ -122,6 +122,12 @@ struct ddh_ctx {
     KState kin, kout;
     // Poisson mode: extreme Ritz values of P^-1 F from the PCG coefficients of the last solve
     std::vector<double> pcg_lmin, pcg_lmax;
+    // per-degree tables of the Dirichlet trace lifting (ddh_dirichlet_point_source)
+    const int64_t* tr_off = nullptr;
+    const int* tr_nq = nullptr;
+    const int64_t* tr_xoff = nullptr;
+    const double* tr_x = nullptr;
+    const double* tr_Q = nullptr;
 };
 
 // accessors for translation units that do not see the context definition
@@ -212,6 +218,7 @@ static void free_model(ddh_ctx* ctx) {
     ctx->kc_ptr = ctx->kc_col = nullptr;
     ctx->kc_val = nullptr;
     ctx->gx = ctx->gw = nullptr;
+    ctx->tr_off = nullptr; ctx->tr_nq = nullptr; ctx->tr_xoff = nullptr; ctx->tr_x = nullptr; ctx->tr_Q = nullptr;
 }
 
 static ddh_status get_work(ddh_ctx* ctx, const std::string& name, size_t bytes, void** out) {
@@ -370,11 +377,13 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, m.row_f, &d.row_f))) return st;
     if ((st = upload(ctx, m.row_hblock, &d.row_hb))) return st;
     if (m.dirichlet) {
-        // diagonal scaling of the Dirichlet preconditioner (Sec. 2.3.3, Poisson): w = 1/diag(A_EE)
-        // per type-1 edge slot, rho_e w for the output side of rho_e S^Lap, and per dual row the
-        // inverse of (C W C^T)_rr = sum of w over the row's slots
-        std::vector<double> win(m.e1_slot.size()), wout(m.e1_slot.size()), rdi(m.n_dual, 0.0);
-        for (int e = 0; e < E; ++e) {
+        // Poisson mode: diagonal scaling of the Dirichlet preconditioner (Sec. 2.3.3): w =
+        // 1/diag(A_EE) per type-1 edge slot, rho_e w for the output side of rho_e S^Lap, and per
+        // dual row the inverse of (C W C^T)_rr = sum of w over the row's slots.  Helmholtz with
+        // Dirichlet data: W unscaled (w = 1), so (C C^T)_rr counts the row's slots (1 on the
+        // single-sided rows of a boundary side, 2 elsewhere)
+        std::vector<double> win(m.e1_slot.size(), 1.0), wout(m.e1_slot.size(), 1.0), rdi(m.n_dual, 0.0);
+        for (int e = 0; e < E && m.poisson; ++e) {
             const Elem& El = m.el[e];
             const int N = El.p + 1;
             for (int i = 0; i < El.nE1; ++i) {
@@ -390,8 +399,8 @@ static ddh_status upload_model(ddh_ctx* ctx) {
             if (m.row_f[r] >= 0) sw += win[m.row_f[r]];
             rdi[r] = 1.0 / sw;
         }
-        if ((st = upload(ctx, win, &d.e1_win))) return st;
-        if ((st = upload(ctx, wout, &d.e1_wout))) return st;
+        if (m.poisson && (st = upload(ctx, win, &d.e1_win))) return st;
+        if (m.poisson && (st = upload(ctx, wout, &d.e1_wout))) return st;
         if ((st = upload(ctx, rdi, &d.row_dinv))) return st;
     }
     if ((st = upload(ctx, m.c2_ptr, &d.c2_ptr))) return st;
@@ -829,6 +838,48 @@ static ddh_status upload_model(ddh_ctx* ctx) {
         ctx->gx = (double*)a;
         if ((st = upload(ctx, w, &a))) return st;
         ctx->gw = (double*)a;
+    }
+    // Dirichlet trace tables per degree: nq = p + 40 Gauss-Legendre nodes and the weights
+    // Q[m-2][i] = (S^-T (p(t_i) w_i))_m, m = 2..p, with orthonormal Legendre p_j (p_j(t) =
+    // sqrt(j + 1/2) P_j(t)); S^T tau = q is upper triangular (S_jj = g_j, S_{j+2,j} = -g_{j+1}), so
+    // tau_j = (q_j + g_{j+1} tau_{j+2}) / g_j from j = p down
+    if (m.dirichlet) {
+        std::vector<int64_t> toff, txoff;
+        std::vector<int> tnq;
+        std::vector<double> tx, tQ;
+        for (const auto& T : m.tabs) {
+            const int p = T.p, nq = p + 40;
+            std::vector<double> x, w;
+            gauss_legendre(nq, x, w);
+            std::vector<double> g(p + 2, 0.0);
+            g[0] = 1.0;
+            for (int i = 1; i <= p + 1; ++i) g[i] = 1.0 / std::sqrt((2.0 * i + 1.0) * (2.0 * i - 1.0));
+            toff.push_back((int64_t)tQ.size());
+            txoff.push_back((int64_t)tx.size());
+            tnq.push_back(nq);
+            tx.insert(tx.end(), x.begin(), x.end());
+            std::vector<double> Q((size_t)(p - 1) * nq);
+            std::vector<double> q(p + 1), tau(p + 3, 0.0);
+            for (int i = 0; i < nq; ++i) {
+                double P0 = 1.0, P1 = x[i];
+                for (int j = 0; j <= p; ++j) {
+                    double Pj;
+                    if (j == 0) Pj = P0;
+                    else if (j == 1) Pj = P1;
+                    else { Pj = ((2.0 * j - 1.0) * x[i] * P1 - (j - 1.0) * P0) / j; P0 = P1; P1 = Pj; }
+                    q[j] = std::sqrt(j + 0.5) * Pj * w[i];
+                }
+                std::fill(tau.begin(), tau.end(), 0.0);
+                for (int j = p; j >= 0; --j) tau[j] = (q[j] + g[j + 1] * tau[j + 2]) / g[j];
+                for (int mm = 2; mm <= p; ++mm) Q[(size_t)(mm - 2) * nq + i] = tau[mm];
+            }
+            tQ.insert(tQ.end(), Q.begin(), Q.end());
+        }
+        if ((st = upload(ctx, toff, &ctx->tr_off))) return st;
+        if ((st = upload(ctx, tnq, &ctx->tr_nq))) return st;
+        if ((st = upload(ctx, txoff, &ctx->tr_xoff))) return st;
+        if ((st = upload(ctx, tx, &ctx->tr_x))) return st;
+        if ((st = upload(ctx, tQ, &ctx->tr_Q))) return st;
     }
     // device error word (bounded waits record failures here)
     {
@@ -1617,7 +1668,7 @@ static KrylovOps dual_ops(ddh_ctx* ctx, const Work& w) {
             apply_op<T>(ctx, w, in, 1.0, nullptr, 0, K.w, nullptr, K.R, K.ctl + 1, &K);
         };
     // conforming meshes with the Dirichlet preconditioner: fetch + precondition + store fused
-    if (ctx->opt.precond == DDH_PRECOND_DIRICHLET && ctx->m.hblk_row0.empty()) {
+    if (ctx->opt.precond == DDH_PRECOND_DIRICHLET && ctx->m.hblk_row0.empty() && !ctx->dm.row_dinv) {
         o.prec_krylov = [ctx, w](const KrylovDev& K) {
             launch_pre_krylov<T>(ctx->dm, K, w.outE, K.R, ctx->stream);
             ctx->launches += 2;
@@ -1772,9 +1823,10 @@ static ddh_status solve_plain(ddh_ctx* ctx, const double2* b_dev, double2* u_dev
     std::vector<double> pr;
     ctx->refine_active = true;
     struct Off { ddh_ctx* c; ~Off() { c->refine_active = false; } } off_guard{ctx};
+    // primal_tol 0 (dual_stop): one FGMRES run to the dual tolerance, the paper's criterion
     if ((st = dd_solve_tilde<double>(ctx, (const double2*)bt, (double2*)phit, R, tol, ctx->opt.maxit,
                                      std::min(std::max(2, ctx->opt.restart), 200), ctx->opt.check_every, its, res,
-                                     tol, &pr, hflag != 0)))
+                                     ctx->opt.dual_stop ? 0.0 : tol, &pr, hflag != 0)))
         return st;
     launch_basis(d, (const double2*)phit, u_dev, 0, R, ctx->stream);
     ctx->launches++;
@@ -2013,6 +2065,7 @@ void ddh_default_options(ddh_options* o) {
     o->inner_passes_fp64 = 0;
     o->split_pass1 = 0;
     o->nd_pdl = 0;
+    o->dual_stop = 0;
 }
 
 ddh_status ddh_create(ddh_ctx** out, int device, void* cuda_stream) {
@@ -2091,9 +2144,82 @@ ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho) {
     return DDH_OK;
 }
 
+ddh_status ddh_set_boundary(ddh_ctx* ctx, int32_t kind) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->have_mesh || !ctx->have_coef) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh and coefficients first");
+    if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "the Poisson mode has its own Dirichlet boundary");
+    if (kind == DDH_BOUNDARY_IMPEDANCE) {
+        ctx->m.dirichlet = false;
+    } else if (kind == DDH_BOUNDARY_DIRICHLET) {
+        std::string err;
+        if (!set_dirichlet_boundary(ctx->m, err)) return fail(ctx, DDH_ERR_INVALID_ARG, err);
+    } else {
+        return fail(ctx, DDH_ERR_INVALID_ARG, "kind must be a ddh_boundary value");
+    }
+    ctx->factored = false;
+    return DDH_OK;
+}
+
+ddh_status ddh_dirichlet_point_source(ddh_ctx* ctx, const double* src, int32_t R, void* g_dev) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!ctx->m.dirichlet || ctx->m.poisson || !ctx->tr_Q)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "needs the Helmholtz problem with DDH_BOUNDARY_DIRICHLET");
+    if (!src || R <= 0 || !g_dev) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    cudaSetDevice(ctx->device);
+    void *sd, *gt;
+    ddh_status st;
+    if ((st = get_work(ctx, "dl_src", sizeof(double) * 2 * (size_t)R, &sd))) return st;
+    if ((st = get_work(ctx, "dl_gt", sizeof(double2) * (size_t)R * ctx->dm.n_local, &gt))) return st;
+    CK(cudaMemcpyAsync(sd, src, sizeof(double) * 2 * (size_t)R, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(gt, 0, sizeof(double2) * (size_t)R * ctx->dm.n_local, ctx->stream));
+    launch_dirichlet_trace(ctx->dm, (const double*)sd, ctx->m.k, ctx->tr_off, ctx->tr_nq, ctx->tr_xoff, ctx->tr_x,
+                           ctx->tr_Q, (double2*)gt, R, ctx->stream);
+    launch_basis(ctx->dm, (const double2*)gt, (double2*)g_dev, 0, R, ctx->stream);
+    ctx->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    return DDH_OK;
+}
+
+ddh_status ddh_solve_dirichlet(ddh_ctx* ctx, const void* b_dev, const void* g_dev, void* u_dev, int32_t R,
+                               double tol, ddh_rhs_stats* stats) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
+    if (!ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "needs a Dirichlet boundary");
+    if (!b_dev || !g_dev || !u_dev || R <= 0 || R > 1024) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
+    if (((uintptr_t)b_dev | (uintptr_t)g_dev | (uintptr_t)u_dev) & 15)
+        return fail(ctx, DDH_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    cudaSetDevice(ctx->device);
+    const DevModel& d = ctx->dm;
+    const size_t lb = sizeof(double2) * (size_t)R * d.n_local;
+    void *bt, *gt, *bg;
+    ddh_status st;
+    if ((st = get_work(ctx, "dl_bt", lb, &bt))) return st;
+    if ((st = get_work(ctx, "dl_gt", lb, &gt))) return st;
+    if ((st = get_work(ctx, "dl_bg", lb, &bg))) return st;
+    // b - A g on the interpolatory basis, back to the N basis: the load of the zero-data problem
+    launch_basis(d, (const double2*)b_dev, (double2*)bt, 0, R, ctx->stream);
+    launch_basis(d, (const double2*)g_dev, (double2*)gt, 0, R, ctx->stream);
+    launch_elem_matvec(d, (const double2*)gt, (const double2*)bt, (double2*)bg, R, ctx->stream);
+    launch_basis(d, (const double2*)bg, (double2*)bt, 0, R, ctx->stream);
+    ctx->launches += 4;
+    CK(cudaGetLastError());
+    st = ddh_solve(ctx, bt, u_dev, R, tol, stats);
+    if (st != DDH_OK && st != DDH_ERR_NO_CONVERGENCE) return st;
+    const std::string msg = ctx->err;
+    launch_axpby((const double2*)u_dev, 1.0, (const double2*)g_dev, 1.0, (double2*)u_dev, (int64_t)R * d.n_local,
+                 ctx->stream);
+    ctx->launches++;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (st != DDH_OK) ctx->err = msg;
+    return st;
+}
+
 ddh_status ddh_pcg_spectrum(const ddh_ctx* ctx, int32_t r, double* lambda_min, double* lambda_max) {
     if (!ctx || !lambda_min || !lambda_max) return DDH_ERR_INVALID_ARG;
-    if (!ctx->m.dirichlet || r < 0 || r >= (int32_t)ctx->pcg_lmax.size()) return DDH_ERR_NOT_READY;
+    if (!ctx->m.poisson || r < 0 || r >= (int32_t)ctx->pcg_lmax.size()) return DDH_ERR_NOT_READY;
     *lambda_min = ctx->pcg_lmin[r];
     *lambda_max = ctx->pcg_lmax[r];
     return DDH_OK;
@@ -2171,7 +2297,7 @@ ddh_status ddh_rhs_planewave(ddh_ctx* ctx, const double* theta, int32_t R, void*
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!theta || R <= 0 || !b_dev) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
-    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "impedance data: not available with a Dirichlet boundary");
     void* th;
     void* bt;
     ddh_status st;
@@ -2194,7 +2320,7 @@ ddh_status ddh_solve(ddh_ctx* ctx, const void* b_dev, void* u_dev, int32_t R, do
     if (((uintptr_t)b_dev | (uintptr_t)u_dev) & 15) return fail(ctx, DDH_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     if (tol <= 0) tol = ctx->opt.tol;
     cudaSetDevice(ctx->device);
-    if (ctx->m.dirichlet) return solve_pcg(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
+    if (ctx->m.poisson) return solve_pcg(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
     if (ctx->opt.precision == DDH_PREC_MIXED_FP32)
         return solve_mixed(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
     return solve_plain(ctx, (const double2*)b_dev, (double2*)u_dev, R, tol, stats);
@@ -2246,7 +2372,7 @@ ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, in
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !grad_eps_dev || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
-    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
     void *ut, *lt;
     ddh_status st;
     const size_t bytes = sizeof(double2) * (size_t)R * ctx->dm.n_local;
@@ -2266,7 +2392,7 @@ ddh_status ddh_grad_k(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, cons
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !theta || !grad_k_host || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
-    if (ctx->m.dirichlet) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
     void *ut, *lt, *db, *pe, *th;
     ddh_status st;
     const DevModel& d = ctx->dm;

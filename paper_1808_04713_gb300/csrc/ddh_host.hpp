@@ -69,6 +69,7 @@ struct Model {
     // boundary; the boundary vertices and the moments 2..l of a boundary side are discarded,
     // its moments above l become single-sided dual rows (Sec. 2.2.1 Dirichlet constraints)
     bool dirichlet = false;
+    bool poisson = false;         // Poisson mode: diagonally scaled Dirichlet preconditioner
     std::unordered_map<uint64_t, int> leaf_of;    // (level, i, j) key -> element
     // tables
     std::vector<PTable> tabs;
@@ -137,6 +138,10 @@ void set_coefficients(Model& m, double k, const double* eps);
 // Poisson mode: k = 0, eps = 1, rho[e] > 0 per element, zero Dirichlet data on the boundary
 // (no Robin terms); the mesh must be conforming (returns false with err otherwise)
 bool set_poisson(Model& m, const double* rho, std::string& err);
+// Helmholtz with Dirichlet data on the whole boundary (after set_coefficients): the same
+// constraint split as the Poisson mode, no Robin term on boundary sides, unit rho; the mesh must
+// be conforming (returns false with err otherwise)
+bool set_dirichlet_boundary(Model& m, std::string& err);
 // Robin coefficients per element side: gamma_eff = -i k h/2 on the boundary of the domain;
 // with `modified` (the Robin-modified local problems of Sec. 2.3.4) also +- i k h/2 on each
 // conforming interior side shared with an element of the opposite sign of the weak

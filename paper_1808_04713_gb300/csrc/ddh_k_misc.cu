@@ -335,6 +335,66 @@ __global__ void k_readback(DevModel dm, const double2* __restrict__ phi, double2
 }
 
 // ------------------------------------------------------------------ launch wrappers
+// ------------------------------------------------------------------ Dirichlet data (Sec. 2.2.1, 3.2)
+// The lifting of point-source Dirichlet data phi = -(i/4) H0^(2)(k r), r = |x - x_c|, on the
+// interpolatory basis: every boundary vertex slot of the element holds the data's value there;
+// every boundary side holds, in its bubble slots m = 2..p, tau_m = sum_i Q[m-2][i] phi(x_i) with
+// the per-degree weights Q = S^-T [p_j(t_i) w_i] (the N-basis coefficients of the L^2 projection
+// onto degree p, Gauss-Legendre nodes t_i); nothing else is written.  One CTA per (element, RHS).
+// H0^(2)(z) = J0(z) - i Y0(z), so phi = (-Y0(z) - i J0(z)) / 4.
+__device__ __forceinline__ double2 point_source_value(double k, double xc, double yc, double x, double y) {
+    const double z = k * hypot(x - xc, y - yc);
+    return make_double2(-0.25 * y0(z), -0.25 * j0(z));
+}
+__global__ void __launch_bounds__(128) k_dirichlet_trace(DevModel dm, const double* __restrict__ src, double k,
+                                                         const int64_t* __restrict__ tr_off, const int* __restrict__ tr_nq,
+                                                         const int64_t* __restrict__ tr_xoff, const double* __restrict__ tr_x,
+                                                         const double* __restrict__ tr_Q, double2* __restrict__ out) {
+    const int e = blockIdx.x, r = blockIdx.y;
+    const int bm = dm.bmask[e];
+    if (!bm) return;
+    __shared__ double2 val[kTraceMaxNodes];
+    const int p = dm.p[e], N = p + 1, t = dm.ptab[e];
+    const double x0 = dm.geo[3 * e], y0c = dm.geo[3 * e + 1], h = dm.geo[3 * e + 2];
+    const double xc = src[2 * r], yc = src[2 * r + 1];
+    double2* o = out + (int64_t)r * dm.n_local + dm.off[e];
+    // corners (a = 0: x1 = +1, a = 1: x1 = -1; b likewise along x2)
+    if (threadIdx.x < 4) {
+        const int a = threadIdx.x & 1, b = threadIdx.x >> 1;
+        const bool on = (a == 1 && (bm & 1)) || (a == 0 && (bm & 2)) || (b == 1 && (bm & 4)) || (b == 0 && (bm & 8));
+        if (on) o[a + N * b] = point_source_value(k, xc, yc, x0 + (a == 0 ? h : 0.0), y0c + (b == 0 ? h : 0.0));
+    }
+    const int nq = tr_nq[t];
+    const double* xs = tr_x + tr_xoff[t];
+    const double* Q = tr_Q + tr_off[t];
+    for (int s = 0; s < 4; ++s) {
+        if (!(bm & (1 << s))) continue;
+        __syncthreads();
+        for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+            const double u = 0.5 * h * (1.0 + xs[i]);
+            const double X = s < 2 ? (s == 0 ? x0 : x0 + h) : x0 + u;
+            const double Y = s < 2 ? y0c + u : (s == 2 ? y0c : y0c + h);
+            val[i] = point_source_value(k, xc, yc, X, Y);
+        }
+        __syncthreads();
+        for (int m = 2 + (int)threadIdx.x; m <= p; m += blockDim.x) {
+            const double* q = Q + (int64_t)(m - 2) * nq;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int i = 0; i < nq; ++i) {
+                acc.x = fma(q[i], val[i].x, acc.x);
+                acc.y = fma(q[i], val[i].y, acc.y);
+            }
+            const int slot = s == 0 ? 1 + N * m : (s == 1 ? N * m : (s == 2 ? m + N : m));
+            o[slot] = acc;
+        }
+    }
+}
+void launch_dirichlet_trace(const DevModel& dm, const double* src, double k, const int64_t* tr_off, const int* tr_nq,
+                            const int64_t* tr_xoff, const double* tr_x, const double* tr_Q, double2* out, int R,
+                            cudaStream_t st) {
+    k_dirichlet_trace<<<dim3(dm.E, R), 128, 0, st>>>(dm, src, k, tr_off, tr_nq, tr_xoff, tr_x, tr_Q, out);
+}
+
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
                           int nq, double2* bt, int R, cudaStream_t st, int dk) {
     k_rhs_planewave<<<dim3(dm.E, R), 128, 0, st>>>(dm, theta, k, gx, gw, nq, bt, dk);

@@ -158,6 +158,13 @@ void launch_dinv(const DevModel& dm, const double2* x, double2* y, int R, const 
 // factor time)
 void launch_gemv(const void* A, bool f32, int n_out, int n_in, const double2* x, double2* y, const double2* c, int mode,
                  int64_t xs, int64_t ys, int R, const int* done, cudaStream_t st, int form = 1);
+// Lifting of point-source Dirichlet data (tilde basis, boundary slots only; `out` zeroed by the
+// caller): per degree table t, tr_nq[t] Gauss-Legendre nodes tr_x[tr_xoff[t] ..] and the weights
+// tr_Q[tr_off[t] ..] ((p - 1) x nq, bubble m = 2..p by node); src [2R] source centres
+constexpr int kTraceMaxNodes = 96;
+void launch_dirichlet_trace(const DevModel& dm, const double* src, double k, const int64_t* tr_off, const int* tr_nq,
+                            const int64_t* tr_xoff, const double* tr_x, const double* tr_Q, double2* out, int R,
+                            cudaStream_t st);
 void launch_rhs_planewave(const DevModel& dm, const double* theta, double k, const double* gx, const double* gw,
                           int nq, double2* bt, int R, cudaStream_t st, int dk = 0);
 void launch_grad_elem(const DevModel& dm, const double2* ut, const double2* lt, int R, double k, int mode, double* out,

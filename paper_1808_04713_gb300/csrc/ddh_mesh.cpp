@@ -175,6 +175,7 @@ int locate_point(const Model& m, double x, double y, double& u1, double& u2) {
 void set_coefficients(Model& m, double k, const double* eps) {
     m.k = k;
     m.dirichlet = false;
+    m.poisson = false;
     for (size_t e = 0; e < m.el.size(); ++e) {
         Elem& E = m.el[e];
         E.eps = eps[e];
@@ -195,6 +196,7 @@ bool set_poisson(Model& m, const double* rho, std::string& err) {
         if (!(rho[e] > 0.0) || !std::isfinite(rho[e])) { err = "rho must be positive and finite"; return false; }
     m.k = 0.0;
     m.dirichlet = true;
+    m.poisson = true;
     for (size_t e = 0; e < m.el.size(); ++e) {
         Elem& E = m.el[e];
         E.eps = 1.0;
@@ -205,6 +207,17 @@ bool set_poisson(Model& m, const double* rho, std::string& err) {
             E.gam[s] = cd(0.0, 0.0);
         }
     }
+    return true;
+}
+
+bool set_dirichlet_boundary(Model& m, std::string& err) {
+    for (const auto& ed : m.edges)
+        if (ed.kind == 2) { err = "Dirichlet boundary data need a conforming mesh (no hanging edges)"; return false; }
+    m.dirichlet = true;
+    m.poisson = false;
+    for (auto& E : m.el)
+        for (int s = 0; s < 4; ++s)
+            if (E.boundary[s]) E.gam[s] = cd(0.0, 0.0);
     return true;
 }
 
@@ -244,7 +257,8 @@ int set_robin(Model& m, bool modified) {
             const MasterEdge& ed = m.edges[se.first];
             El.gam[s] = cd(0.0, 0.0);
             if (ed.kind == 0) {
-                El.gam[s] = cd(0.0, -m.k * 0.5 * El.h);
+                // impedance boundary; none on a Dirichlet boundary (the data are constraints)
+                El.gam[s] = m.dirichlet ? cd(0.0, 0.0) : cd(0.0, -m.k * 0.5 * El.h);
             } else if (modified && ed.kind == 1) {
                 const int nb = se.second == 1 ? ed.subs[0].elem : ed.elem;
                 if (sign[nb] != sign[e]) {

@@ -19,6 +19,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NOT_READY, ERR_NO_CONVERGENCE, ERR_S
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 PRECOND_DIRICHLET, PRECOND_LUMPED, PRECOND_NONE = 0, 1, 2
 LOCAL_EDGE, LOCAL_FDM = 0, 1
+BOUNDARY_IMPEDANCE, BOUNDARY_DIRICHLET = 0, 1
 COARSE_AUTO, COARSE_DENSE, COARSE_ND, COARSE_ND_LEVELS = 0, 1, 2, 3
 EDGE_LAUNCH_AUTO, EDGE_LAUNCH_PER_TASK, EDGE_LAUNCH_PERSISTENT = 0, 1, 2
 
@@ -37,7 +38,7 @@ class Options(C.Structure):
                 ("inner_tol", C.c_double), ("coarse_form", C.c_int32), ("robin_modified", C.c_int32),
                 ("tensor_cores", C.c_int32), ("inner_krylov_fp32", C.c_int32), ("edge_launch", C.c_int32),
                 ("nd_chains", C.c_int32), ("inner_passes_fp64", C.c_int32), ("split_pass1", C.c_int32),
-                ("nd_pdl", C.c_int32)]
+                ("nd_pdl", C.c_int32), ("dual_stop", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -59,6 +60,10 @@ _SIGS = {
     "ddh_set_mesh": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32]),
     "ddh_set_coefficients": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "ddh_set_poisson": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ddh_set_boundary": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ddh_dirichlet_point_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ddh_solve_dirichlet": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
+                                      C.c_void_p]),
     "ddh_pcg_spectrum": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ddh_factor": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
     "ddh_get_info": (C.c_int, [C.c_void_p, C.POINTER(Info)]),
@@ -167,6 +172,29 @@ class DDH:
         """Poisson mode: -div(rho grad phi) = f, zero Dirichlet data, rho per element."""
         r = np.ascontiguousarray(rho, dtype=np.float64)
         self._check(self.lib.ddh_set_poisson(self.h, r.ctypes.data))
+
+    def set_boundary(self, kind: int):
+        """BOUNDARY_IMPEDANCE (default) or BOUNDARY_DIRICHLET for the Helmholtz problem."""
+        self._check(self.lib.ddh_set_boundary(self.h, int(kind)))
+
+    def dirichlet_point_source(self, src):
+        """Lifting [R, n_local] of the data -(i/4) H0^(2)(k |x - x_c|) for centres src [R, 2]."""
+        c = np.ascontiguousarray(np.atleast_2d(src), dtype=np.float64)
+        g = self._vec(c.shape[0])
+        self._check(self.lib.ddh_dirichlet_point_source(self.h, c.ctypes.data, int(c.shape[0]), _ptr(g)))
+        return g
+
+    def solve_dirichlet(self, b, g, tol: float = 0.0, out=None, stats: bool = True, allow_noconv: bool = False):
+        """phi = g + phi_0 for load b and Dirichlet lifting g (both [R, n_local])."""
+        b = b.contiguous()
+        g = g.contiguous()
+        R = b.shape[0]
+        u = self._vec(R) if out is None else out
+        st = (RhsStats * R)() if stats else None
+        allow = (OK, ERR_NO_CONVERGENCE) if allow_noconv else (OK,)
+        self._check(self.lib.ddh_solve_dirichlet(self.h, _ptr(b), _ptr(g), _ptr(u), R, float(tol),
+                                                 C.cast(st, C.c_void_p) if stats else None), allow=allow)
+        return u, (list(st) if stats else None)
 
     def pcg_spectrum(self, r: int = 0):
         """(lambda_min, lambda_max) Lanczos estimates of P^-1 F from the last Poisson solve."""

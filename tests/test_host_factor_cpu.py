@@ -78,3 +78,20 @@ def test_host_factor_poisson_split_matches_oracle(ddh, n, p, l):
     assert sizes["n_conforming"] == (m - 1) ** 2 + 2 * m * (m - 1) * (p - 1) + interior
     assert secs[2] <= 1e-12, secs
     assert secs[3] <= 1e-10, secs
+
+
+def test_dispersion_l_reproduces_the_bold_cells_of_table3(ddh):
+    """The library's l from the dispersion criterion (eq. dispersion_criterion) is the smallest l
+    the paper's Table 3 marks bold for every (N, k) it prints: bold exactly when l >= the
+    library's choice.  The criterion reads kh only; the paper's kh = k * 2/sqrt(N) on (-1,1)^2 is
+    set on a 2 x 2 mesh of the unit square (h = 1/2) by the wavenumber 2 kh."""
+    import os
+    fix = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_helmholtz.txt")
+    rows = [tuple(int(v) for v in ln.split()) for ln in open(fix) if ln[:1].isdigit()]
+    seen = {}
+    for p, N, k, l, its, bold in rows:
+        if (N, k) not in seen:
+            kh = k * 2.0 / np.sqrt(N)
+            _, _, l_lib = ddh.host_factor(2, W.uniform_leaves(2), np.full(4, 3), 2.0 * kh, np.ones(4))
+            seen[(N, k)] = l_lib
+        assert bool(bold) == (l >= seen[(N, k)]), (p, N, k, l, seen[(N, k)])
