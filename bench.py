@@ -14,6 +14,9 @@ relative residual 1e-10.  Beside it, on the same workload and tolerance:
   poisson_table2  the Poisson test problem of Sec. 3.1 (PCG with the scaled Dirichlet
                 preconditioner) on three Table 2 cases, with iterations and the Lanczos lambda_max
                 beside the printed values.
+  helmholtz_table3  the Helmholtz test with point-source Dirichlet data of Sec. 3.2 on its
+                largest Table 3 cells (32 x 32 squares, p = 32 and 16), plain FP64 beside the
+                printed iteration counts, and the mixed form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -296,6 +299,59 @@ def _poisson_form(p, N, l, R, local, stream, flush, warmup, steps):
     return out
 
 
+# the paper's Table 3 (Sec. 3.2): printed PGMRES iterations of the Helmholtz Dirichlet test for the
+# cells timed here, (p, N, k, l) -> iterations
+TABLE3_PRINTED = {(32, 1024, 31, 3): 15, (16, 1024, 21, 3): 11}
+
+
+def _dirichlet_form(p, N, kp, l, R, prec, local, stream, flush, warmup, steps):
+    """Solves/s of the Helmholtz problem with point-source Dirichlet data (Table 3 workload: the
+    paper's (-1,1)^2 mapped to the unit square, k doubled, x_c = (-1/2, 1)); `dual_stop` in FP64
+    (the paper's criterion), the FP64 primal yardstick in the mixed form."""
+    import torch
+    import workloads as W
+    from paper_1808_04713_gb300 import ddh
+    m = int(round(N ** 0.5))
+    leaves = W.uniform_leaves(m)
+    s = ddh.DDH(local, stream=stream)
+    s.set_mesh(m, leaves, [p] * (m * m))
+    s.set_coefficients(2.0 * kp, [1.0] * (m * m))
+    s.set_boundary(ddh.BOUNDARY_DIRICHLET)
+    s.factor(tol=TOL, l_override=l, precision=prec, dual_stop=1 if prec == ddh.PREC_FP64 else 0)
+    with torch.cuda.stream(stream):
+        g = s.dirichlet_point_source([[-0.5, 1.0]] * R)
+        b = torch.zeros_like(g)
+        u = torch.empty_like(g)
+    for _ in range(warmup):
+        s.solve_dirichlet(b, g, tol=TOL, out=u, stats=False)
+    l0 = s.kernel_launches()
+    ts = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        s.solve_dirichlet(b, g, tol=TOL, out=u, stats=False)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    launches = (s.kernel_launches() - l0) // max(1, steps)
+    _, st = s.solve_dirichlet(b, g, tol=TOL, out=u)
+    info = s.info()
+    out = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT, "rhs": R,
+           "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3), "steps": len(ts),
+           "form": "plain FP64 (dual residual 1e-10)" if prec == ddh.PREC_FP64 else "mixed (primal residual 1e-10)",
+           "iterations": max(x.iterations for x in st), "inner_iterations": max(x.inner_iterations for x in st),
+           "iterations_printed": TABLE3_PRINTED.get((p, N, int(kp), l)) if prec == ddh.PREC_FP64 else None,
+           "max_primal_residual": float(max(x.primal_residual for x in st)),
+           "launches_per_step": int(launches), "dof": int(info.n_conforming), "n_dual": info.n_dual,
+           "n_coarse": info.n_coarse}
+    s.close()
+    return out
+
+
 def _cpu_baseline(n_elem_full: int, iters_full: int) -> dict:
     """The oracle, as it stands, on the 16 x 16 corner of the workload (same element operators),
     timed with one BLAS thread and with all host cores; rates scaled to the full workload."""
@@ -438,6 +494,14 @@ def run_ours(args):
         for (pp, NN, ll), R_ in (((3, 64, 2), 1), ((8, 16, 2), 1), ((16, 4, 1), 1), ((8, 16, 2), 8)):
             pt[f"p{pp}_N{NN}_l{ll}_R{R_}"] = _poisson_form(pp, NN, ll, R_, local, stream, flush, 3, max(3, args.steps))
         extras["poisson_table2"] = pt
+        # ---- the Helmholtz test with Dirichlet data of Sec. 3.2 (Table 3), its largest cells
+        ht = {}
+        for (pp, NN, kk, ll) in ((32, 1024, 31, 3), (16, 1024, 21, 3)):
+            ht[f"p{pp}_N{NN}_k{kk}_l{ll}_fp64"] = _dirichlet_form(pp, NN, float(kk), ll, 1, ddh.PREC_FP64, local,
+                                                                   stream, flush, 3, max(3, args.steps))
+        ht["p32_N1024_k31_l3_mixed"] = _dirichlet_form(32, 1024, 31.0, 3, 1, ddh.PREC_MIXED_FP32, local, stream,
+                                                       flush, 3, max(3, args.steps))
+        extras["helmholtz_table3"] = ht
 
     out = None
     if rank == 0:
