@@ -327,7 +327,9 @@ ddh_status ddh_primal_residual(ddh_ctx* ctx, const void* b_dev, const void* u_de
  * naming the limit.  Before factor it returns DDH_ERR_NOT_READY.  The first call on a device
  * looks up the scratch address (cudaGetSymbolAddress) with that device current; make that
  * first call before any stream capture.  The call synchronises the context stream to copy the
- * norms to out_host, and leaves the caller's current device as it found it.  Every call on a
+ * norms to out_host, so it is not capturable: while the context stream is being captured it
+ * returns DDH_ERR_INVALID_ARG without touching the stream.  It leaves the caller's current device
+ * as it found it.  Every call on a
  * device shares the one array (it keeps the last call's contents; the accumulators are cleared
  * on entry), so calls that overlap on the GPU -- from several streams or threads -- race.
  * Same arguments and result as ddh_primal_residual. */

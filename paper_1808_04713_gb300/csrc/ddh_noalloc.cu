@@ -9,7 +9,8 @@
 // file-scope scratch array in device memory instead of the context's on-demand work
 // buffers, so it allocates nothing.  The array is a symbol of this library: every GPU
 // that loads the library holds kScratchBytes of it until the process exits.  The call
-// still synchronises the context stream to return the norms to the host.
+// still synchronises the context stream to return the norms to the host, so it refuses to
+// run while that stream is being captured into a CUDA graph.
 #include <mutex>
 
 #include "../../include/ddh.h"
@@ -79,6 +80,16 @@ extern "C" ddh_status ddh_primal_residual_noalloc(ddh_ctx* ctx, const void* b_de
     }
     const DeviceGuard guard(dev);
     if (!guard.ok) { ctx_set_error(ctx, "cudaSetDevice failed"); return DDH_ERR_CUDA; }
+    {
+        // the call ends with a host read of the norms (a stream synchronisation), which a stream
+        // capture cannot hold: refuse before touching the stream, and leave the capture intact
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(ctx_stream(ctx), &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            ctx_set_error(ctx, "ddh_primal_residual_noalloc: the context stream is being captured; the call "
+                               "synchronises the stream and cannot be captured");
+            return DDH_ERR_INVALID_ARG;
+        }
+    }
     unsigned char* base;
     {
         // once per device, with that device current: the device address of the scratch symbol
