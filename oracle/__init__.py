@@ -23,6 +23,9 @@ Modules
   dirichlet    Section 3.2: the Helmholtz test with point-source Dirichlet data (lifting of
                the boundary trace, zero-data dual-primal solve, FGMRES), pinned to the exact
                solution and to the printed Table 3.
+  pml          Section 4: axis-aligned PMLs by complex coordinate stretching (per-element
+               anisotropic coefficients on the same split), pinned to the exact stretched plane
+               wave and to the layer's absorption.
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``; see the
 docstrings for the pin of each part.

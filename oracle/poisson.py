@@ -67,11 +67,15 @@ class PoissonDD:
     A11_lap: sp.csr_matrix    # stiffness part of A11 (equal to A11 when k = 0)
 
 
-def build(n: int, p: int, l: int, rho: np.ndarray | None = None, k: float = 0.0) -> PoissonDD:
+def build(n: int, p: int, l: int, rho: np.ndarray | None = None, k: float = 0.0,
+          coef: np.ndarray | None = None) -> PoissonDD:
     """The dual-primal pieces for 2^n x 2^n squares of degree p with l primal moments per edge.
     With k > 0 the element operators are those of the Helmholtz problem with the same zero
     Dirichlet constraints (alpha = I, beta = -k^2 on the unit square: S + c_e M, c_e = -k^2 (h/2)^2;
-    Sec. 3.2); A11_lap then holds the stiffness part, which the Dirichlet preconditioner uses."""
+    Sec. 3.2); A11_lap then holds the stiffness part, which the Dirichlet preconditioner uses.
+    coef [E, 3] (complex) replaces both: element e's operator is
+    a_e K(x1) M(x2) + b_e M(x1) K(x2) + c_e M (x) M (diagonal alpha = diag(a_e, b_e) and
+    beta_eff = c_e per element, as a coordinate-stretched PML gives, Sec. 4)."""
     m = 2 ** n
     E = m * m
     leaves = uniform_leaves(m)
@@ -143,7 +147,15 @@ def build(n: int, p: int, l: int, rho: np.ndarray | None = None, k: float = 0.0)
     C1 = sp.csr_matrix((dv, (dr, dc)), shape=(r, n1))
     # ---- element operators rho_e (K (x) M + M (x) K) on the interpolatory basis
     S = to_tilde(p, stiffness_matrix_N(p))
-    if k > 0.0:
+    if coef is not None:
+        M1 = lg.mass_1d(p)
+        K1 = lg.stiff_1d(p)
+        Sx = to_tilde(p, np.kron(M1, K1))     # K along x1 (index a, fastest), M along x2
+        Sy = to_tilde(p, np.kron(K1, M1))
+        Mt = to_tilde(p, mass_matrix_N(p))
+        cf = np.asarray(coef, complex)
+        A = sp.block_diag([cf[e, 0] * Sx + cf[e, 1] * Sy + cf[e, 2] * Mt for e in range(E)], format="csr")
+    elif k > 0.0:
         c = -(k * 0.5 / m) ** 2
         Ae = S + c * to_tilde(p, mass_matrix_N(p))
         A = sp.block_diag([rho[e] * Ae for e in range(E)], format="csr")
