@@ -14,6 +14,8 @@ relative residual 1e-10.  Beside it, on the same workload and tolerance:
   poisson_table2  the Poisson test problem of Sec. 3.1 (PCG with the scaled Dirichlet
                 preconditioner) on three Table 2 cases, with iterations and the Lanczos lambda_max
                 beside the printed values.
+  pml           axis-aligned PMLs (Sec. 4) on every side of 32 x 32 squares (p = 12, k = 40),
+                8 seeded loads, plain FP64 and mixed;
   helmholtz_table3  the Helmholtz test with point-source Dirichlet data of Sec. 3.2 on its
                 largest Table 3 cells (32 x 32 squares, p = 32 and 16), plain FP64 beside the
                 printed iteration counts, and the mixed form.
@@ -352,6 +354,48 @@ def _dirichlet_form(p, N, kp, l, R, prec, local, stream, flush, warmup, steps):
     return out
 
 
+def _pml_form(prec, local, stream, flush, warmup, steps, m=32, p=12, k=40.0, cells=2, sigma=40.0, R=8):
+    """Solves/s with axis-aligned PMLs (Sec. 4): m x m squares of degree p, layers `cells` elements
+    thick on all four sides (s_i = 1 - i sigma/k), zero Dirichlet data beyond them, R seeded
+    volume loads (entries ~ U(-1, 1), seed 41)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_1808_04713_gb300 import ddh
+    E = m * m
+    leaves = W.uniform_leaves(m)
+    st_ = 1.0 - 1j * sigma / k
+    s1 = np.where((leaves[:, 1] < cells) | (leaves[:, 1] >= m - cells), st_, 1.0)
+    s2 = np.where((leaves[:, 2] < cells) | (leaves[:, 2] >= m - cells), st_, 1.0)
+    s = ddh.DDH(local, stream=stream)
+    s.set_mesh(m, leaves, np.full(E, p))
+    s.set_coefficients(k, np.ones(E))
+    s.set_pml(s1, s2)
+    s.set_boundary(ddh.BOUNDARY_DIRICHLET)
+    s.factor(tol=TOL, precision=prec)
+    loads = np.random.default_rng(41).uniform(-1.0, 1.0, size=(R, E * (p + 1) ** 2)).astype(np.complex128)
+    with torch.cuda.stream(stream):
+        b = torch.tensor(loads, device=f"cuda:{local}")
+        u = torch.empty_like(b)
+    for _ in range(warmup):
+        s.solve(b, tol=TOL, out=u, stats=False)
+    l0 = s.kernel_launches()
+    ts = _time_solves(s, b, u, stream, flush, steps)
+    launches = (s.kernel_launches() - l0) // max(1, steps)
+    _, st = s.solve(b, tol=TOL, out=u)
+    info = s.info()
+    out = {"value": round(R * len(ts) / sum(ts), 3), "unit": UNIT, "rhs": R,
+           "ms_per_solve_batch": round(1e3 * sum(ts) / len(ts), 3), "steps": len(ts),
+           "form": "plain FP64" if prec == ddh.PREC_FP64 else "mixed",
+           "iterations": max(x.iterations for x in st), "inner_iterations": max(x.inner_iterations for x in st),
+           "max_primal_residual": float(max(x.primal_residual for x in st)), "l": info.l,
+           "launches_per_step": int(launches), "dof": int(info.n_conforming), "n_dual": info.n_dual,
+           "n_coarse": info.n_coarse,
+           "workload": f"{m}x{m} squares, p = {p}, k = {k}, PML {cells} elements thick on every side, sigma = {sigma}"}
+    s.close()
+    return out
+
+
 def _cpu_baseline(n_elem_full: int, iters_full: int) -> dict:
     """The oracle, as it stands, on the 16 x 16 corner of the workload (same element operators),
     timed with one BLAS thread and with all host cores; rates scaled to the full workload."""
@@ -502,6 +546,9 @@ def run_ours(args):
         ht["p32_N1024_k31_l3_mixed"] = _dirichlet_form(32, 1024, 31.0, 3, 1, ddh.PREC_MIXED_FP32, local, stream,
                                                        flush, 3, max(3, args.steps))
         extras["helmholtz_table3"] = ht
+        # ---- axis-aligned PMLs (Sec. 4): layers on every side, zero data beyond, 8 loads
+        extras["pml"] = {"fp64": _pml_form(ddh.PREC_FP64, local, stream, flush, 2, max(3, min(args.steps, 10))),
+                         "mixed": _pml_form(ddh.PREC_MIXED_FP32, local, stream, flush, 2, max(3, min(args.steps, 10)))}
 
     out = None
     if rank == 0:

@@ -221,6 +221,20 @@ ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho);
  * lambda_max this way).  DDH_ERR_NOT_READY before a Poisson solve or for r out of range. */
 ddh_status ddh_pcg_spectrum(const ddh_ctx* ctx, int32_t r, double* lambda_min, double* lambda_max);
 
+/* Axis-aligned perfectly matched layers by complex coordinate stretching (Sec. 4, the PML paragraph:
+ * eps_PML = Lambda eps, mu_PML = Lambda mu with Lambda = det(S) S^-2): s host [4 n_elem] =
+ * (Re s1, Im s1, Re s2, Im s2) per element, the stretch factors along x1 and x2 (1 outside the
+ * layers; with sigma_i piecewise constant per element, s_i = 1 - i sigma_i / k makes waves
+ * exp(-i k x) decay inside a layer).  A stretched element's operator becomes
+ *   (s2/s1) K(x1) M(x2) + (s1/s2) M(x1) K(x2) - k^2 eps (h/2)^2 s1 s2 M (x) M,
+ * which stays separable: the element fast solver divides by complex eigenvalues, and the explicit
+ * edge operators, the coarse matrix and the element kernels carry the complex coefficients.  The
+ * Dirichlet preconditioner keeps the unstretched stiffness.  Call after ddh_set_coefficients (which
+ * removes any layer) and before ddh_factor; close the domain with DDH_BOUNDARY_DIRICHLET (zero data
+ * beyond the layers) or keep the impedance boundary.  ddh_grad_eps and ddh_grad_k return
+ * DDH_ERR_INVALID_ARG on a context with a layer. */
+ddh_status ddh_set_pml(ddh_ctx* ctx, const double* s);
+
 /* Boundary condition of the Helmholtz problem set by ddh_set_coefficients: DDH_BOUNDARY_IMPEDANCE
  * (the default: Robin data g = du/dn - i k u on every boundary side) or DDH_BOUNDARY_DIRICHLET
  * (phi given on the whole boundary; Sec. 2.2.1 Dirichlet constraints, the test of Sec. 3.2 /

@@ -284,19 +284,42 @@ static ddh_status upload_model(ddh_ctx* ctx) {
     if ((st = upload(ctx, bmask, &d.bmask))) return st;
     if ((st = upload(ctx, geo, &d.geo))) return st;
     {
-        // 1 / (rho_e (mu_a + mu_b + c_e mu_a mu_b)): the divide of the element fast solver
+        // 1 / (rho_e (mu_a + mu_b + c_e mu_a mu_b)): the divide of the element fast solver; with a
+        // PML, 1 / (pa mu_b + pb mu_a + pc mu_a mu_b) (a along x1) for the stretched elements, its
+        // imaginary part in a second table
+        bool any_pml = false;
+        for (const auto& El : m.el) any_pml |= El.pml;
         std::vector<int64_t> doff(E);
-        std::vector<double> dv;
+        std::vector<double> dv, dvi, pco;
         for (int e = 0; e < E; ++e) {
             const Elem& El = m.el[e];
             const auto& mu = m.tabs[El.ptab].mu;
             const int n = El.p - 1;
             doff[e] = (int64_t)dv.size();
             for (int a = 0; a < n; ++a)
-                for (int b = 0; b < n; ++b) dv.push_back(1.0 / (mu[a] + mu[b] + El.c * mu[a] * mu[b]) / El.rho);
+                for (int b = 0; b < n; ++b) {
+                    if (El.pml) {
+                        const cd D = El.pa * mu[b] + El.pb * mu[a] + El.pc * (mu[a] * mu[b]);
+                        const cd q = 1.0 / D;
+                        dv.push_back(q.real());
+                        dvi.push_back(q.imag());
+                    } else {
+                        dv.push_back(1.0 / (mu[a] + mu[b] + El.c * mu[a] * mu[b]) / El.rho);
+                        if (any_pml) dvi.push_back(0.0);
+                    }
+                }
+            if (any_pml) {
+                const cd pa = El.pml ? El.pa : cd(1.0), pb = El.pml ? El.pb : cd(1.0), pc = El.pml ? El.pc : cd(El.c);
+                const double v6[6] = {pa.real(), pa.imag(), pb.real(), pb.imag(), pc.real(), pc.imag()};
+                pco.insert(pco.end(), v6, v6 + 6);
+            }
         }
         if ((st = upload(ctx, dv, &d.dinv_all))) return st;
         if ((st = upload(ctx, doff, &d.dinv_off))) return st;
+        if (any_pml) {
+            if ((st = upload(ctx, dvi, &d.dinv_im))) return st;
+            if ((st = upload(ctx, pco, &d.pml))) return st;
+        }
     }
     // tables
     std::vector<int> tp;
@@ -2144,6 +2167,21 @@ ddh_status ddh_set_poisson(ddh_ctx* ctx, const double* rho) {
     return DDH_OK;
 }
 
+ddh_status ddh_set_pml(ddh_ctx* ctx, const double* s) {
+    if (!ctx) return DDH_ERR_INVALID_ARG;
+    if (!ctx->have_mesh || !ctx->have_coef) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh and coefficients first");
+    if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (!s) return fail(ctx, DDH_ERR_INVALID_ARG, "s must be non-null");
+    for (size_t e = 0; e < 4 * ctx->m.el.size(); ++e)
+        if (!std::isfinite(s[e])) return fail(ctx, DDH_ERR_INVALID_ARG, "stretch factors must be finite");
+    for (size_t e = 0; e < ctx->m.el.size(); ++e)
+        if (s[4 * e] * s[4 * e] + s[4 * e + 1] * s[4 * e + 1] == 0.0 || s[4 * e + 2] * s[4 * e + 2] + s[4 * e + 3] * s[4 * e + 3] == 0.0)
+            return fail(ctx, DDH_ERR_INVALID_ARG, "stretch factors must be non-zero");
+    set_pml(ctx->m, s);
+    ctx->factored = false;
+    return DDH_OK;
+}
+
 ddh_status ddh_set_boundary(ddh_ctx* ctx, int32_t kind) {
     if (!ctx) return DDH_ERR_INVALID_ARG;
     if (!ctx->have_mesh || !ctx->have_coef) return fail(ctx, DDH_ERR_NOT_READY, "set the mesh and coefficients first");
@@ -2373,6 +2411,7 @@ ddh_status ddh_grad_eps(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, in
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !grad_eps_dev || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
     if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (ctx->dm.pml) return fail(ctx, DDH_ERR_INVALID_ARG, "gradients are not available with a PML");
     void *ut, *lt;
     ddh_status st;
     const size_t bytes = sizeof(double2) * (size_t)R * ctx->dm.n_local;
@@ -2393,6 +2432,7 @@ ddh_status ddh_grad_k(ddh_ctx* ctx, const void* u_dev, const void* lam_dev, cons
     if (!ctx->factored) return fail(ctx, DDH_ERR_NOT_READY, "factor first");
     if (!u_dev || !lam_dev || !theta || !grad_k_host || R <= 0) return fail(ctx, DDH_ERR_INVALID_ARG, "bad arguments");
     if (ctx->m.poisson) return fail(ctx, DDH_ERR_INVALID_ARG, "a Helmholtz call: not available in the Poisson mode");
+    if (ctx->dm.pml) return fail(ctx, DDH_ERR_INVALID_ARG, "gradients are not available with a PML");
     void *ut, *lt, *db, *pe, *th;
     ddh_status st;
     const DevModel& d = ctx->dm;

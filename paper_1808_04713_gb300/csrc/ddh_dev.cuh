@@ -51,6 +51,11 @@ struct DevModel {
     const double* geo = nullptr;        // [E][3] x0, y0, h
     const double* dinv_all = nullptr;   // per element n^2: 1 / (ks_e (mu_a + mu_b + c_e mu_a mu_b))
     const int64_t* dinv_off = nullptr;
+    // axis-aligned PML (Sec. 4), null without one: per element (pa, pb, pc) as 6 doubles (re, im),
+    // the operator pa K(x1) M(x2) + pb M(x1) K(x2) + pc M (x) M (plain elements: 1, 1, c_e), and
+    // the imaginary part of the divide 1 / (pa mu_b + pb mu_a + pc mu_a mu_b) beside dinv_all
+    const double* pml = nullptr;
+    const double* dinv_im = nullptr;
     // per degree table t
     const int* tab_p = nullptr;
     const int64_t* tab_Mt = nullptr;    // offsets into Mt_all ((p+1)^2)

@@ -102,7 +102,8 @@ cd elem_entry(const Model& m, const Elem& E, int a, int b, int c, int d, bool st
     const double Mac = T.Mt[(size_t)a * N + c], Mbd = T.Mt[(size_t)b * N + d];
     cd v = Kt(a, c) * Mbd + Mac * Kt(b, d);
     if (stiff_only) return v;
-    v += E.c * Mac * Mbd;
+    if (E.pml) v = E.pa * (Kt(a, c) * Mbd) + E.pb * (Mac * Kt(b, d)) + E.pc * (Mac * Mbd);
+    else v += E.c * Mac * Mbd;
     if (a == 1 && c == 1) v += E.gam[0] * Mbd;
     if (a == 0 && c == 0) v += E.gam[1] * Mbd;
     if (b == 1 && d == 1) v += E.gam[2] * Mac;
@@ -187,6 +188,52 @@ static void cross_slots(int p, std::vector<int>& X) {
     for (int b = 2; b < N; ++b)
         for (int a = 2; a < N; ++a)
             if (a <= 3 || b <= 3) X.push_back(a + N * b);
+}
+
+// The same for a PML element: A_II = pa K(x1) M(x2) + pb M(x1) K(x2) + pc M (x) M, whose fast
+// diagonalisation divides by D[al][be] = pa mu_be + pb mu_al + pc mu_al mu_be (al along x1)
+static void cross_green_c(const PTable& T, cd pa, cd pb, cd pc, const std::vector<int>& X, std::vector<cd>& G,
+                          double* gap) {
+    const int n = T.n, N = T.p + 1, nx = (int)X.size();
+    std::vector<cd> Dinv((size_t)n * n);
+    double dmin = 1e300, dmax = 0;
+    for (int al = 0; al < n; ++al)
+        for (int be = 0; be < n; ++be) {
+            const cd D = pa * T.mu[be] + pb * T.mu[al] + pc * (T.mu[al] * T.mu[be]);
+            dmin = std::min(dmin, std::abs(D));
+            dmax = std::max(dmax, std::abs(D));
+            Dinv[(size_t)al * n + be] = 1.0 / D;
+        }
+    if (gap) *gap = dmin / dmax;
+    G.assign((size_t)nx * nx, cd(0.0));
+    std::vector<cd> Gs((size_t)n * n), U((size_t)2 * n), W((size_t)n * 2);
+    const double* V = T.V.data();
+    for (int q = 0; q < nx; ++q) {
+        const int i2 = X[q] % N - 2, j2 = X[q] / N - 2;
+        for (int al = 0; al < n; ++al)
+            for (int be = 0; be < n; ++be)
+                Gs[(size_t)al * n + be] = V[(size_t)i2 * n + al] * V[(size_t)j2 * n + be] * Dinv[(size_t)al * n + be];
+        const int nr = std::min(2, n);
+        for (int i = 0; i < nr; ++i)
+            for (int be = 0; be < n; ++be) {
+                cd s = 0;
+                for (int al = 0; al < n; ++al) s += V[(size_t)i * n + al] * Gs[(size_t)al * n + be];
+                U[(size_t)i * n + be] = s;
+            }
+        for (int al = 0; al < n; ++al)
+            for (int j = 0; j < nr; ++j) {
+                cd s = 0;
+                for (int be = 0; be < n; ++be) s += Gs[(size_t)al * n + be] * V[(size_t)j * n + be];
+                W[(size_t)al * 2 + j] = s;
+            }
+        for (int r = 0; r < nx; ++r) {
+            const int i = X[r] % N - 2, j = X[r] / N - 2;
+            cd s = 0;
+            if (i < 2) for (int be = 0; be < n; ++be) s += U[(size_t)i * n + be] * V[(size_t)j * n + be];
+            else for (int al = 0; al < n; ++al) s += V[(size_t)i * n + al] * W[(size_t)al * 2 + j];
+            G[(size_t)r * nx + q] = s;
+        }
+    }
 }
 
 // G = A_II^-1 restricted to the cross (row-major |X| x |X|) for A_II = rho (K (x) M + M (x) K + c M (x) M)
@@ -323,9 +370,14 @@ bool factor(Model& m, int nthreads, std::string& err) {
         std::vector<int> X;
         cross_slots(El.p, X);
         const int nE = El.nE1, nT = El.nT, nX = (int)X.size();
-        std::vector<double> Gr;
-        cross_green(T, El.rho, El.c, X, Gr, &ef[e].gap);
-        std::vector<cd> G(Gr.begin(), Gr.end());
+        std::vector<cd> G;
+        if (El.pml) {
+            cross_green_c(T, El.pa, El.pb, El.pc, X, G, &ef[e].gap);
+        } else {
+            std::vector<double> Gr;
+            cross_green(T, El.rho, El.c, X, Gr, &ef[e].gap);
+            G.assign(Gr.begin(), Gr.end());
+        }
         auto f = [&](int a, int b, int c, int d) { return elem_entry(m, El, a, b, c, d, false); };
         std::vector<cd> AEE, AEX, AXE, AET, AXT, ATE, ATX, ATT;
         dense_block(Es, Es, N, f, AEE);

@@ -40,6 +40,10 @@ struct Elem {
     int64_t X0 = 0, X1 = 0, Y0 = 0, Y1 = 0;       // integer box (finest units)
     double h = 0, x0 = 0, y0 = 0, eps = 1, c = 0;
     double rho = 1;                                // stiffness coefficient (Poisson mode, Sec. 3.1)
+    // PML element (Sec. 4, complex coordinate stretching s_1, s_2): operator
+    // pa K(x1) M(x2) + pb M(x1) K(x2) + pc M (x) M with pa = s2/s1, pb = s1/s2, pc = c s1 s2
+    bool pml = false;
+    cd pa = 1.0, pb = 1.0, pc = 0.0;
     cd gam[4];                                     // Robin gamma_eff per side (set_robin)
     bool boundary[4] = {false, false, false, false};
     int64_t off = 0;                               // start in local vectors
@@ -138,6 +142,9 @@ void set_coefficients(Model& m, double k, const double* eps);
 // Poisson mode: k = 0, eps = 1, rho[e] > 0 per element, zero Dirichlet data on the boundary
 // (no Robin terms); the mesh must be conforming (returns false with err otherwise)
 bool set_poisson(Model& m, const double* rho, std::string& err);
+// Axis-aligned PML (after set_coefficients): s[4e..4e+3] = (Re s1, Im s1, Re s2, Im s2) per
+// element; elements with s1 = s2 = 1 stay plain.  Returns the number of stretched elements.
+int set_pml(Model& m, const double* s);
 // Helmholtz with Dirichlet data on the whole boundary (after set_coefficients): the same
 // constraint split as the Poisson mode, no Robin term on boundary sides, unit rho; the mesh must
 // be conforming (returns false with err otherwise)

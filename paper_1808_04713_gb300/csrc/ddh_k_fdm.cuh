@@ -45,7 +45,8 @@ __device__ inline FdmBatch<T> carve_batch(char* base, int pmax, int qb) {
 
 // A[q] <- dinv .* (V^T A[q] V) for q < Q (the divided spectral coefficients; B scratch)
 template <class T, class G>
-__device__ inline void spec_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int n, int Q) {
+__device__ inline void spec_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int n, int Q,
+                              const double* di = nullptr) {
     const int nn = n * n;
     for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
         const int q = idx / nn, r = idx % nn, al = r / n, bb = r % n;
@@ -60,7 +61,7 @@ __device__ inline void spec_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T
         const cpx<T>* X = b.B + (size_t)q * nn;
         cpx<T> v = mk<T>(0, 0);
         for (int bb = (be & 1); bb < n; bb += 2) fma_r(v, s.V[bb * n + be], X[al * n + bb]);
-        b.A[idx] = s.dinv[r] * v;
+        b.A[idx] = di ? mk<T>(s.dinv[r], (T)di[r]) * v : s.dinv[r] * v;
     }
     g.sync();
 }
@@ -152,7 +153,8 @@ struct FrameTile {
 // element coefficient ks into sign
 template <class T, class G>
 __device__ inline void cross_coupling_b(const G& g, const ElemSmem<T>& s, const FdmBatch<T>& b, int p, T ce, T sign,
-                                        const cpx<T>* xe, const cpx<T>* ut, int stride, int Q) {
+                                        const cpx<T>* xe, const cpx<T>* ut, int stride, int Q,
+                                        const double* pml = nullptr) {
     const int N = p + 1, n = p - 1, n2 = 2 * n;
     for (int idx = g.t(); idx < Q * n2; idx += g.n()) {
         const int q = idx / n2, r = idx % n2, v = r / n, be = r % n;
@@ -163,14 +165,26 @@ __device__ inline void cross_coupling_b(const G& g, const ElemSmem<T>& s, const 
         for (int d = B - 2; d <= B + 2; d += 2)
             if (d >= 2 && d <= p) fma_r(acc, s.Mt[d * N + B], F(v, d));
         for (int w = 0; w < 2; ++w) fma_r(acc, s.Mt[w * N + B], F(v, w));
-        fma_r(x, ce, acc);
+        if (pml) {
+            const cpx<T> pb = mk<T>((T)pml[2], (T)pml[3]), pc = mk<T>((T)pml[4], (T)pml[5]);
+            x = pb * x;
+            fma_c(x, pc, acc);
+        } else {
+            fma_r(x, ce, acc);
+        }
         b.rho[idx] = x;
         const int A = be + 2;
         cpx<T> y = F(A, v);
         cpx<T> acc2 = mk<T>(0, 0);
         for (int c = A - 2; c <= A + 2; c += 2)
             if (c >= 2 && c <= p) fma_r(acc2, s.Mt[A * N + c], F(c, v));
-        fma_r(y, ce, acc2);
+        if (pml) {
+            const cpx<T> pa = mk<T>((T)pml[0], (T)pml[1]), pc = mk<T>((T)pml[4], (T)pml[5]);
+            y = pa * y;
+            fma_c(y, pc, acc2);
+        } else {
+            fma_r(y, ce, acc2);
+        }
         b.kap[idx] = y;
     }
     g.sync();
@@ -222,6 +236,9 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const int64_t off = dm.off[e];
     const T ce = (T)dm.c[e], ks = (T)dm.ks[e];
+    // PML element coefficients and the imaginary part of its divide (null without a PML)
+    const double* pml = dm.pml ? dm.pml + 6 * (int64_t)e : nullptr;
+    const double* di = dm.dinv_im ? dm.dinv_im + dm.dinv_off[e] : nullptr;
     T gam[4];
     elem_gam<T>(dm, e, gam);
     for (int idx = g.t(); idx < cnt * nE; idx += g.n()) {
@@ -245,13 +262,13 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
                 bb.A[idx] = ld<T>(bt, (int64_t)(r0 + q0 + q) * dm.n_local + off + (a + 2) + N * (b + 2));
             }
             g.sync();
-            spec_b<T>(g, s, bb, n, Q);
+            spec_b<T>(g, s, bb, n, Q, di);
             cross_b<T>(g, s, bb, n, Q);
             for (int idx = g.t(); idx < Q * (nE + nT); idx += g.n()) {
                 const int q = idx / (nE + nT), i = idx % (nE + nT);
                 const CrossTile<T> X{bb.rrow + (size_t)q * 2 * n, bb.rcol + (size_t)q * 2 * n, n};
                 const int slot = i < nE ? dm.e1_slot[e1o + i] : dm.t_slot[to + i - nE];
-                const cpx<T> v = apply_A_entry_f<T>(X, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
+                const cpx<T> v = apply_A_entry_f<T>(X, s.Mt, p, ks, ce, gam, slot % N, slot / N, false, false, pml);
                 if (i < nE) rE[(q0 + q) * stride + i] -= v;
                 else if (Y) cT[(q0 + q) * stride + (i - nE)] = v;
             }
@@ -286,14 +303,14 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
         for (int i = g.t(); i < nE; i += g.n()) s.tile[dm.e1_slot[e1o + i]] = xE[q * stride + i];
         g.sync();
         // y_I = A_II^-1 (b_I - A_IE x_E) on the cross: the coupling part first ...
-        cross_coupling<T>(g, s, p, ce, -ks);
+        cross_coupling<T>(g, s, p, ce, -ks, pml);
         spec_from_cross<T>(g, s, n, false);
-        spec_divide<T>(g, s, n);
+        spec_divide<T>(g, s, n, di);
         cross_from_spec<T>(g, s, n);
         cross_to_tile<T>(g, s, p, (T)1);
         if (bt && has_bI) {
             // ... then + A_II^-1 b_I on the cross (the tile keeps the coupling part)
-            interior_load_cross<T>(g, s, bt, (int64_t)r * dm.n_local + off, p, ce);
+            interior_load_cross<T>(g, s, bt, (int64_t)r * dm.n_local + off, p, ce, di);
             for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
                 const int i = idx / n, qq = idx % n;
                 s.tile[(i + 2) + N * (qq + 2)] += s.rrow[i * n + qq];
@@ -303,7 +320,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass1(DevModel dm, const cpx<T>
         }
         for (int i = g.t(); i < nT; i += g.n()) {
             const int slot = dm.t_slot[to + i];
-            tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
+            tT_out[(int64_t)r * dm.nT_tot + to + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false, false, pml);
         }
         g.sync();
     }
@@ -343,6 +360,9 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
     load_tables<T>(g, dm, e, s);
     const int nE = dm.nE1[e], e1o = dm.e1_off[e], nT = dm.nT[e], to = dm.t_off[e];
     const T ce = (T)dm.c[e], ks = (T)dm.ks[e];
+    // PML element coefficients and the imaginary part of its divide (null without a PML)
+    const double* pml = dm.pml ? dm.pml + 6 * (int64_t)e : nullptr;
+    const double* di = dm.dinv_im ? dm.dinv_im + dm.dinv_off[e] : nullptr;
     T gam[4];
     elem_gam<T>(dm, e, gam);
     for (int idx = g.t(); idx < cnt * nT; idx += g.n()) {
@@ -377,14 +397,14 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
         for (int i = g.t(); i < nT; i += g.n()) s.tile[dm.t_slot[to + i]] = uT[q * stride + i];
         g.sync();
         // w_I = A_II^-1 (A_IT u_T) on the cross; r'_E = A_ET u_T - A_EI w_I
-        cross_coupling<T>(g, s, p, ce, ks);
+        cross_coupling<T>(g, s, p, ce, ks, pml);
         spec_from_cross<T>(g, s, n, false);
-        spec_divide<T>(g, s, n);
+        spec_divide<T>(g, s, n, di);
         cross_from_spec<T>(g, s, n);
         cross_to_tile<T>(g, s, p, (T)-1);
         for (int i = g.t(); i < nE; i += g.n()) {
             const int slot = dm.e1_slot[e1o + i];
-            rE[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false);
+            rE[q * stride + i] = apply_A_entry<T>(s.tile, s.Mt, p, ks, ce, gam, slot % N, slot / N, false, false, pml);
         }
         g.sync();
     }
@@ -414,7 +434,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
     g.sync();
     for (int q0 = 0; q0 < cnt; q0 += QB) {
         const int Q = min(QB, cnt - q0);
-        cross_coupling_b<T>(g, s, bb, p, ce, -ks, sE + q0 * stride, uT + q0 * stride, stride, Q);
+        cross_coupling_b<T>(g, s, bb, p, ce, -ks, sE + q0 * stride, uT + q0 * stride, stride, Q, pml);
         for (int idx = g.t(); idx < Q * nn; idx += g.n()) {
             const int q = idx / nn, r = idx % nn, a = r / n, b = r % n;
             cpx<T> v = mk<T>(0, 0);
@@ -424,7 +444,7 @@ __global__ void __launch_bounds__(kFdmThreads) k_pass2(DevModel dm, const cpx<T>
             bb.A[idx] = v;
         }
         g.sync();
-        spec_b<T>(g, s, bb, n, Q);
+        spec_b<T>(g, s, bb, n, Q, di);
         full_b<T>(g, s, bb, n, Q);
         for (int idx = g.t(); idx < Q * N * N; idx += g.n()) {
             const int q = idx / (N * N), r = idx % (N * N), a = r % N, b = r / N;

@@ -139,7 +139,13 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
             if (kv != 0.0) fma_r(t2, kv, v);
         }
         T1[idx] = t1;
-        T2[idx] = t2 + ce * t1;
+        if (dm.pml) {
+            // PML: pb M(x1) K(x2) + pc M (x) M on this side of the product
+            const double* q = dm.pml + 6 * (int64_t)e;
+            T2[idx] = mk<double>(q[2], q[3]) * t2 + mk<double>(q[4], q[5]) * t1;
+        } else {
+            T2[idx] = t2 + ce * t1;
+        }
     }
     for (int idx = threadIdx.x; idx < 2 * N; idx += blockDim.x) {
         const int a = idx % N, bp = idx / N;
@@ -159,7 +165,10 @@ __global__ void __launch_bounds__(128) k_elem_matvec(DevModel dm, const double2*
             const int c = ca[q];
             fma_r(v, s.Mt[a * N + c], T2[c + N * bb]);
             const double kv = kt<double>(a, c);
-            if (kv != 0.0) fma_r(v, kv, T1[c + N * bb]);
+            if (kv != 0.0) {
+                if (dm.pml) fma_c(v, mk<double>(kv * dm.pml[6 * (int64_t)e], kv * dm.pml[6 * (int64_t)e + 1]), T1[c + N * bb]);
+                else fma_r(v, kv, T1[c + N * bb]);
+            }
         }
         // Robin: i g (...) with g the imaginary part of gamma_eff on the side
         cpx<double> rob = mk<double>(0, 0);

@@ -70,7 +70,8 @@ __device__ inline void sinv_apply_batched(const G& g, const cpx<T>* __restrict__
 // A_II^-1 b_I on the cross for one RHS (b_I read from the local vector): leaves the divided
 // spectral coefficients in spec and the cross values in rrow/rcol.
 template <class T, class G>
-__device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, const double2* bt, int64_t base, int p, T ce) {
+__device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, const double2* bt, int64_t base, int p, T ce,
+                                           const double* di = nullptr) {
     const int N = p + 1, n = p - 1;
     for (int idx = g.t(); idx < n * n; idx += g.n()) {
         const int a = idx / n, b = idx % n;
@@ -78,7 +79,7 @@ __device__ inline void interior_load_cross(const G& g, const ElemSmem<T>& s, con
     }
     g.sync();
     spec_from_full<T>(g, s, n);
-    spec_divide<T>(g, s, n);
+    spec_divide<T>(g, s, n, di);
     cross_from_spec<T>(g, s, n);
 }
 

@@ -155,11 +155,40 @@ __device__ __forceinline__ T kt(int a, int c) {
 // the product by ks is exact and leaves every bit as without it).
 template <class T, class F>
 __device__ inline cpx<T> apply_A_entry_f(const F& tile, const T* Mt, int p, T ks, T ce, const T* gam,
-                                          int a, int b, bool stiff_only, bool no_stiff = false) {
+                                          int a, int b, bool stiff_only, bool no_stiff = false,
+                                          const double* pml = nullptr) {
     const int N = p + 1;
     int ca[6], cb[6];
     const int na = cand_list(a, p, ca), nb = cand_list(b, p, cb);
     cpx<T> acc = mk<T>(0, 0);
+    if (pml) {
+        // PML element (complex coefficients, pml = pa, pb, pc as re/im pairs): weights
+        // pa Kt[a][c] Mt[b][d] + pb Mt[a][c] Kt[b][d] + pc Mt[a][c] Mt[b][d]
+        const cpx<T> pa = mk<T>((T)pml[0], (T)pml[1]), pb = mk<T>((T)pml[2], (T)pml[3]),
+                     pc = mk<T>((T)pml[4], (T)pml[5]);
+        for (int i = 0; i < na; ++i) {
+            const int c = ca[i];
+            const T Mac = Mt[a * N + c], Kac = kt<T>(a, c);
+            for (int j = 0; j < nb; ++j) {
+                const int d = cb[j];
+                const T Mbd = Mt[b * N + d], Kbd = kt<T>(b, d);
+                cpx<T> w = mk<T>(0, 0);
+                if (!no_stiff) w = (Kac * Mbd) * pa + (Mac * Kbd) * pb;
+                if (!stiff_only) w += (Mac * Mbd) * pc;
+                if (w.x != (T)0 || w.y != (T)0) fma_c(acc, w, tile(c, d));
+            }
+        }
+        if (!stiff_only) {
+            cpx<T> rob = mk<T>(0, 0);
+            if (a == 1 && gam[0] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile(1, cb[j])); rob += gam[0] * s; }
+            if (a == 0 && gam[1] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int j = 0; j < nb; ++j) fma_r(s, Mt[b * N + cb[j]], tile(0, cb[j])); rob += gam[1] * s; }
+            if (b == 1 && gam[2] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile(ca[i], 1)); rob += gam[2] * s; }
+            if (b == 0 && gam[3] != (T)0) { cpx<T> s = mk<T>(0, 0); for (int i = 0; i < na; ++i) fma_r(s, Mt[a * N + ca[i]], tile(ca[i], 0)); rob += gam[3] * s; }
+            acc.x -= rob.y;
+            acc.y += rob.x;
+        }
+        return ks * acc;
+    }
     for (int i = 0; i < na; ++i) {
         const int c = ca[i];
         const T Mac = Mt[a * N + c], Kac = kt<T>(a, c);
@@ -195,8 +224,9 @@ struct TileRef {
 // (A Phi)[a][b] from the tile (N x N, column-major)
 template <class T>
 __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T ks, T ce, const T* gam,
-                                        int a, int b, bool stiff_only, bool no_stiff = false) {
-    return apply_A_entry_f<T>(TileRef<T>{tile, p + 1}, Mt, p, ks, ce, gam, a, b, stiff_only, no_stiff);
+                                        int a, int b, bool stiff_only, bool no_stiff = false,
+                                        const double* pml = nullptr) {
+    return apply_A_entry_f<T>(TileRef<T>{tile, p + 1}, Mt, p, ks, ce, gam, a, b, stiff_only, no_stiff, pml);
 }
 
 // Interior coupling of the frame values: coupling = Mt_BV X + Y Mt_VB with
@@ -204,7 +234,8 @@ __device__ inline cpx<T> apply_A_entry(const cpx<T>* tile, const T* Mt, int p, T
 // Writes sign * coupling into rrow (interior rows 0,1) and rcol (interior cols 0,1); callers
 // fold the element coefficient ks into sign.
 template <class T, class G>
-__device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T ce, T sign) {
+__device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T ce, T sign,
+                                      const double* pml = nullptr) {
     const int N = p + 1, n = p - 1;
     // X into rho (2 x n), Y into kap (stored [v][a], 2 x n)
     for (int idx = g.t(); idx < 2 * n; idx += g.n()) {
@@ -216,7 +247,14 @@ __device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T
         for (int d = B - 2; d <= B + 2; d += 2)
             if (d >= 2 && d <= p) fma_r(acc, s.Mt[d * N + B], s.tile[v + N * d]);
         for (int w = 0; w < 2; ++w) fma_r(acc, s.Mt[w * N + B], s.tile[v + N * w]);
-        fma_r(x, ce, acc);
+        if (pml) {
+            // PML: X = pb Phi_VB + pc (...): pb multiplies M(x1) K(x2), pc the mass
+            const cpx<T> pb = mk<T>((T)pml[2], (T)pml[3]), pc = mk<T>((T)pml[4], (T)pml[5]);
+            x = pb * x;
+            fma_c(x, pc, acc);
+        } else {
+            fma_r(x, ce, acc);
+        }
         s.rho[v * n + be] = x;
         // Y[al][v] = Phi[al+2][v] + c sum_a Mt[al+2][a+2] Phi[a+2][v]
         const int al = be;
@@ -225,7 +263,14 @@ __device__ inline void cross_coupling(const G& g, const ElemSmem<T>& s, int p, T
         cpx<T> acc2 = mk<T>(0, 0);
         for (int c = A - 2; c <= A + 2; c += 2)
             if (c >= 2 && c <= p) fma_r(acc2, s.Mt[A * N + c], s.tile[c + N * v]);
-        fma_r(y, ce, acc2);
+        if (pml) {
+            // PML: Y = pa Phi_BV + pc (...): pa multiplies K(x1) M(x2)
+            const cpx<T> pa = mk<T>((T)pml[0], (T)pml[1]), pc = mk<T>((T)pml[4], (T)pml[5]);
+            y = pa * y;
+            fma_c(y, pc, acc2);
+        } else {
+            fma_r(y, ce, acc2);
+        }
         s.kap[v * n + al] = y;
     }
     g.sync();
@@ -271,9 +316,14 @@ __device__ inline void spec_from_cross(const G& g, const ElemSmem<T>& s, int n, 
 }
 
 // spec /= D,  D[al][be] = mu_al + mu_be + c mu_al mu_be  (1/D precomputed per element in FP64)
+// With a PML, di = the imaginary part of 1/D (global, per element; null otherwise)
 template <class T, class G>
-__device__ inline void spec_divide(const G& g, const ElemSmem<T>& s, int n) {
-    for (int idx = g.t(); idx < n * n; idx += g.n()) s.spec[idx] = s.dinv[idx] * s.spec[idx];
+__device__ inline void spec_divide(const G& g, const ElemSmem<T>& s, int n, const double* di = nullptr) {
+    if (di) {
+        for (int idx = g.t(); idx < n * n; idx += g.n()) s.spec[idx] = mk<T>(s.dinv[idx], (T)di[idx]) * s.spec[idx];
+    } else {
+        for (int idx = g.t(); idx < n * n; idx += g.n()) s.spec[idx] = s.dinv[idx] * s.spec[idx];
+    }
     g.sync();
 }
 

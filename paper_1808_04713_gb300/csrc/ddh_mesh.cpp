@@ -180,6 +180,8 @@ void set_coefficients(Model& m, double k, const double* eps) {
         Elem& E = m.el[e];
         E.eps = eps[e];
         E.rho = 1.0;
+        E.pml = false;
+        E.pa = 1.0; E.pb = 1.0; E.pc = 0.0;
         E.c = -k * k * E.eps * (0.5 * E.h) * (0.5 * E.h);
         for (int s = 0; s < 4; ++s) {
             const auto& se = m.side_edge[4 * e + s];
@@ -208,6 +210,20 @@ bool set_poisson(Model& m, const double* rho, std::string& err) {
         }
     }
     return true;
+}
+
+int set_pml(Model& m, const double* s) {
+    int n = 0;
+    for (size_t e = 0; e < m.el.size(); ++e) {
+        Elem& E = m.el[e];
+        const cd s1(s[4 * e], s[4 * e + 1]), s2(s[4 * e + 2], s[4 * e + 3]);
+        E.pml = s1 != cd(1.0, 0.0) || s2 != cd(1.0, 0.0);
+        E.pa = s2 / s1;
+        E.pb = s1 / s2;
+        E.pc = E.c * s1 * s2;
+        n += E.pml ? 1 : 0;
+    }
+    return n;
 }
 
 bool set_dirichlet_boundary(Model& m, std::string& err) {

@@ -61,6 +61,7 @@ _SIGS = {
     "ddh_set_coefficients": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p]),
     "ddh_set_poisson": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ddh_set_boundary": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ddh_set_pml": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ddh_dirichlet_point_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ddh_solve_dirichlet": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_double,
                                       C.c_void_p]),
@@ -172,6 +173,13 @@ class DDH:
         """Poisson mode: -div(rho grad phi) = f, zero Dirichlet data, rho per element."""
         r = np.ascontiguousarray(rho, dtype=np.float64)
         self._check(self.lib.ddh_set_poisson(self.h, r.ctypes.data))
+
+    def set_pml(self, s1, s2):
+        """Complex stretch factors per element along x1 and x2 (1 outside the layers)."""
+        a = np.asarray(s1, dtype=np.complex128)
+        b = np.asarray(s2, dtype=np.complex128)
+        v = np.ascontiguousarray(np.stack([a.real, a.imag, b.real, b.imag], axis=1).ravel(), dtype=np.float64)
+        self._check(self.lib.ddh_set_pml(self.h, v.ctypes.data))
 
     def set_boundary(self, kind: int):
         """BOUNDARY_IMPEDANCE (default) or BOUNDARY_DIRICHLET for the Helmholtz problem."""
