@@ -421,7 +421,8 @@ ddh_status ddh_table_gauss(int32_t m, double* x_out, double* w_out);
  * seconds_out[5]: classification and factorisation wall time, the relative residual
  * ||K x - t||/||t|| of one coarse solve with a seeded random t, max_e ||S_E S_E^-1 - I||_max, and
  * the minimum relative resonance gap of the interior blocks; l_out: l in use.  k = 0 selects
- * the Poisson mode of ddh_set_poisson with eps_r read as rho. */
+ * the Poisson mode of ddh_set_poisson with eps_r read as rho; k < 0 the Helmholtz problem with
+ * wavenumber |k| and DDH_BOUNDARY_DIRICHLET. */
 ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem,
                            double k, const double* eps_r, int32_t l_override, int64_t* sizes_out,
                            double* seconds_out, int32_t* l_out);

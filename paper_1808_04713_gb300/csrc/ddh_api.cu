@@ -2666,19 +2666,21 @@ void ddh_destroy(ddh_ctx* ctx) {
 
 ddh_status ddh_host_factor(int32_t base_n, const int32_t* leaves, const int32_t* p, int32_t n_elem, double k,
                            const double* eps, int32_t l_override, int64_t* sizes, double* secs, int32_t* l_out) {
-    if (!leaves || !p || !eps || !sizes || !secs || n_elem <= 0 || !(k >= 0)) return DDH_ERR_INVALID_ARG;
+    if (!leaves || !p || !eps || !sizes || !secs || n_elem <= 0 || !std::isfinite(k)) return DDH_ERR_INVALID_ARG;
     Model m;
     std::string err;
     if (!build_model(m, base_n, leaves, p, n_elem, err)) return DDH_ERR_INVALID_ARG;
     if (k == 0.0) {
         if (!set_poisson(m, eps, err)) return DDH_ERR_INVALID_ARG;
     } else {
-        set_coefficients(m, k, eps);
+        set_coefficients(m, std::fabs(k), eps);
+        if (k < 0.0 && !set_dirichlet_boundary(m, err)) return DDH_ERR_INVALID_ARG;
     }
     const int l = l_override > 0 ? l_override : dispersion_l(m);
     auto t0 = std::chrono::steady_clock::now();
     if (!classify(m, l, err)) return DDH_ERR_INVALID_ARG;
     auto t1 = std::chrono::steady_clock::now();
+    set_robin(m, false);
     m.check_factor = true;
     if (!factor(m, std::max(1u, std::thread::hardware_concurrency()), err)) return DDH_ERR_SINGULAR;
     auto t2 = std::chrono::steady_clock::now();

@@ -95,3 +95,20 @@ def test_dispersion_l_reproduces_the_bold_cells_of_table3(ddh):
             _, _, l_lib = ddh.host_factor(2, W.uniform_leaves(2), np.full(4, 3), 2.0 * kh, np.ones(4))
             seen[(N, k)] = l_lib
         assert bool(bold) == (l >= seen[(N, k)]), (p, N, k, l, seen[(N, k)])
+
+
+@pytest.mark.parametrize("n,p,l,kp", [(1, 8, 1, 11.0), (2, 8, 3, 21.0), (2, 12, 2, 31.0)])
+def test_host_factor_dirichlet_helmholtz_split_matches_oracle(ddh, n, p, l, kp):
+    """Helmholtz with Dirichlet data (k < 0 selects it here; Sec. 3.2): the library's split has the
+    sizes of the oracle's, and its factor (indefinite A11 blocks) passes the self-checks."""
+    from oracle import dirichlet as D
+    m = 2 ** n
+    k, _ = D.table3_problem(kp)
+    sizes, secs, l_used = ddh.host_factor(m, W.uniform_leaves(m), np.full(m * m, p), -k, np.ones(m * m),
+                                          l_override=l)
+    ref = D.Solver(n, p, l, k)
+    assert l_used == l
+    assert (sizes["n_dual"], sizes["n_coarse"]) == (ref.dd.nd, ref.dd.n2)
+    assert sizes["n_e1"] + m * m * (p - 1) ** 2 == ref.dd.n1
+    assert secs[2] <= 1e-11, secs
+    assert secs[3] <= 1e-10, secs
